@@ -1,0 +1,285 @@
+"""Pins of the oracle's time stepping against what the paper and physics fix.
+
+Invariants of one step (Eqs. 12-14, 17-18), the rest state, the flat
+interface profile of Eq. 2, the Laplace law with the surface tension of
+Eq. 4, the shear viscosity of Eq. 27, the ideal-gas term of Eq. 28 (sound
+speed sqrt(T)), Galilean invariance of a convected drop (Sec. III), symmetry,
+and the closed-form force of Eq. 28 on a single Fourier mode.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0902_3921_gb300 import inputs as I
+
+CFG1 = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5, m=4)
+
+
+def test_closed_forms_of_the_configs():
+    """phi_eq, interface width and surface tension (Sec. II, Eqs. 2-4)."""
+    p = O.Params(**CFG1)
+    assert O.phi0_of(p) == 1.0
+    np.testing.assert_allclose(O.xi_of(p), np.sqrt(2 * 0.14 / 0.1), rtol=1e-15)
+    # Eq. 4 (2/3) sqrt(2 a^2 kappa / b) and the textbook form agree for -a = b
+    eq4 = 2 / 3 * np.sqrt(2 * p.a ** 2 * p.kappa / p.b)
+    np.testing.assert_allclose(O.sigma_of(p), eq4, rtol=1e-14)
+    np.testing.assert_allclose(O.sigma_of(p), 0.111554670, rtol=1e-8)
+    # the paper's own parameters (Sec. III): xi of Eq. 3 is about 5 lattice units
+    pp = O.Params(a=-1e-3, b=1e-3, kappa=3e-3)
+    assert 4.5 < 2 * O.xi_of(pp) < 5.0
+    np.testing.assert_allclose(O.sigma_of(pp), 1.63299e-3, rtol=1e-5)
+
+
+def test_force_on_a_fourier_mode():
+    """F = -phi d_D mu (Eq. 28) on phi = eps sin(kx) with b = 0 has the closed
+    form -eps^2 (a - kappa lam) s sin(kx) cos(kx), lam and s the symbols of
+    lap_D and d_Dx (Eqs. 30-31)."""
+    for N, Q in [(0.5, 1.0), (0.3, 2.5)]:
+        p = O.Params(Lx=32, Ly=8, a=-0.1, b=0.0, kappa=0.14, N=N, Q=Q)
+        x = np.arange(32.0)[None, :] + np.zeros((8, 1))
+        k = 2 * np.pi * 3 / 32
+        eps = 0.2
+        phi = eps * np.sin(k * x)
+        M = (1 - 2 * N) / 4
+        R = (1 - Q) / 2
+        lam = 2 * Q * (np.cos(k) + 1) + 4 * R * np.cos(k) - 4 * (Q + R)
+        s = 2 * np.sin(k) * (N + 2 * M)
+        F = O.force(p, phi, np.ones_like(phi), t=0)
+        want = -eps * eps * (p.a - p.kappa * lam) * s * np.sin(k * x) * np.cos(k * x)
+        np.testing.assert_allclose(F[0], want, atol=1e-15)
+        np.testing.assert_allclose(F[1], 0.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_step_invariants(dims):
+    """Sum n is unchanged by a step (Eqs. 13, 17) and the population momentum
+    sum f e grows by exactly sum F (Eqs. 14, 18, 20, 26)."""
+    rng = np.random.default_rng(7)
+    if dims == 2:
+        p = O.Params(dims=2, Lx=20, Ly=14, tau=0.8, g=(1e-4, 3e-5, 0), force_steps=100, **{
+            k: v for k, v in CFG1.items() if k != "tau"})
+    else:
+        p = O.Params(dims=3, Lx=8, Ly=7, Lz=6, N=1 / 6, Q=1 / 3, m=8, tau=1.2,
+                     g=(1e-4, 3e-5, -2e-5), force_steps=100,
+                     **{k: v for k, v in CFG1.items() if k not in ("N", "Q", "m", "tau")})
+    phi = 0.8 * (rng.random(p.shape) - 0.5)
+    n = 1 + 0.02 * (rng.random(p.shape) - 0.5)
+    u = 0.01 * (rng.random((dims,) + p.shape) - 0.5)
+    f = O.init(p, n, phi, u)
+    e, _ = O.lattice(dims)
+    e = e[:, :dims].astype(float)
+    for t in range(5):
+        dens = f.sum(0)
+        mom = np.einsum("is,ia->a", f.reshape(len(e), -1), e)
+        F = O.force(p, phi, dens, t)
+        O.lb_step(p, f, phi, t)
+        O.fd_step(p, phi, np.zeros((dims,) + p.shape))
+        np.testing.assert_allclose(f.sum(), dens.sum(), rtol=1e-14)
+        mom2 = np.einsum("is,ia->a", f.reshape(len(e), -1), e)
+        np.testing.assert_allclose(mom2 - mom, F.reshape(dims, -1).sum(1), atol=1e-14)
+
+
+@pytest.mark.parametrize("dims,phival", [(2, 1.0), (2, -1.0), (2, 0.0), (3, 1.0), (3, -1.0)])
+def test_rest_state_is_a_fixed_point(dims, phival):
+    """Uniform n, phi = +-phi0 or 0 and u = 0: F = 0, f = feq, no flux (Sec. III).
+    phi stays exactly as it is, u* below 1e-30; the populations move by a few
+    ulp because the binary weights 4/9, 1/9, 1/36 do not sum to exactly 1."""
+    if dims == 2:
+        p = O.Params(Lx=12, Ly=10, **CFG1)
+    else:
+        p = O.Params(dims=3, Lx=6, Ly=5, Lz=4, **{**CFG1, "N": 1 / 6, "Q": 1 / 3, "m": 8})
+    n, u = I.rest(dims, p.Lx, p.Ly, p.Lz)
+    phi = np.full(p.shape, phival)
+    st = O.State.create(p, n, phi, u)
+    f0 = st.f.copy()
+    st.run(20)
+    assert np.max(np.abs(st.f - f0)) <= 4e-16
+    assert np.array_equal(st.phi, phi)
+    _, uu = st.moments()
+    assert np.max(np.abs(uu)) < 1e-30
+
+
+def test_flat_interface_profile():
+    """A sharp planar interface relaxes to phi0 tanh(x/xi) (Eq. 2, Sec. III,
+    Fig. 2) and the velocities decay.  The gap to Eq. 2 is the discretisation
+    error of the FD equilibrium: it shrinks by about 4 when xi doubles
+    (kappa x 4), i.e. second order, SC and OC alike.  Quasi-1D 64 x 4 lattice."""
+    errs = {}
+    for tau, N, Q, kappa, m, steps in [(1.0, 0.5, 1.0, 0.14, 4, 4000),
+                                       (2.0, 0.3, 2.5, 0.14, 4, 4000),
+                                       (1.0, 0.5, 1.0, 0.56, 16, 5000)]:
+        p = O.Params(Lx=64, Ly=4, **{**CFG1, "tau": tau, "N": N, "Q": Q, "kappa": kappa,
+                                     "m": m})
+        phi0, xi = O.phi0_of(p), O.xi_of(p)
+        # a sharp initial interface (width xi/2) that must widen to xi
+        phi = I.flat_interface(2, 64, 4, phi0=phi0, xi=xi / 2)
+        n, u = I.rest(2, 64, 4)
+        st = O.State.create(p, n, phi, u)
+        st.run(steps)
+        exact = I.flat_interface(2, 64, 4, phi0=phi0, xi=xi)
+        errs[(tau, kappa)] = np.max(np.abs(st.phi - exact))
+        _, uu = st.moments()
+        assert np.max(np.abs(uu)) < 5e-6, (tau, np.max(np.abs(uu)))
+        # the profile is flat along y
+        assert np.max(np.abs(st.phi - st.phi[:1])) < 1e-12
+    assert 0.015 < errs[(1.0, 0.14)] < 0.025, errs
+    assert 0.015 < errs[(2.0, 0.14)] < 0.025, errs
+    assert errs[(1.0, 0.56)] < 0.0065, errs
+    assert errs[(1.0, 0.14)] / errs[(1.0, 0.56)] > 3.3, errs
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """Drop of radius 16 on 64^2 (the FP64 drop configuration, 2000 steps):
+    the pressure jump p0(centre) - p0(corner) (Eq. 6), averaged over the second
+    half of the run, matches sigma / R_eff with sigma = 0.1115547 (Eq. 4).
+    The spurious speed stays small and mass is conserved."""
+    p = O.Params(Lx=64, Ly=64, **CFG1)
+    phi = I.drop(2, 64, 64, R=16, phi0=O.phi0_of(p), xi=O.xi_of(p))
+    n, u = I.rest(2, 64, 64)
+    st = O.State.create(p, n, phi, u)
+    dps = []
+    for k in range(40):
+        st.run(50)
+        if st.t > 1000:
+            d = st.diagnostics()
+            dps.append(d["dp"])
+    laplace = O.sigma_of(p) / d["R_eff"]
+    np.testing.assert_allclose(np.mean(dps), laplace, rtol=0.06)
+    assert abs(d["sum_n"] - 4096) < 1e-9
+    assert 1e-4 < d["u_max"] < 5e-3
+    assert d["r_cm"] == pytest.approx([32.0, 32.0], abs=1e-9)
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.0, 1.5])
+def test_shear_wave_viscosity(tau):
+    """u_x = U sin(2 pi y / L) in uniform phi decays as exp(-nu k^2 t) with
+    nu = cs2 (tau - 1/2) (Eq. 27 at n = 1)."""
+    L = 32
+    p = O.Params(Lx=4, Ly=L, **{**CFG1, "tau": tau})
+    n, _ = I.rest(2, 4, L)
+    u = I.shear_wave(2, 4, L, U=1e-4)
+    phi = np.ones(p.shape)
+    st = O.State.create(p, n, phi, u)
+    y = np.arange(L)
+    mode = np.sin(2 * np.pi * y / L)
+    amps, ts = [], []
+    for k in range(8):
+        st.run(25)
+        _, uu = st.moments()
+        amps.append(np.sum(uu[0][:, 0] * mode) / np.sum(mode * mode))
+        ts.append(st.t)
+    rate = -np.polyfit(ts[2:], np.log(amps[2:]), 1)[0]
+    nu = (tau - 0.5) / 3
+    kk = 2 * np.pi / L
+    np.testing.assert_allclose(rate, nu * kk * kk, rtol=1e-2)
+
+
+@pytest.mark.parametrize("T,phibar", [(1 / 3, 0.0), (0.25, 0.0), (0.4, 0.0), (1 / 3, 1.0),
+                                       (0.25, -1.0)])
+def test_sound_speed(T, phibar):
+    """Linear sound in a uniform mixture.  Momentum obeys d_t(n u) =
+    -grad(n T) - phi grad mu (Eqs. 9, 25, 28 with the ideal-gas term
+    grad((cs2 - T) n)) and phi is carried by the flow (Eq. 10), so a density
+    wave exp(ikx) moves at c^2 = T + phibar^2 (a + 3 b phibar^2 + kappa k^2).
+    phibar = 0 isolates T; phibar = +-1 checks the sign and size of
+    -phi grad mu.  Standing wave n = 1 + eps cos(kx), 64 x 2, tau = 0.6."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    L = 64
+    p = O.Params(Lx=L, Ly=2, **{**CFG1, "T": T, "tau": 0.6})
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    n = 1 + 1e-4 * np.cos(k * x)[None, :] * np.ones((2, 1))
+    u = np.zeros((2, 2, L))
+    st = O.State.create(p, n, np.full((2, L), phibar), u)
+    vals = []
+    for _ in range(400):
+        st.run(1)
+        nn, _ = st.moments()
+        vals.append(np.sum((nn[0] - 1) * np.cos(k * x)))
+    t = np.arange(1, 401)
+    y = np.array(vals) / vals[0]
+
+    def model(t, A, g, w, ph, B, d):
+        return A * np.exp(-g * t) * np.cos(w * t + ph) + B * np.exp(-d * t)
+
+    # the stencil derivative of cos(kx) has symbol sin(k) (2N + 4M = 1) and the
+    # 5-point / stencil Laplacians give k^2 up to O(k^4); both are < 0.1 % here
+    c2 = T + phibar ** 2 * (p.a + 3 * p.b * phibar ** 2 + p.kappa * k * k)
+    w0 = k * np.sqrt(c2)
+    popt, _ = scipy_opt.curve_fit(model, t, y, p0=[1, 1e-3, w0, 0, 0, 1e-3], maxfev=20000)
+    np.testing.assert_allclose(abs(popt[2]), w0, rtol=1.5e-2)
+
+
+def test_translation_equivariance_is_bitwise():
+    """Shifting the initial fields by whole lattice vectors shifts the state
+    after 30 steps bit for bit (periodic lattice, Sec. II)."""
+    rng = np.random.default_rng(8)
+    p = O.Params(Lx=24, Ly=20, **{**CFG1, "g": (1e-5, 0, 0), "force_steps": 10})
+    phi = 0.5 * (rng.random(p.shape) - 0.5)
+    n, u = I.rest(2, 24, 20)
+    a = O.State.create(p, n, phi, u)
+    b = O.State.create(p, n, np.roll(phi, (3, 5), axis=(0, 1)), u)
+    a.run(30)
+    b.run(30)
+    assert np.array_equal(np.roll(a.phi, (3, 5), axis=(0, 1)), b.phi)
+    assert np.array_equal(np.roll(a.f, (3, 5), axis=(1, 2)), b.f)
+
+
+def test_transposition_symmetry():
+    """Swapping x and y maps the scheme onto itself: phi^T and u with swapped
+    components, to round-off (the stencils of Eq. 30 are transposes)."""
+    rng = np.random.default_rng(9)
+    p = O.Params(Lx=16, Ly=16, **CFG1)
+    phi = 0.5 * (rng.random(p.shape) - 0.5)
+    n, u = I.rest(2, 16, 16)
+    a = O.State.create(p, n, phi, u)
+    b = O.State.create(p, n, phi.T.copy(), u)
+    a.run(40)
+    b.run(40)
+    np.testing.assert_allclose(a.phi.T, b.phi, atol=1e-13)
+    _, ua = a.moments()
+    _, ub = b.moments()
+    np.testing.assert_allclose(ua[0].T, ub[1], atol=1e-15)
+    np.testing.assert_allclose(ua[1].T, ub[0], atol=1e-15)
+
+
+PAPER = dict(a=-1e-3, b=1e-3, kappa=3e-3, tau=1.0, Gamma=5.0, N=0.3, Q=2.5, m=1)
+
+
+@pytest.mark.slow
+def test_galilean_convected_drop():
+    """Sec. III, Figs. 5-6, with the paper's parameters (-a = b = 1e-3,
+    kappa = 3e-3, Gamma = 5, tau = 1, OC) on a half-size box: a drop of
+    radius 16 on 128 x 64 is pushed by G = n g_x, g_x = 3e-5, for 250 steps and
+    then left free.  The whole fluid reaches 250 g_x; afterwards the drop's
+    centre of mass (Eq. 40) moves with the fluid velocity at that point
+    (v_CM = v_f within 1 %) and keeps its shape (diameter ratio within 3 %)."""
+    p = O.Params(Lx=128, Ly=64, **{**PAPER, "g": (3e-5, 0, 0), "force_steps": 250})
+    phi = I.drop(2, 128, 64, R=16, phi0=O.phi0_of(p), xi=O.xi_of(p))
+    n, u = I.rest(2, 128, 64)
+    st = O.State.create(p, n, phi, u)
+    st.run(300)
+    xs, vfs = [st.diagnostics()["r_cm"][0]], []
+    for _ in range(4):
+        st.run(100)
+        d = st.diagnostics()
+        xs.append(d["r_cm"][0])
+        vfs.append(d["v_f"][0])
+    v_cm = np.diff(xs) / 100.0
+    nn, uu = st.moments()
+    # -phi d_D mu does not sum to exactly zero on the lattice, so the free
+    # drop loses a little momentum (0.2 % here)
+    assert np.sum(nn * uu[0]) / np.sum(nn) == pytest.approx(250 * 3e-5, rel=5e-3)
+    np.testing.assert_allclose(np.mean(v_cm), np.mean(vfs), rtol=1e-2)
+    cx, cy = d["r_cm"]
+
+    def width(profile, c):
+        prof = np.roll(profile, len(profile) // 2 - int(round(c)))
+        s = np.sign(prof)
+        idx = np.where(s[:-1] != s[1:])[0]
+        zs = [i + prof[i] / (prof[i] - prof[i + 1]) for i in idx]
+        return zs[-1] - zs[0]
+
+    ratio = (width(st.phi[int(round(cy)) % 64], cx) / width(st.phi[:, int(round(cx)) % 128], cy))
+    assert abs(ratio - 1) < 0.03
