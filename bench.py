@@ -1,0 +1,313 @@
+"""Benchmark of the hybrid lattice Boltzmann hot path on GB300.
+
+Workload (the throughput configuration of the method): D2Q9 spinodal
+decomposition on a 1024 x 1024 periodic lattice, FP32-deviation populations,
+a = -0.1, b = 0.1, kappa = 0.14, tau = 1, Gamma = 0.5, OC stencil (N = 0.3,
+Q = 2.5), m = 4 FD substeps, phi uniform in [-0.01, 0.01] (splitmix64, seed
+0), n = 1, u = 0; 20000 LB steps.
+
+One timed "step" of this benchmark is one call lbm_step(h, 1000): 1000 LB
+steps of the whole hot path (stencil force, collide/stream, FD update), so the
+default --steps 20 covers the configuration's 20000 LB steps.  L2 is flushed
+(a 256 MiB write) between timed steps.  Metric: MLUPS = sites x LB steps /
+seconds / 1e6, whole job.
+
+--impl reference times the FP64 CPU oracle (single thread) on the same
+workload, each step one LB step of the 1024 x 1024 lattice.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L = 1024
+LB_PER_STEP = 1000
+CFG = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+M_SUB = 4
+# algorithmic bytes per site of the collide kernel (FP32 deviations):
+# populations read + written (2 x 9 x 4 B) and phi read (4 B)
+COLLIDE_BYTES_PER_SITE = 76
+METRIC = "MLUPS (D2Q9 hybrid LB + FD step)"
+WORKLOAD = "spinodal-1024x1024-d2q9-f32dev"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(seed):
+    from paper_0902_3921_gb300 import inputs as I
+    phi = I.spinodal(2, L, L, seed=seed)
+    n, u = I.rest(2, L, L)
+    return n, phi, u
+
+
+def cpu_oracle_mlups(steps=1, seed=0):
+    """The FP64 oracle as it stands, single thread, `steps` LB steps of the
+    1024^2 workload.  Returns (MLUPS, seconds)."""
+    import oracle as O
+    O.build()
+    op = O.Params(Lx=L, Ly=L, m=M_SUB, **CFG)
+    n, phi, u = make_inputs(seed)
+    st = O.State.create(op, n, phi, u)
+    t0 = time.perf_counter()
+    st.run(steps)
+    dt = time.perf_counter() - t0
+    return L * L * steps / dt / 1e6, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = 1
+    times = []
+    for k in range(args.warmup + args.steps):
+        mlups, dt = cpu_oracle_mlups(1, seed=k)
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = L * L * args.steps / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": [L, L],
+                       "lb_steps_per_timed_step": 1,
+                       "note": "FP64 CPU oracle, single thread, one LB step per timed step"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} LB steps of the 1024x1024 workload"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_0902_3921_gb300 import build as B
+    from paper_0902_3921_gb300 import lbm
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    lib = lbm.load_library()
+    stream = torch.cuda.Stream()
+    params = lbm.LbmParams(Lx=L, Ly=L, fd_substeps=M_SUB, precision=lbm.LBM_F32DEV, **CFG)
+    S = params.S
+    n, phi, u = make_inputs(seed=rank)
+    lat = lbm.Lattice(params, stream=stream.cuda_stream)
+    lat.init_fields(n, phi, u)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fd_launches = (M_SUB + 3) // 4
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (also builds and caches the CUDA graphs)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lat.step(LB_PER_STEP)
+        lat.synchronize()
+    # timed region: device-resident state, K x lbm_step(1000), L2 flushed between
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                lat.step(LB_PER_STEP)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * S * LB_PER_STEP * args.steps / (ms_max / 1000.0) / 1e6
+
+    # kernel timing region: the same steps, each kernel bracketed by events
+    lbm.lbm_set_kernel_timing(lat.handle, True)
+    lbm.lbm_kernel_times(lat.handle, reset=True)
+    with torch.cuda.stream(stream):
+        lat.step(2000)
+    kt = lbm.lbm_kernel_times(lat.handle, reset=True)
+    lbm.lbm_set_kernel_timing(lat.handle, False)
+    coll_ms, coll_n = kt["collide"]
+    fd_ms, fd_n = kt["fd"]
+    coll_avg_s = coll_ms / coll_n / 1000.0
+    achieved = COLLIDE_BYTES_PER_SITE * S / coll_avg_s / 1e9
+    peak, peak_kind = measured_peak()
+
+    # end to end through the C ABI with host buffers: H2D of the inputs from
+    # pinned memory, 1000 LB steps, D2H of n, phi, u*
+    pin = {k: torch.empty(S, dtype=torch.float64).pin_memory() for k in
+           ("n", "phi", "ux", "uy", "on", "ophi", "oux", "ouy")}
+    pin["n"].numpy()[:] = n.reshape(-1)
+    pin["phi"].numpy()[:] = phi.reshape(-1)
+    pin["ux"].numpy()[:] = u[0].reshape(-1)
+    pin["uy"].numpy()[:] = u[1].reshape(-1)
+    import ctypes
+    P = {k: ctypes.cast(v.data_ptr(), ctypes.POINTER(ctypes.c_double)) for k, v in pin.items()}
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        rc = lib.lbm_init_fields(lat.handle, P["n"], P["phi"], P["ux"], P["uy"], None)
+        rc |= lib.lbm_step(lat.handle, LB_PER_STEP)
+        rc |= lib.lbm_moments(lat.handle, P["on"], P["ophi"], P["oux"], P["ouy"], None)
+        if rc:
+            raise RuntimeError(lbm.lbm_last_error(lat.handle))
+    t_e2e = time.perf_counter() - t0
+    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * S * LB_PER_STEP * e2e_steps / float(te.item()) / 1e6
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            steps_cpu = args.cpu_sample_steps
+            mlups, dt = cpu_oracle_mlups(steps_cpu)
+            cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{steps_cpu} LB steps of the 1024x1024 workload "
+                             f"({dt:.1f} s, single thread)"}
+        gpu_launches = args.steps * LB_PER_STEP * (1 + fd_launches)
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": [L, L], "lb_steps_per_timed_step":
+                       LB_PER_STEP, "fd_substeps": M_SUB, "precision": "f32 deviations",
+                       "params": CFG, "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "collide2d (stencil force + collide + stream)",
+                         "bytes_per_site": COLLIDE_BYTES_PER_SITE,
+                         "avg_launch_us": coll_avg_s * 1e6, "peak_kind": peak_kind,
+                         "fd_avg_launch_us": fd_ms / max(fd_n, 1) * 1000.0},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 4 * 8 * S, "d2h_bytes_per_step": 4 * 8 * S,
+                    "lb_steps_per_step": LB_PER_STEP},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * hybrid_lbm.h -- C ABI of the GB300 (sm_103a) implementation of the hybrid
+ * free-energy lattice Boltzmann scheme for binary fluid mixtures of
+ * Tiribocchi, Stella, Gonnella and Lamura (arXiv:0902.3921).
+ *
+ * One LB step (Sec. II) is, at every lattice site r of a periodic
+ * Lx x Ly (x Lz) lattice with unit spacing and unit LB time step:
+ *   1. mu = a phi + b phi^3 - kappa lap_D phi                         (Eq. 5)
+ *   2. F  = -phi d_D mu [+ d_D((cs^2 - T) n)] [+ n g while t < force_steps]
+ *                                                              (Eq. 28, Sec. III)
+ *      with the 3x3 "stencil" operators d_D (N, M) and lap_D (Q, R) of
+ *      Eqs. 30-31 (M = (1-2N)/4, R = (1-Q)/2; D3Q19: M = (1-2N)/8, R = (1-Q)/4)
+ *   3. n = sum_i f_i, n u* = sum_i f_i e_i + F/2                  (Eqs. 12, 18)
+ *   4. f_i(r + e_i, t+1) = f_i - (f_i - feq_i(n, u*))/tau + F_i
+ *      with feq of Eq. 15 and the forcing term F_i of Eq. 29       (Eq. 17)
+ *   5. phi(t) -> phi(t+1) by m substeps of dt = 1/m (Sec. II C), each an
+ *      upwind convective half step (Eqs. 32-35) with u*(t) and an explicit
+ *      diffusive half step (Eq. 36) with the 5-point (7-point) Laplacian.
+ * Both halves of a step read the state at time t.  Lattices: D2Q9 (Sec. II A,
+ * Fig. 1) and its 3D generalisation D3Q19.
+ *
+ * Conventions for every entry point:
+ *   - Host arrays are caller-owned, read or written only during the call,
+ *     row-major [z][y][x] (site s = (z*Ly + y)*Lx + x), FP64.
+ *   - The handle owns all device memory it allocates.  Calls on one handle
+ *     are not thread-safe; distinct handles are independent.
+ *   - Work is queued on the handle's CUDA stream.  lbm_step returns without
+ *     waiting; every other call that returns data waits for the stream.
+ *   - Errors are negative return codes, latched on the handle: after an
+ *     error the handle refuses further work (except lbm_free and
+ *     lbm_last_error) and lbm_last_error() says what failed.  Nothing aborts
+ *     the process.
+ */
+#ifndef HYBRID_LBM_H
+#define HYBRID_LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,     /* bad parameter, size or pointer                      */
+  LBM_ECUDA = -2,      /* a CUDA runtime call failed                          */
+  LBM_ENOMEM = -3,     /* device allocation failed                            */
+  LBM_ENONFINITE = -4, /* NaN or Inf found by lbm_diagnostics                 */
+  LBM_ETIMEOUT = -5,   /* a bounded device wait gave up                       */
+  LBM_ESTATE = -6      /* call out of order (e.g. lbm_step before init)      */
+};
+
+/* Storage/compute precision of the populations (h_i = f_i - w_i is stored). */
+enum {
+  LBM_F64 = 0,    /* FP64 populations, phi and arithmetic                      */
+  LBM_F32DEV = 1, /* FP32 deviations h_i = f_i - w_i, FP32 phi and arithmetic  */
+  LBM_F16DEV = 2  /* FP16 deviations scaled by 2^f16_scale_log2, FP32 phi and
+                     arithmetic                                                */
+};
+
+enum {
+  LBM_ADV_PAPER = 0, /* Eqs. 32-35 as printed (does not conserve sum phi)     */
+  LBM_ADV_FLUX = 1   /* conservative upwind flux form, same stencil radius    */
+};
+
+typedef struct {
+  int dims;              /* 2 (D2Q9) or 3 (D3Q19)                              */
+  int Lx, Ly, Lz;        /* periodic lattice, each >= 3; Lz ignored in 2D      */
+  double a, b, kappa;    /* free energy, Eq. 1; b > 0, kappa >= 0              */
+  double T;              /* temperature of the ideal-gas term (Eqs. 1, 28)     */
+  double tau;            /* relaxation time (Eq. 11), > 1/2                    */
+  double Gamma;          /* mobility (Eq. 10), >= 0                            */
+  double N, Q;           /* stencil parameters of Eqs. 30-31                   */
+  int fd_substeps;       /* m of Sec. II C: 0 = smallest m with the diffusive
+                            step's stiffness * dt <= 1.5; m > 0 must meet the
+                            Euler bound (stiffness * dt <= 2); m < 0 forces |m| */
+  int adv_variant;       /* LBM_ADV_PAPER or LBM_ADV_FLUX                       */
+  int cubic_at_half;     /* 0: b lap (phi^n)^3 as in Eq. 36; 1: cube of phi^{n+1/2} */
+  double g[3];           /* body force per unit density, G = n g (Sec. III)    */
+  long long force_steps; /* G acts at steps t = 0 .. force_steps-1             */
+  int precision;         /* LBM_F64, LBM_F32DEV or LBM_F16DEV                  */
+  int f16_scale_log2;    /* FP16 scale exponent s (0 = default 10), 0..14      */
+} lbm_params;
+
+/* FP64 observables (Sec. III) at the handle's current time t. */
+typedef struct {
+  long long t;
+  double sum_n;       /* sum of n over all sites                               */
+  double sum_phi;     /* sum of phi                                            */
+  double momentum[3]; /* sum of n u*                                           */
+  double u_max;       /* max |u*| (Table I reports u_max / c_s)                */
+  double dp;          /* p0(centre site) - p0(site 0), p0 of Eq. 6 with the
+                         stencil operators: the Laplace jump of a centred drop */
+  double r_cm[3];     /* sum phi r / sum phi over sites with phi > 0 (Eq. 40),
+                         periodic images nearest to the previous r_cm (the box
+                         centre before the first call)                         */
+  double v_f[3];      /* u* at r_cm, bi/trilinear, periodic (Sec. III)          */
+  double area;        /* sum (1 + phi/phi0)/2, phi0 = sqrt(-a/b) (or 1 if a>=0)*/
+  double R_eff;       /* sqrt(area/pi) in 2D, (3 area / 4 pi)^(1/3) in 3D      */
+  int nonfinite;      /* 1 if any n, u* or phi is NaN or Inf                   */
+} lbm_diag;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Validates *params (EINVAL: tau <= 1/2, b <= 0, kappa < 0, Gamma < 0, a side
+ * < 3, dims not 2 or 3, N or Q not finite, a requested m below the Euler bound,
+ * unknown precision/variant), picks m (Sec. II C), allocates device memory and
+ * returns a handle in *out (NULL on error; the error text is then available
+ * from lbm_last_error(NULL)).  cuda_stream is a cudaStream_t to queue work on,
+ * or NULL for a stream owned by the handle.  Does not initialise the fields. */
+int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out);
+
+/* Sets t = 0, phi(0) = phi and populations f_i = feq_i(n, u - F/(2n)) (Eqs. 15,
+ * 18), F from Eq. 28 at t = 0, so that the u* of Eq. 18 at t = 0 equals u.
+ * n, phi, ux, uy (and uz in 3D; ignored and may be NULL in 2D) are host arrays
+ * of Lx*Ly*Lz doubles.  n must be > 0 (not checked per site). */
+int lbm_init_fields(lbm_handle *h, const double *n, const double *phi,
+                    const double *ux, const double *uy, const double *uz);
+
+/* Advances nsteps >= 0 LB steps (each: one LB step and m FD substeps).
+ * Asynchronous: returns once the work is queued (CUDA graphs when enabled).
+ * ESTATE before lbm_init_fields/lbm_load. */
+int lbm_step(lbm_handle *h, long long nsteps);
+
+/* n(t), phi(t) and u*(t) (Eq. 18, including F/2) into host arrays of Lx*Ly*Lz
+ * doubles; any output pointer may be NULL to skip it.  Waits for the stream. */
+int lbm_moments(lbm_handle *h, double *n, double *phi, double *ux, double *uy,
+                double *uz);
+
+/* The pre-collision populations f_i(r, t) as a host array [q][z][y][x] of
+ * doubles, q = 9 (D2Q9) or 19 (D3Q19), in the direction order of lbm_lattice. */
+int lbm_populations(lbm_handle *h, double *f);
+
+/* Copies the lattice vectors (q rows of 3 ints) and weights (q doubles) used by
+ * lbm_populations; either pointer may be NULL.  Returns q, or EINVAL. */
+int lbm_lattice(int dims, int *e, double *w);
+
+/* FP64 diagnostics at the current t (deterministic reduction order).  Returns
+ * ENONFINITE (and fills *out) when a NaN/Inf is found; the handle stays usable. */
+int lbm_diagnostics(lbm_handle *h, lbm_diag *out);
+
+/* Waits for all queued work; returns the first latched error. */
+int lbm_synchronize(lbm_handle *h);
+
+long long lbm_time(const lbm_handle *h);       /* current LB step t, or -1     */
+int lbm_fd_substeps(const lbm_handle *h);      /* the m in use, or -1          */
+
+/* 1 (default) captures lbm_step into CUDA graphs; 0 launches kernels one by
+ * one.  Kernel timing (below) forces one-by-one launches. */
+int lbm_set_graphs(lbm_handle *h, int enable);
+
+/* When enabled, every kernel of lbm_step is bracketed by CUDA events on the
+ * handle's stream and lbm_kernel_times returns, per kernel family, the summed
+ * milliseconds and launch counts since the last reset.  Families:
+ * 0 = collide/stream (steps 1-4), 1 = FD update (step 5), 2 = density (only
+ * when T != 1/3).  ms and launches point to arrays of 3; reset != 0 clears. */
+int lbm_set_kernel_timing(lbm_handle *h, int enable);
+int lbm_kernel_times(lbm_handle *h, double *ms, long long *launches, int reset);
+
+/* Raw checkpoint: header (magic, version, parameters, t, precision, CRC32)
+ * followed by the device state.  lbm_load needs a handle created with equal
+ * parameters and restores t; it returns EINVAL on a mismatch or bad CRC. */
+int lbm_save(lbm_handle *h, const char *path);
+int lbm_load(lbm_handle *h, const char *path);
+
+/* Frees the handle and its device memory (and its stream if it owns one).
+ * NULL-safe.  Does not free a caller-provided stream. */
+void lbm_free(lbm_handle *h);
+
+/* Text of the last error on h (or of the last failed lbm_create if h is
+ * NULL); "" when there is none.  Valid until the next call on h. */
+const char *lbm_last_error(const lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYBRID_LBM_H */

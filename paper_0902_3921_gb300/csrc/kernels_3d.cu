@@ -1,0 +1,414 @@
+// kernels_3d.cu -- D3Q19 hot path on sm_103a (the 3D generalisation of the
+// paper's D2Q9 scheme).  Same structure as the 2D kernels:
+//   collide3d : phi tile + halo 2 in shared memory -> mu (Eq. 5, 19-point lap_D)
+//               -> F (Eq. 28, 19-point d_D) -> pull streaming -> n, u* -> BGK
+//               with the Guo forcing term (Eqs. 15, 17, 29).
+//   fd3d      : `sub` substeps of Eqs. 32-36 (7-point Laplacian) per launch,
+//               blocked in shared memory with halo 3 per substep.
+//   density3d : n - 1 for the T != 1/3 force term.
+// Stencils (3D reading of Eqs. 30-31): d_D has N on the two face neighbours
+// along the axis and M on the eight edge neighbours with a non-zero component
+// along it (2N + 8M = 1); lap_D has Q on the six faces, R on the twelve edges
+// and -(6Q + 12R) at the centre (Q + 4R = 1).
+#include "lbm_common.cuh"
+
+namespace hlbm {
+
+namespace {
+
+constexpr int C3_TX = 32, C3_TY = 8, C3_TZ = 4;  // block 32 x 8, 4 z-planes per thread
+
+template <typename S, typename C, bool TGEN, int MODE>
+__global__ void __launch_bounds__(256)
+    collide3d_kernel(const S *__restrict__ hin, S *__restrict__ hout, const C *__restrict__ phi,
+                     const C *__restrict__ dn, C *__restrict__ uout, double *__restrict__ stg,
+                     KParams<C> p) {
+  constexpr int PX = C3_TX + 4, PY = C3_TY + 4, PZ = C3_TZ + 4;
+  constexpr int MX = C3_TX + 2, MY = C3_TY + 2, MZ = C3_TZ + 2;
+  __shared__ C sphi[PZ][PY][PX];
+  __shared__ C smu[MZ][MY][MX];
+  __shared__ C spn[TGEN ? MZ : 1][TGEN ? MY : 1][TGEN ? MX : 1];
+  const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
+  const long long Sz = (long long)Lx * Ly * Lz;
+  const int x0 = blockIdx.x * C3_TX, y0 = blockIdx.y * C3_TY, z0 = blockIdx.z * C3_TZ;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int k = tid; k < PX * PY * PZ; k += 256) {
+    const int rz = k / (PX * PY), rem = k - rz * PX * PY, ry = rem / PX, rx = rem - ry * PX;
+    const int gx = wrapi(x0 + rx - 2, Lx), gy = wrapi(y0 + ry - 2, Ly), gz = wrapi(z0 + rz - 2, Lz);
+    sphi[rz][ry][rx] = phi[((long long)gz * Ly + gy) * Lx + gx];
+  }
+  if constexpr (TGEN) {
+    for (int k = tid; k < MX * MY * MZ; k += 256) {
+      const int rz = k / (MX * MY), rem = k - rz * MX * MY, ry = rem / MX, rx = rem - ry * MX;
+      const int gx = wrapi(x0 + rx - 1, Lx), gy = wrapi(y0 + ry - 1, Ly),
+                gz = wrapi(z0 + rz - 1, Lz);
+      spn[rz][ry][rx] = p.cs2mT * (C(1) + dn[((long long)gz * Ly + gy) * Lx + gx]);
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < MX * MY * MZ; k += 256) {
+    const int mz = k / (MX * MY), rem = k - mz * MX * MY, my = rem / MX, mx = rem - my * MX;
+    const int cz = mz + 1, cy = my + 1, cx = mx + 1;
+    const C c = sphi[cz][cy][cx];
+    const C faces = ((sphi[cz][cy][cx - 1] + sphi[cz][cy][cx + 1]) +
+                     (sphi[cz][cy - 1][cx] + sphi[cz][cy + 1][cx])) +
+                    (sphi[cz - 1][cy][cx] + sphi[cz + 1][cy][cx]);
+    const C edges =
+        ((sphi[cz][cy - 1][cx - 1] + sphi[cz][cy - 1][cx + 1]) +
+         (sphi[cz][cy + 1][cx - 1] + sphi[cz][cy + 1][cx + 1])) +
+        ((sphi[cz - 1][cy][cx - 1] + sphi[cz - 1][cy][cx + 1]) +
+         (sphi[cz + 1][cy][cx - 1] + sphi[cz + 1][cy][cx + 1])) +
+        ((sphi[cz - 1][cy - 1][cx] + sphi[cz - 1][cy + 1][cx]) +
+         (sphi[cz + 1][cy - 1][cx] + sphi[cz + 1][cy + 1][cx]));
+    const C lap = p.Q * faces + p.R * edges + p.C0 * c;
+    smu[mz][my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
+  }
+  __syncthreads();
+
+  const int lx = threadIdx.x, ly = threadIdx.y, x = x0 + lx, y = y0 + ly;
+  if (x >= Lx || y >= Ly) return;
+  const int xm = x == 0 ? Lx - 1 : x - 1, xp = x == Lx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? Ly - 1 : y - 1, yp = y == Ly - 1 ? 0 : y + 1;
+#pragma unroll 1
+  for (int lz = 0; lz < C3_TZ; ++lz) {
+    const int z = z0 + lz;
+    if (z >= Lz) break;
+    const int zm = z == 0 ? Lz - 1 : z - 1, zp = z == Lz - 1 ? 0 : z + 1;
+    const int mx = lx + 1, my = ly + 1, mz = lz + 1;
+    // d_D mu along x, y, z
+    auto grad = [&](const C (*f)[MY][MX], C &gx_, C &gy_, C &gz_) {
+      gx_ = p.N * (f[mz][my][mx + 1] - f[mz][my][mx - 1]) +
+            p.M * (((f[mz][my - 1][mx + 1] - f[mz][my - 1][mx - 1]) +
+                    (f[mz][my + 1][mx + 1] - f[mz][my + 1][mx - 1])) +
+                   ((f[mz - 1][my][mx + 1] - f[mz - 1][my][mx - 1]) +
+                    (f[mz + 1][my][mx + 1] - f[mz + 1][my][mx - 1])));
+      gy_ = p.N * (f[mz][my + 1][mx] - f[mz][my - 1][mx]) +
+            p.M * (((f[mz][my + 1][mx - 1] - f[mz][my - 1][mx - 1]) +
+                    (f[mz][my + 1][mx + 1] - f[mz][my - 1][mx + 1])) +
+                   ((f[mz - 1][my + 1][mx] - f[mz - 1][my - 1][mx]) +
+                    (f[mz + 1][my + 1][mx] - f[mz + 1][my - 1][mx])));
+      gz_ = p.N * (f[mz + 1][my][mx] - f[mz - 1][my][mx]) +
+            p.M * (((f[mz + 1][my][mx - 1] - f[mz - 1][my][mx - 1]) +
+                    (f[mz + 1][my][mx + 1] - f[mz - 1][my][mx + 1])) +
+                   ((f[mz + 1][my - 1][mx] - f[mz - 1][my - 1][mx]) +
+                    (f[mz + 1][my + 1][mx] - f[mz - 1][my + 1][mx])));
+    };
+    C gmx, gmy, gmz;
+    grad(smu, gmx, gmy, gmz);
+    const C ph = sphi[lz + 2][ly + 2][lx + 2];
+    C Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
+    if constexpr (TGEN) {
+      C px, py, pz;
+      grad(spn, px, py, pz);
+      Fx += px;
+      Fy += py;
+      Fz += pz;
+    }
+    const long long pl = (long long)Lx * Ly;
+    const long long zc = (long long)z * pl, zmo = (long long)zm * pl, zpo = (long long)zp * pl;
+    const long long yc = (long long)y * Lx, ymo = (long long)ym * Lx, ypo = (long long)yp * Lx;
+    // f_i(r) = buf_i(r - e_i)
+    C hv[19];
+#define LD(i, zz, yy, xx) hv[i] = Store<S, C>::ld(hin + (i)*Sz + (zz) + (yy) + (xx), p.inv_scale)
+    LD(0, zc, yc, x);
+    LD(1, zc, yc, xm);
+    LD(2, zc, yc, xp);
+    LD(3, zc, ymo, x);
+    LD(4, zc, ypo, x);
+    LD(5, zmo, yc, x);
+    LD(6, zpo, yc, x);
+    LD(7, zc, ymo, xm);    // (1,1,0)
+    LD(8, zc, ypo, xp);    // (-1,-1,0)
+    LD(9, zc, ypo, xm);    // (1,-1,0)
+    LD(10, zc, ymo, xp);   // (-1,1,0)
+    LD(11, zmo, yc, xm);   // (1,0,1)
+    LD(12, zpo, yc, xp);   // (-1,0,-1)
+    LD(13, zpo, yc, xm);   // (1,0,-1)
+    LD(14, zmo, yc, xp);   // (-1,0,1)
+    LD(15, zmo, ymo, x);   // (0,1,1)
+    LD(16, zpo, ypo, x);   // (0,-1,-1)
+    LD(17, zpo, ymo, x);   // (0,1,-1)
+    LD(18, zmo, ypo, x);   // (0,-1,1)
+#undef LD
+    C dens = hv[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) dens += hv[i];
+    C jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      if (q19_ex(i) > 0) jx += hv[i];
+      if (q19_ex(i) < 0) jx -= hv[i];
+      if (q19_ey(i) > 0) jy += hv[i];
+      if (q19_ey(i) < 0) jy -= hv[i];
+      if (q19_ez(i) > 0) jz += hv[i];
+      if (q19_ez(i) < 0) jz -= hv[i];
+    }
+    const C n = C(1) + dens;
+    Fx += n * p.gx;
+    Fy += n * p.gy;
+    Fz += n * p.gz;
+    const C ux = (jx + C(0.5) * Fx) / n;
+    const C uy = (jy + C(0.5) * Fy) / n;
+    const C uz = (jz + C(0.5) * Fz) / n;
+    const long long s = zc + yc + x;
+    if constexpr (MODE == COLLIDE_MOMENTS) {
+      stg[s] = (double)n;
+      stg[Sz + s] = (double)ph;
+      stg[2 * Sz + s] = (double)ux;
+      stg[3 * Sz + s] = (double)uy;
+      stg[4 * Sz + s] = (double)uz;
+      continue;
+    }
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+      const int ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
+      const C w = C(q19_w(i));
+      const C eu = C(ex) * ux + C(ey) * uy + C(ez) * uz;
+      const C eF = C(ex) * Fx + C(ey) * Fy + C(ez) * Fz;
+      const C heq = w * (dens + n * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq));
+      const C Fi = p.pref * w * (C(3) * (eF - uF) + C(9) * eu * eF);
+      const C post = hv[i] - (hv[i] - heq) * p.tau_inv + Fi;
+      Store<S, C>::st(hout + i * Sz + s, post, p.scale);
+    }
+    uout[s] = ux;
+    uout[Sz + s] = uy;
+    uout[2 * Sz + s] = uz;
+  }
+}
+
+template <typename C, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256)
+    fd3d_kernel(const C *__restrict__ phi_in, const C *__restrict__ u, C *__restrict__ phi_out,
+                KParams<C> p, int sub) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *sm = reinterpret_cast<C *>(smem_raw);
+  const int H = 3 * sub, RX = TX + 2 * H, RY = TY + 2 * H, RZ = TZ + 2 * H;
+  const int R = RX * RY * RZ, PL = RX * RY;
+  C *sp = sm, *sh = sm + R, *sq = sm + 2 * R, *su = sm + 3 * R, *sv = sm + 4 * R,
+    *sw = sm + 5 * R;
+  const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
+  const long long Sz = (long long)Lx * Ly * Lz;
+  const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H, z0 = blockIdx.z * TZ - H;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rz = 0; rz < RZ; ++rz)
+    for (int ry = ty; ry < RY; ry += 8) {
+      const long long row = ((long long)wrapi(z0 + rz, Lz) * Ly + wrapi(y0 + ry, Ly)) * Lx;
+      for (int rx = tx; rx < RX; rx += 32) {
+        const long long g = row + wrapi(x0 + rx, Lx);
+        const int k = rz * PL + ry * RX + rx;
+        sp[k] = phi_in[g];
+        su[k] = u[g];
+        sv[k] = u[Sz + g];
+        sw[k] = u[2 * Sz + g];
+      }
+    }
+  __syncthreads();
+  const C dt = p.dt, dtG = p.dtG;
+#pragma unroll 1
+  for (int s = 1; s <= sub; ++s) {
+    int lo = 3 * s - 2;
+    for (int rz = lo; rz < RZ - lo; ++rz)
+      for (int ry = lo + ty; ry < RY - lo; ry += 8)
+        for (int rx = lo + tx; rx < RX - lo; rx += 32) {
+          const int k = rz * PL + ry * RX + rx;
+          const C ph = sp[k];
+          C tend;
+          if (p.adv_variant == LBM_ADV_PAPER) {
+            const C ua = su[k], va = sv[k], wa = sw[k];
+            const C dux = (su[k + 1] - su[k - 1]) / C(2);
+            const C dpx = ua < C(0) ? sp[k + 1] - ph : ph - sp[k - 1];
+            const C duy = (sv[k + RX] - sv[k - RX]) / C(2);
+            const C dpy = va < C(0) ? sp[k + RX] - ph : ph - sp[k - RX];
+            const C duz = (sw[k + PL] - sw[k - PL]) / C(2);
+            const C dpz = wa < C(0) ? sp[k + PL] - ph : ph - sp[k - PL];
+            tend = (ph * dux + ua * dpx);
+            tend += (ph * duy + va * dpy);
+            tend += (ph * duz + wa * dpz);
+          } else {
+            auto flux = [&](const C *uu, int st) {
+              const C Up = C(0.5) * (uu[k] + uu[k + st]);
+              const C Um = C(0.5) * (uu[k - st] + uu[k]);
+              const C Jp = Up > C(0) ? Up * ph : Up * sp[k + st];
+              const C Jm = Um > C(0) ? Um * sp[k - st] : Um * ph;
+              return Jp - Jm;
+            };
+            tend = flux(su, 1);
+            tend += flux(sv, RX);
+            tend += flux(sw, PL);
+          }
+          sh[k] = ph - dt * tend;
+        }
+    __syncthreads();
+    lo = 3 * s - 1;
+    for (int rz = lo; rz < RZ - lo; ++rz)
+      for (int ry = lo + ty; ry < RY - lo; ry += 8)
+        for (int rx = lo + tx; rx < RX - lo; rx += 32) {
+          const int k = rz * PL + ry * RX + rx;
+          const C hk = sh[k];
+          const C c = p.cubic_at_half ? hk : sp[k];
+          C lap = sh[k - PL];
+          lap += sh[k - RX];
+          lap += sh[k - 1];
+          lap += C(-6) * hk;
+          lap += sh[k + 1];
+          lap += sh[k + RX];
+          lap += sh[k + PL];
+          sq[k] = p.a * hk + p.b * (c * c * c) - p.kappa * lap;
+        }
+    __syncthreads();
+    lo = 3 * s;
+    for (int rz = lo; rz < RZ - lo; ++rz)
+      for (int ry = lo + ty; ry < RY - lo; ry += 8)
+        for (int rx = lo + tx; rx < RX - lo; rx += 32) {
+          const int k = rz * PL + ry * RX + rx;
+          C lap = sq[k - PL];
+          lap += sq[k - RX];
+          lap += sq[k - 1];
+          lap += C(-6) * sq[k];
+          lap += sq[k + 1];
+          lap += sq[k + RX];
+          lap += sq[k + PL];
+          sp[k] = sh[k] + dtG * lap;
+        }
+    __syncthreads();
+  }
+  for (int rz = H; rz < H + TZ; ++rz) {
+    const int gz = z0 + rz;
+    if (gz >= Lz) break;
+    for (int ry = H + ty; ry < H + TY; ry += 8) {
+      const int gy = y0 + ry;
+      if (gy >= Ly) break;
+      for (int rx = H + tx; rx < H + TX; rx += 32) {
+        const int gx = x0 + rx;
+        if (gx < Lx) phi_out[((long long)gz * Ly + gy) * Lx + gx] = sp[rz * PL + ry * RX + rx];
+      }
+    }
+  }
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(256)
+    density3d_kernel(const S *__restrict__ hin, C *__restrict__ dn, KParams<C> p) {
+  const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
+  const long long Sz = (long long)Lx * Ly * Lz;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  if (x >= Lx || y >= Ly) return;
+  C d = C(0);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const int sx = wrapi(x - q19_ex(i), Lx), sy = wrapi(y - q19_ey(i), Ly),
+              sz = wrapi(z - q19_ez(i), Lz);
+    d += Store<S, C>::ld(hin + i * Sz + ((long long)sz * Ly + sy) * Lx + sx, p.inv_scale);
+  }
+  dn[((long long)z * Ly + y) * Lx + x] = d;
+}
+
+template <typename S, typename C>
+cudaError_t collide3d(lbm_handle *h, int in, int force_on, int mode) {
+  KParams<C> p = make_params<C>(h, force_on);
+  dim3 grid((p.Lx + C3_TX - 1) / C3_TX, (p.Ly + C3_TY - 1) / C3_TY, (p.Lz + C3_TZ - 1) / C3_TZ);
+  dim3 block(32, C3_TY);
+  const S *hin = static_cast<const S *>(h->h[in]);
+  S *hout = static_cast<S *>(h->h[1 - in]);
+  const C *phi = static_cast<const C *>(h->phi[in]);
+  const C *dn = static_cast<const C *>(h->dn);
+  C *u = static_cast<C *>(h->u);
+  const bool tgen = p.cs2mT != C(0);
+  if (mode == COLLIDE_STEP) {
+    if (tgen)
+      collide3d_kernel<S, C, true, COLLIDE_STEP>
+          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+    else
+      collide3d_kernel<S, C, false, COLLIDE_STEP>
+          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+  } else {
+    if (tgen)
+      collide3d_kernel<S, C, true, COLLIDE_MOMENTS>
+          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+    else
+      collide3d_kernel<S, C, false, COLLIDE_MOMENTS>
+          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+  }
+  return cudaGetLastError();
+}
+
+template <typename C, int TX, int TY, int TZ>
+cudaError_t fd3d(lbm_handle *h, int in) {
+  KParams<C> p = make_params<C>(h, 0);
+  dim3 grid((p.Lx + TX - 1) / TX, (p.Ly + TY - 1) / TY, (p.Lz + TZ - 1) / TZ), block(32, 8);
+  const int launches = (h->m + h->sub - 1) / h->sub;
+  const C *u = static_cast<const C *>(h->u);
+  const C *src = static_cast<const C *>(h->phi[in]);
+  for (int j = 0; j < launches; ++j) {
+    const int sub = (j == launches - 1) ? h->m - h->sub * (launches - 1) : h->sub;
+    C *dst = static_cast<C *>(((launches - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
+    const int H = 3 * sub;
+    const size_t smem = sizeof(C) * 6 * (size_t)(TX + 2 * H) * (TY + 2 * H) * (TZ + 2 * H);
+    fd3d_kernel<C, TX, TY, TZ><<<grid, block, smem, h->stream>>>(src, u, dst, p, sub);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = dst;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// FD tiles: FP32 32 x 4 x 4, FP64 16 x 4 x 4 (one substep per launch: halo 3).
+constexpr int FD3_TX_F = 32, FD3_TX_D = 16, FD3_TY = 4, FD3_TZ = 4;
+
+size_t fd3d_smem_bytes(int precision, int sub) {
+  const int H = 3 * sub;
+  const int tx = precision == LBM_F64 ? FD3_TX_D : FD3_TX_F;
+  const size_t cb = precision == LBM_F64 ? 8 : 4;
+  return cb * 6 * (size_t)(tx + 2 * H) * (FD3_TY + 2 * H) * (FD3_TZ + 2 * H);
+}
+
+cudaError_t fd3d_configure(int precision, size_t smem) {
+  if (precision == LBM_F64)
+    return cudaFuncSetAttribute(fd3d_kernel<double, FD3_TX_D, FD3_TY, FD3_TZ>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(fd3d_kernel<float, FD3_TX_F, FD3_TY, FD3_TZ>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t collide3d_launch(lbm_handle *h, int in, int force_on, int mode) {
+  switch (h->P.precision) {
+    case LBM_F64: return collide3d<double, double>(h, in, force_on, mode);
+    case LBM_F32DEV: return collide3d<float, float>(h, in, force_on, mode);
+    default: return collide3d<__half, float>(h, in, force_on, mode);
+  }
+}
+
+cudaError_t fd3d_launch(lbm_handle *h, int in) {
+  if (h->P.precision == LBM_F64) return fd3d<double, FD3_TX_D, FD3_TY, FD3_TZ>(h, in);
+  return fd3d<float, FD3_TX_F, FD3_TY, FD3_TZ>(h, in);
+}
+
+cudaError_t density3d_launch(lbm_handle *h, int in) {
+  dim3 grid((h->P.Lx + 31) / 32, (h->P.Ly + 7) / 8, h->P.Lz), block(32, 8);
+  switch (h->P.precision) {
+    case LBM_F64: {
+      KParams<double> p = make_params<double>(h, 0);
+      density3d_kernel<double, double><<<grid, block, 0, h->stream>>>(
+          static_cast<const double *>(h->h[in]), static_cast<double *>(h->dn), p);
+      break;
+    }
+    case LBM_F32DEV: {
+      KParams<float> p = make_params<float>(h, 0);
+      density3d_kernel<float, float><<<grid, block, 0, h->stream>>>(
+          static_cast<const float *>(h->h[in]), static_cast<float *>(h->dn), p);
+      break;
+    }
+    default: {
+      KParams<float> p = make_params<float>(h, 0);
+      density3d_kernel<__half, float><<<grid, block, 0, h->stream>>>(
+          static_cast<const __half *>(h->h[in]), static_cast<float *>(h->dn), p);
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

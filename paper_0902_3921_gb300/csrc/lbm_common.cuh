@@ -1,0 +1,169 @@
+// lbm_common.cuh -- internal declarations shared by the translation units of
+// the sm_103a hybrid lattice Boltzmann library: lattice constants, storage
+// conversions, kernel parameter blocks, the handle and the kernel launchers.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hybrid_lbm.h"
+
+namespace hlbm {
+
+// ---- lattices (Sec. II A, Fig. 1; D3Q19 for 3D) --------------------------------
+// D2Q9 order: 0 rest; 1..4 = (1,0),(0,1),(-1,0),(0,-1); 5..8 = (1,1),(-1,1),(-1,-1),(1,-1).
+__host__ __device__ constexpr int q9_ex(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int q9_ey(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr double q9_w(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+// D3Q19 order: 0 rest; 1..6 faces (+x,-x,+y,-y,+z,-z); 7..18 edges
+// (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),
+// (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1).
+__host__ __device__ constexpr int q19_ex(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)
+             ? 1
+             : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+}
+__host__ __device__ constexpr int q19_ey(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17)
+             ? 1
+             : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+}
+__host__ __device__ constexpr int q19_ez(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18)
+             ? 1
+             : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+}
+__host__ __device__ constexpr double q19_w(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// ---- population storage ----------------------------------------------------------
+// Stored value = (f_i - w_i) * scale; scale is 1 except for FP16 storage.
+template <typename S, typename C>
+struct Store;
+template <>
+struct Store<double, double> {
+  static __device__ __forceinline__ double ld(const double *p, double) { return __ldg(p); }
+  static __device__ __forceinline__ void st(double *p, double v, double) { *p = v; }
+};
+template <>
+struct Store<float, float> {
+  static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+template <>
+struct Store<__half, float> {
+  static __device__ __forceinline__ float ld(const __half *p, float inv_scale) {
+    return __half2float(__ldg(p)) * inv_scale;
+  }
+  static __device__ __forceinline__ void st(__half *p, float v, float scale) {
+    *p = __float2half_rn(v * scale);
+  }
+};
+
+__device__ __forceinline__ int wrapi(int x, int L) {
+  x %= L;
+  return x < 0 ? x + L : x;
+}
+
+// ---- kernel parameter block (host computes it in FP64, kernels read type C) -------
+template <typename C>
+struct KParams {
+  int Lx, Ly, Lz;
+  C a, b, kappa;
+  C tau_inv, pref;          // 1/tau and 1 - 1/(2 tau) (Eq. 29)
+  C N, M, Q, R, C0;         // stencils (Eqs. 30-31); C0 = centre of lap_D
+  C gx, gy, gz;             // body force per unit density, 0 when off
+  C cs2mT;                  // cs^2 - T (Eq. 28), 0 on the fast path
+  C dt, dtG;                // FD step 1/m and Gamma/m (Sec. II C)
+  C scale, inv_scale;       // FP16 storage scale 2^s and its inverse (1 otherwise)
+  int adv_variant, cubic_at_half;
+};
+
+// ---- handle -------------------------------------------------------------------
+struct GraphEntry {
+  long long nsteps;
+  int parity;
+  int force_on;
+  cudaGraphExec_t exec;
+};
+
+struct EventPair {
+  cudaEvent_t a, b;
+  int family;
+};
+
+}  // namespace hlbm
+
+struct lbm_handle {
+  lbm_params P;
+  int dims = 2, q = 9, m = 1, sub = 1;  // sub = FD substeps fused per launch
+  long long S = 0, t = 0;
+  bool inited = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int cur = 0;  // which of the two population/phi buffers holds time t
+  void *h[2] = {nullptr, nullptr};
+  void *phi[3] = {nullptr, nullptr, nullptr};  // [2] = FD scratch between launches
+  void *u = nullptr;
+  void *dn = nullptr;
+  double *staging = nullptr;   // (dims + 3) * S doubles
+  double *partials = nullptr;  // diagnostics block partials
+  double *dres = nullptr;      // diagnostics result
+  double r_ref[3] = {0, 0, 0};
+  double phi0 = 1.0;
+  size_t hbytes = 0, phibytes = 0;
+  int err = 0;
+  std::string msg;
+  bool use_graphs = true;
+  std::vector<hlbm::GraphEntry> graphs;
+  bool timing = false;
+  std::vector<hlbm::EventPair> events;
+  double ms_acc[3] = {0, 0, 0};
+  long long launches_acc[3] = {0, 0, 0};
+};
+
+namespace hlbm {
+
+// Launchers (return cudaError_t of the launch).  `in`/`out` index the
+// population and phi double buffers; force_on selects the body force.
+// collide: h[in], phi[in] -> h[1-in], u (STEP) or n, phi, u* as FP64 in staging (MOMENTS)
+cudaError_t launch_collide(lbm_handle *h, int in, int force_on, int mode);
+// FD update (Sec. II C): phi[in], u -> phi[1-in] (phi[2] between launches)
+cudaError_t launch_fd(lbm_handle *h, int in);
+// density n - 1 of h[in] into h->dn (only needed when T != 1/3)
+cudaError_t launch_density(lbm_handle *h, int in);
+// initial state from staging (n, phi, u as FP64) into h[out], phi[out]
+cudaError_t launch_init(lbm_handle *h, int out);
+// f_i(r, t) of direction i from h[in] into staging[0 .. S) as FP64
+cudaError_t launch_population(lbm_handle *h, int in, int i);
+// FP64 diagnostics from the MOMENTS staging into h->dres (DIAG_* layout)
+cudaError_t launch_diag(lbm_handle *h, const double *r_ref);
+
+// layout of the diagnostics result vector
+enum {
+  DIAG_SUM_N = 0, DIAG_SUM_PHI, DIAG_MOM0, DIAG_MOM1, DIAG_MOM2, DIAG_UMAX, DIAG_AREA,
+  DIAG_CMW, DIAG_CM0, DIAG_CM1, DIAG_CM2, DIAG_NONFINITE, DIAG_NPART,
+  // written by the finishing kernel after the partial sums
+  DIAG_DP = DIAG_NPART, DIAG_RCM0, DIAG_RCM1, DIAG_RCM2, DIAG_VF0, DIAG_VF1, DIAG_VF2,
+  DIAG_COUNT
+};
+constexpr int DIAG_BLOCKS = 1024;
+
+// mode of launch_collide
+enum { COLLIDE_STEP = 0, COLLIDE_MOMENTS = 1 };
+
+template <typename C>
+KParams<C> make_params(const lbm_handle *h, int force_on);
+
+}  // namespace hlbm

@@ -1,0 +1,104 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol
+declared in include/hybrid_lbm.h; parameter validation runs before any CUDA
+call, so invalid parameters give LBM_EINVAL with a message even without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_0902_3921_gb300 import build as B
+from paper_0902_3921_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return lbm.load_library()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(lbm_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared_functions()
+    assert "lbm_create" in declared and "lbm_step" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(lbm.EXPORTS) <= declared
+
+
+def test_struct_layouts_match_header():
+    # the ctypes mirrors must match the C structs field for field
+    src = open(os.path.join(ROOT, "include", "hybrid_lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    for name, mirror in (("lbm_params", lbm.c_lbm_params), ("lbm_diag", lbm.c_lbm_diag)):
+        seg = [s for s in src.split("typedef struct {") if ("} " + name + ";") in s][0]
+        body = seg.split("} " + name + ";")[0]
+        fields = re.findall(r"(\w+)(?:\[\d\])?\s*[;,]", body)
+        assert [f for f, _ in mirror._fields_] == fields, name
+        assert ctypes.sizeof(mirror) % 8 == 0
+
+
+def test_lattice_tables(lib):
+    import numpy as np
+    for dims, q in ((2, 9), (3, 19)):
+        e, w = lbm.lbm_lattice(dims)
+        assert e.shape == (q, 3)
+        assert abs(w.sum() - 1) < 1e-15
+        np.testing.assert_allclose(w @ e, 0, atol=1e-16)
+    assert lib.lbm_lattice(4, None, None) == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("change,needle", [
+    (dict(tau=0.5), "tau"),
+    (dict(b=0.0), "b must"),
+    (dict(kappa=-1.0), "kappa"),
+    (dict(Gamma=-1.0), "Gamma"),
+    (dict(Lx=2), ">= 3"),
+    (dict(dims=4), "dims"),
+    (dict(precision=7), "precision"),
+    (dict(adv_variant=3), "adv_variant"),
+    (dict(fd_substeps=1), "Euler bound"),
+    (dict(N=float("nan")), "finite"),
+    (dict(T=0.0), "T > 0"),
+    (dict(force_steps=-1), "force_steps"),
+    (dict(f16_scale_log2=20), "f16_scale_log2"),
+])
+def test_invalid_parameters_are_rejected(lib, change, needle):
+    p = lbm.LbmParams(**change)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(p)
+    assert ei.value.code == lbm.LBM_EINVAL
+    assert needle in str(ei.value)
+
+
+def test_null_handle_calls_are_safe(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_synchronize(None) == lbm.LBM_EINVAL
+    assert lib.lbm_time(None) == -1
+    lib.lbm_free(None)
+    assert lib.lbm_create(None, None, None) == lbm.LBM_EINVAL
+
+
+def test_fd_substep_rule():
+    """Sec. II C: dt_LB = m dt_FD.  The default m is the smallest with the
+    diffusive stiffness Gamma (a_eff lam + kappa lam^2) * dt <= 1.5; an
+    explicit m below the Euler bound (<= 2) is refused unless forced (m < 0).
+    Checked on the host-side arithmetic through the error text."""
+    # the drop configuration: stiffness 5.28 in 2D -> m_min = 3
+    with pytest.raises(lbm.LbmError, match="m >= 3"):
+        lbm.lbm_create(lbm.LbmParams(fd_substeps=2))
+    with pytest.raises(lbm.LbmError, match="m >= 6"):
+        lbm.lbm_create(lbm.LbmParams(dims=3, Lz=8, fd_substeps=5))

@@ -1,0 +1,345 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances (written here, derived in the design notes):
+  * FP64 mode: |d phi|, |d f| <= 1e-11 and |d u*| <= 1e-12 (FMA contraction and
+    summation order are the only differences from the oracle);
+  * FP32-deviation mode, drop configuration (64^2, R = 16, 2000 steps):
+    |d phi|_inf <= 1e-5 and |d u*|_inf <= 1e-3 max|u*_oracle|;
+  * FP16-deviation mode: error reported, bounded loosely.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0902_3921_gb300 import inputs as I
+from paper_0902_3921_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+CFG1 = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_0902_3921_gb300 import build as B
+    B.build()
+    lbm.load_library()
+
+
+def _pair(Lx, Ly, Lz=1, dims=2, m=4, precision=lbm.LBM_F64, **kw):
+    """Matching oracle / library parameters."""
+    op = O.Params(dims=dims, Lx=Lx, Ly=Ly, Lz=Lz if dims == 3 else 1, m=m, **kw)
+    lp = lbm.LbmParams(dims=dims, Lx=Lx, Ly=Ly, Lz=Lz if dims == 3 else 1, fd_substeps=-m,
+                       precision=precision, **kw)
+    return op, lp
+
+
+def _run_both(op, lp, n, phi, u, steps, chunks=None, graphs=True):
+    ref = O.State.create(op, n, phi, u)
+    ref.run(steps)
+    lat = lbm.Lattice(lp)
+    lbm.lbm_set_graphs(lat.handle, graphs)
+    lat.init_fields(n, phi, u)
+    for c in (chunks or [steps]):
+        lat.step(c)
+    return ref, lat
+
+
+def _errors(ref, lat):
+    rn, ru = ref.moments()
+    gn, gphi, gu = lat.moments()
+    return (float(np.max(np.abs(gphi - ref.phi))), float(np.max(np.abs(gu - ru))),
+            float(np.max(np.abs(gn - rn))))
+
+
+@pytest.fixture(scope="module")
+def drop_2000():
+    """The FP64 drop configuration: 64^2, R = 16, 2000 steps, oracle side."""
+    op = O.Params(Lx=64, Ly=64, m=4, **CFG1)
+    phi = I.drop(2, 64, 64, R=16, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 64, 64)
+    ref = O.State.create(op, n, phi, u)
+    ref.run(2000)
+    return op, (n, phi, u), ref
+
+
+def test_drop_config_fp64(drop_2000):
+    op, (n, phi, u), ref = drop_2000
+    lat = lbm.Lattice(lbm.LbmParams(Lx=64, Ly=64, fd_substeps=4, precision=lbm.LBM_F64, **CFG1))
+    lat.init_fields(n, phi, u).step(2000)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (dphi, du, dn)
+    f = lat.populations()
+    assert np.max(np.abs(f - ref.f)) <= 1e-11
+    # FP64 diagnostics against the oracle's
+    dg = lat.diagnostics()
+    do = O.diagnostics(op, ref.f, ref.phi, ref.t, np.array([32.0, 32.0, 0.0]))
+    for k in ("sum_n", "sum_phi", "u_max", "dp", "area", "R_eff"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-10, abs=1e-12), k
+    np.testing.assert_allclose(dg["r_cm"], do["r_cm"], atol=1e-9)
+    np.testing.assert_allclose(dg["v_f"], do["v_f"], atol=1e-12)
+    np.testing.assert_allclose(dg["momentum"], do["momentum"], atol=1e-12)
+    assert dg["nonfinite"] == 0
+
+
+def test_drop_config_fp32_deviation(drop_2000):
+    """The stated bar: after 2000 steps |d phi|_inf <= 1e-5 and
+    |d u*|_inf <= 1e-3 max |u*_oracle|."""
+    op, (n, phi, u), ref = drop_2000
+    _, ru = ref.moments()
+    lat = lbm.Lattice(lbm.LbmParams(Lx=64, Ly=64, fd_substeps=4, precision=lbm.LBM_F32DEV,
+                                    **CFG1))
+    lat.init_fields(n, phi, u).step(2000)
+    dphi, du, dn = _errors(ref, lat)
+    umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+    print(f"fp32dev drop 2000: |dphi|={dphi:.3e} |du|={du:.3e} umax={umax:.3e} |dn|={dn:.3e}")
+    assert dphi <= 1e-5, dphi
+    assert du <= 1e-3 * umax, (du, umax)
+
+
+def test_drop_config_fp16_deviation(drop_2000):
+    """FP16 deviations (scale 2^10): the error is stated, bounded loosely."""
+    op, (n, phi, u), ref = drop_2000
+    _, ru = ref.moments()
+    lat = lbm.Lattice(lbm.LbmParams(Lx=64, Ly=64, fd_substeps=4, precision=lbm.LBM_F16DEV,
+                                    **CFG1))
+    lat.init_fields(n, phi, u).step(2000)
+    dphi, du, dn = _errors(ref, lat)
+    umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+    print(f"fp16dev drop 2000: |dphi|={dphi:.3e} |du|={du:.3e} umax={umax:.3e} |dn|={dn:.3e}")
+    assert dphi <= 1e-2 and du <= 0.1 * umax
+
+
+@pytest.mark.parametrize("Lx,Ly", [(37, 23), (3, 3), (5, 70), (96, 33), (130, 17)])
+def test_ragged_sizes_fp64(Lx, Ly):
+    """Sizes that are not multiples of any tile, down to 3 x 3."""
+    op, lp = _pair(Lx, Ly, **CFG1)
+    rng = np.random.default_rng(Lx * 100 + Ly)
+    phi = 0.8 * (rng.random((Ly, Lx)) - 0.5)
+    n = 1 + 0.01 * (rng.random((Ly, Lx)) - 0.5)
+    u = 0.01 * (rng.random((2, Ly, Lx)) - 0.5)
+    ref, lat = _run_both(op, lp, n, phi, u, 30)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (dphi, du, dn)
+    assert np.max(np.abs(lat.populations() - ref.f)) <= 1e-11
+
+
+@pytest.mark.parametrize("variant", ["flux", "cubic_half", "T", "force", "m1", "m5", "SC",
+                                     "tau", "m9"])
+def test_variants_fp64(variant):
+    kw = dict(CFG1)
+    m = 4
+    steps, chunks = 40, None
+    if variant == "flux":
+        kw["adv_variant"] = 1
+    elif variant == "cubic_half":
+        kw["cubic_at_half"] = 1
+    elif variant == "T":
+        kw["T"] = 0.28
+    elif variant == "force":
+        kw["g"] = (2e-5, -1e-5, 0.0)
+        kw["force_steps"] = 25
+        chunks = [7, 30, 3]  # the force switches off inside a call
+    elif variant == "m1":
+        kw.update(a=-1e-3, b=1e-3, kappa=3e-3, Gamma=5.0)
+        m = 1
+    elif variant == "m5":
+        m = 5  # two FD launches (4 + 1 substeps) per step
+    elif variant == "m9":
+        m = 9  # three FD launches (4 + 4 + 1)
+    elif variant == "SC":
+        kw.update(N=0.5, Q=1.0)
+    elif variant == "tau":
+        kw["tau"] = 0.7
+    op, lp = _pair(48, 40, m=m, **kw)
+    phi = I.drop(2, 48, 40, R=10, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 48, 40)
+    u = u + 0.002 * np.sin(np.arange(48) / 5.0)[None, None, :]
+    ref, lat = _run_both(op, lp, n, phi, u, steps, chunks=chunks)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (variant, dphi, du, dn)
+
+
+def test_graphs_match_eager_bitwise():
+    op, lp = _pair(64, 48, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.spinodal(2, 64, 48, seed=3)
+    n, u = I.rest(2, 64, 48)
+    outs = []
+    for graphs in (True, False):
+        lat = lbm.Lattice(lp)
+        lbm.lbm_set_graphs(lat.handle, graphs)
+        lat.init_fields(n, phi, u)
+        for c in (1, 64, 65, 3, 130):
+            lat.step(c)
+        outs.append(lat.moments())
+        lat.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_translation_equivariance_bitwise():
+    op, lp = _pair(64, 48, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.spinodal(2, 64, 48, seed=5)
+    n, u = I.rest(2, 64, 48)
+    res = []
+    for shift in ((0, 0), (7, 13)):
+        lat = lbm.Lattice(lp)
+        lat.init_fields(n, np.roll(phi, shift, axis=(0, 1)), u).step(100)
+        res.append(lat.moments())
+        lat.close()
+    for a, b in zip(res[0], res[1]):
+        axes = (0, 1) if a.ndim == 2 else (1, 2)
+        assert np.array_equal(np.roll(a, (7, 13), axis=axes), b)
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_F64, lbm.LBM_F32DEV])
+def test_rest_state_gpu(precision):
+    op, lp = _pair(40, 24, precision=precision, **CFG1)
+    n, u = I.rest(2, 40, 24)
+    phi = np.ones((24, 40))
+    lat = lbm.Lattice(lp)
+    lat.init_fields(n, phi, u).step(50)
+    gn, gphi, gu = lat.moments()
+    assert np.array_equal(gphi, phi)
+    assert np.max(np.abs(gu)) < 1e-15
+    assert np.max(np.abs(gn - 1)) < 1e-12
+
+
+def test_spinodal_full_size_fp32():
+    """The 1024 x 1024 spinodal workload in the benchmark's launch
+    configuration: 5 steps against the oracle at every site."""
+    op, lp = _pair(1024, 1024, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.spinodal(2, 1024, 1024, seed=0)
+    n, u = I.rest(2, 1024, 1024)
+    ref, lat = _run_both(op, lp, n, phi, u, 5)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-6 and du <= 1e-8 and dn <= 1e-6, (dphi, du, dn)
+
+
+def test_sum_n_conserved_fp32_long():
+    """Mass conservation over 2000 steps of the spinodal workload (any size)."""
+    op, lp = _pair(256, 256, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.spinodal(2, 256, 256, seed=1)
+    n, u = I.rest(2, 256, 256)
+    lat = lbm.Lattice(lp)
+    lat.init_fields(n, phi, u)
+    d0 = lat.diagnostics()
+    lat.step(2000)
+    d1 = lat.diagnostics()
+    assert abs(d1["sum_n"] - d0["sum_n"]) < 1e-6 * 65536
+    assert d1["nonfinite"] == 0
+
+
+def test_flux_variant_conserves_phi_fp64():
+    op, lp = _pair(64, 64, adv_variant=1, **CFG1)
+    phi = I.spinodal(2, 64, 64, seed=2, amp=0.1)
+    n, u = I.rest(2, 64, 64)
+    lat = lbm.Lattice(lp)
+    lat.init_fields(n, phi, u)
+    s0 = lat.diagnostics()["sum_phi"]
+    lat.step(300)
+    s1 = lat.diagnostics()["sum_phi"]
+    assert abs(s1 - s0) < 1e-10
+
+
+# ---- 3D (D3Q19) ------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(12, 10, 8), (5, 3, 7)])
+def test_3d_fp64_parity(shape):
+    Lx, Ly, Lz = shape
+    kw = dict(CFG1, N=1 / 6, Q=1 / 3)
+    op, lp = _pair(Lx, Ly, Lz, dims=3, m=8, **kw)
+    rng = np.random.default_rng(11)
+    phi = 0.8 * (rng.random((Lz, Ly, Lx)) - 0.5)
+    n = 1 + 0.01 * (rng.random((Lz, Ly, Lx)) - 0.5)
+    u = 0.01 * (rng.random((3, Lz, Ly, Lx)) - 0.5)
+    ref, lat = _run_both(op, lp, n, phi, u, 12)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (dphi, du, dn)
+    assert np.max(np.abs(lat.populations() - ref.f)) <= 1e-11
+
+
+@pytest.mark.parametrize("variant", ["T", "force", "flux"])
+def test_3d_variants_fp64(variant):
+    kw = dict(CFG1, N=1 / 6, Q=1 / 3)
+    if variant == "T":
+        kw["T"] = 0.3
+    elif variant == "force":
+        kw.update(g=(1e-5, 2e-5, -3e-5), force_steps=4)
+    else:
+        kw["adv_variant"] = 1
+    op, lp = _pair(20, 18, 16, dims=3, m=8, **kw)
+    phi = I.drop(3, 20, 18, 16, R=5, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(3, 20, 18, 16)
+    ref, lat = _run_both(op, lp, n, phi, u, 8)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (variant, dphi, du, dn)
+
+
+def test_3d_drop_64_fp32_and_fp16():
+    """The 64^3 copy of the 3D drop (R = 12): FP32 and FP16 deviations against
+    FP64 after 20 steps; the errors are printed (stated per result)."""
+    kw = dict(CFG1, N=1 / 6, Q=1 / 3)
+    op = O.Params(dims=3, Lx=64, Ly=64, Lz=64, m=8, **kw)
+    phi = I.drop(3, 64, 64, 64, R=12, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(3, 64, 64, 64)
+    ref = O.State.create(op, n, phi, u)
+    ref.run(20)
+    _, ru = ref.moments()
+    umax = float(np.max(np.abs(ru)))
+    for prec, bphi, bu in ((lbm.LBM_F32DEV, 1e-5, 1e-3), (lbm.LBM_F16DEV, 1e-2, 0.2)):
+        lat = lbm.Lattice(lbm.LbmParams(dims=3, Lx=64, Ly=64, Lz=64, fd_substeps=8,
+                                        precision=prec, **kw))
+        lat.init_fields(n, phi, u).step(20)
+        dphi, du, dn = _errors(ref, lat)
+        print(f"3D 64^3 drop, precision {prec}: |dphi|={dphi:.3e} |du|={du:.3e} "
+              f"umax={umax:.3e}")
+        assert dphi <= bphi and du <= bu * umax
+        lat.close()
+
+
+def test_checkpoint_roundtrip_bitwise(tmp_path):
+    op, lp = _pair(48, 40, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.spinodal(2, 48, 40, seed=9)
+    n, u = I.rest(2, 48, 40)
+    a = lbm.Lattice(lp)
+    a.init_fields(n, phi, u).step(100)
+    path = str(tmp_path / "ck.bin")
+    lbm.lbm_save(a.handle, path)
+    a.step(100)
+    b = lbm.Lattice(lp)
+    assert lbm.lbm_load(b.handle, path) == lbm.LBM_OK
+    assert b.t == 100
+    b.step(100)
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x, y)
+    # a corrupted file is refused and leaves the handle usable
+    raw = bytearray(open(path, "rb").read())
+    raw[-5] ^= 0xFF
+    open(path, "wb").write(bytes(raw))
+    assert lbm.lbm_load(b.handle, path) == lbm.LBM_EINVAL
+    b.step(1)
+
+
+def test_errors_are_latched_not_fatal():
+    lp = lbm.LbmParams(Lx=16, Ly=16, precision=lbm.LBM_F32DEV, **CFG1)
+    lat = lbm.Lattice(lp)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(1)  # before init
+    assert ei.value.code == lbm.LBM_ESTATE
+    # the handle refuses further work and still frees cleanly
+    with pytest.raises(lbm.LbmError):
+        lat.init_fields(np.ones((16, 16)), np.zeros((16, 16)), np.zeros((2, 16, 16)))
+    lat.close()
+
+
+def test_nonfinite_is_reported():
+    lp = lbm.LbmParams(Lx=16, Ly=16, precision=lbm.LBM_F32DEV, **CFG1)
+    lat = lbm.Lattice(lp)
+    phi = np.zeros((16, 16))
+    phi[3, 4] = np.nan
+    lat.init_fields(np.ones((16, 16)), phi, np.zeros((2, 16, 16)))
+    d = lat.diagnostics()
+    assert d["nonfinite"] == 1 and d["rc"] == lbm.LBM_ENONFINITE
+    lat.step(1)  # still usable
