@@ -27,7 +27,6 @@ __global__ void __launch_bounds__(256)
   constexpr int MX = C3_TX + 2, MY = C3_TY + 2, MZ = C3_TZ + 2;
   __shared__ C sphi[PZ][PY][PX];
   __shared__ C smu[MZ][MY][MX];
-  __shared__ C spn[TGEN ? MZ : 1][TGEN ? MY : 1][TGEN ? MX : 1];
   const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
   const long long Sz = (long long)Lx * Ly * Lz;
   const int x0 = blockIdx.x * C3_TX, y0 = blockIdx.y * C3_TY, z0 = blockIdx.z * C3_TZ;
@@ -36,14 +35,6 @@ __global__ void __launch_bounds__(256)
     const int rz = k / (PX * PY), rem = k - rz * PX * PY, ry = rem / PX, rx = rem - ry * PX;
     const int gx = wrapi(x0 + rx - 2, Lx), gy = wrapi(y0 + ry - 2, Ly), gz = wrapi(z0 + rz - 2, Lz);
     sphi[rz][ry][rx] = phi[((long long)gz * Ly + gy) * Lx + gx];
-  }
-  if constexpr (TGEN) {
-    for (int k = tid; k < MX * MY * MZ; k += 256) {
-      const int rz = k / (MX * MY), rem = k - rz * MX * MY, ry = rem / MX, rx = rem - ry * MX;
-      const int gx = wrapi(x0 + rx - 1, Lx), gy = wrapi(y0 + ry - 1, Ly),
-                gz = wrapi(z0 + rz - 1, Lz);
-      spn[rz][ry][rx] = p.cs2mT * (C(1) + dn[((long long)gz * Ly + gy) * Lx + gx]);
-    }
   }
   __syncthreads();
   for (int k = tid; k < MX * MY * MZ; k += 256) {
@@ -98,11 +89,21 @@ __global__ void __launch_bounds__(256)
     const C ph = sphi[lz + 2][ly + 2][lx + 2];
     C Fx = -ph * gmx, Fy = -ph * gmy, Fz = -ph * gmz;
     if constexpr (TGEN) {
-      C px, py, pz;
-      grad(spn, px, py, pz);
-      Fx += px;
-      Fy += py;
-      Fz += pz;
+      // d_D((cs2 - T) n) from the density pass, read directly (rare path)
+      auto pn = [&](int dx, int dy, int dz) {
+        const long long g = ((long long)wrapi(z + dz, Lz) * Ly + wrapi(y + dy, Ly)) * Lx +
+                            wrapi(x + dx, Lx);
+        return p.cs2mT * (C(1) + dn[g]);
+      };
+      Fx += p.N * (pn(1, 0, 0) - pn(-1, 0, 0)) +
+            p.M * (((pn(1, -1, 0) - pn(-1, -1, 0)) + (pn(1, 1, 0) - pn(-1, 1, 0))) +
+                   ((pn(1, 0, -1) - pn(-1, 0, -1)) + (pn(1, 0, 1) - pn(-1, 0, 1))));
+      Fy += p.N * (pn(0, 1, 0) - pn(0, -1, 0)) +
+            p.M * (((pn(-1, 1, 0) - pn(-1, -1, 0)) + (pn(1, 1, 0) - pn(1, -1, 0))) +
+                   ((pn(0, 1, -1) - pn(0, -1, -1)) + (pn(0, 1, 1) - pn(0, -1, 1))));
+      Fz += p.N * (pn(0, 0, 1) - pn(0, 0, -1)) +
+            p.M * (((pn(-1, 0, 1) - pn(-1, 0, -1)) + (pn(1, 0, 1) - pn(1, 0, -1))) +
+                   ((pn(0, -1, 1) - pn(0, -1, -1)) + (pn(0, 1, 1) - pn(0, 1, -1))));
     }
     const long long pl = (long long)Lx * Ly;
     const long long zc = (long long)z * pl, zmo = (long long)zm * pl, zpo = (long long)zp * pl;

@@ -384,9 +384,10 @@ int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out) {
     cudaError_t e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc"));
   }
-  cudaError_t e = h->dims == 2
-                      ? fd2d_configure(P.precision, fd2d_smem_bytes(P.precision, h->sub))
-                      : fd3d_configure(P.precision, fd3d_smem_bytes(P.precision, h->sub));
+  // opt in to the largest FD tile any handle may launch (the attribute is
+  // per kernel, shared by all handles of the process)
+  cudaError_t e = h->dims == 2 ? fd2d_configure(P.precision, fd2d_smem_bytes(P.precision, 4))
+                               : fd3d_configure(P.precision, fd3d_smem_bytes(P.precision, 1));
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "FD shared-memory configuration"));
   *out = h;
   return LBM_OK;
