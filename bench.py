@@ -115,10 +115,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(seed):
+def make_inputs(seed, side=None):
     from paper_0902_3921_gb300 import inputs as I
-    phi = I.spinodal(2, L, L, seed=seed)
-    n, u = I.rest(2, L, L)
+    side = side or L
+    phi = I.spinodal(2, side, side, seed=seed)
+    n, u = I.rest(2, side, side)
     return n, phi, u
 
 
@@ -179,10 +180,13 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     lib = lbm.load_library()
     stream = torch.cuda.Stream()
-    params = lbm.LbmParams(Lx=L, Ly=L, fd_substeps=M_SUB, precision=lbm.LBM_F32DEV, **CFG)
+    side = args.lattice
+    params = lbm.LbmParams(Lx=side, Ly=side, fd_substeps=M_SUB, precision=lbm.LBM_F32DEV,
+                           **CFG)
     S = params.S
-    n, phi, u = make_inputs(seed=rank)
+    n, phi, u = make_inputs(seed=rank, side=side)
     lat = lbm.Lattice(params, stream=stream.cuda_stream)
+    lbm.lbm_set_graphs(lat.handle, not args.no_graphs)
     lat.init_fields(n, phi, u)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     fd_launches = (M_SUB + 3) // 4
@@ -216,6 +220,13 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
     ms_max = float(t_local.item())
     value = world * S * LB_PER_STEP * args.steps / (ms_max / 1000.0) / 1e6
+    if args.quick:
+        # profiling runs: the timed region only
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS",
+                              "lattice": side, "quick": True}), flush=True)
+        lat.close()
+        return
 
     # kernel timing region: the same steps, each kernel bracketed by events
     lbm.lbm_set_kernel_timing(lat.handle, True)
@@ -270,7 +281,8 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": [L, L], "lb_steps_per_timed_step":
+            "config": {"workload": WORKLOAD if side == L else f"spinodal-{side}x{side}-d2q9-f32dev",
+                       "lattice": [side, side], "lb_steps_per_timed_step":
                        LB_PER_STEP, "fd_substeps": M_SUB, "precision": "f32 deviations",
                        "params": CFG, "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
@@ -301,6 +313,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", type=int, default=L,
+                    help="lattice side (the workload is 1024; other sides are for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region only (no kernel timing, e2e or CPU baseline)")
+    ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
