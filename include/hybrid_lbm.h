@@ -161,6 +161,41 @@ int lbm_kernel_times(lbm_handle *h, double *ms, long long *launches, int reset);
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
 
+/* Allocation-free diagnostics.  The paper has no counterpart to this entry
+ * point: it exists for callers that cannot allocate device memory, such as a
+ * host framework that owns all device memory through its own allocator and
+ * budget, or a time-critical loop in which cudaMalloc/cudaFree would
+ * synchronise the device.  It computes the same FP64 observables as
+ * lbm_diagnostics, with the same kernels, from fields the caller passes in,
+ * and allocates nothing: its scratch (per-block partial sums and the result
+ * vector, LBM_NOALLOC_MAX_BLOCKS * 12 + 19 doubles, about 192 KiB) is a
+ * static device array that every GPU using the library holds until the
+ * process exits.
+ *
+ *   params  geometry and the a, b, kappa, T, N, Q used by p0; other fields
+ *           are ignored.  At most LBM_NOALLOC_MAX_SITES sites: larger
+ *           lattices return LBM_EINVAL ("exceed the ... capacity").
+ *   fields  DEVICE pointer to (2 + dims) * S doubles, [n | phi | u*_x | u*_y
+ *           (| u*_z)], each block row-major [z][y][x] (what lbm_moments
+ *           returns, laid end to end).  Read only.
+ *   r_ref   host array of 3 doubles: the reference point of the periodic
+ *           centre-of-mass unwrap (lbm_diagnostics uses the previous r_cm),
+ *           or NULL for the box centre.
+ *   cuda_stream  the stream to run on (NULL: the legacy default stream).
+ *   out     host struct, filled on return (out->t = -1).
+ * Waits for the stream.  Returns LBM_OK, LBM_ENONFINITE (out filled),
+ * LBM_EINVAL or LBM_ECUDA; lbm_noalloc_last_error() describes the failure.
+ * The first call on each device looks up the device address of the scratch
+ * array with that device current; make that first call before any stream
+ * capture.  All calls share the one array and leave the last call's values
+ * in it (each call writes every entry it reads, so nothing is cleared):
+ * calls that overlap on the GPU (other streams, other host threads) race. */
+#define LBM_NOALLOC_MAX_BLOCKS 2048
+#define LBM_NOALLOC_MAX_SITES (LBM_NOALLOC_MAX_BLOCKS * 2048)
+int lbm_diagnostics_noalloc(const lbm_params *params, const double *fields,
+                            const double *r_ref, void *cuda_stream, lbm_diag *out);
+const char *lbm_noalloc_last_error(void);
+
 /* Frees the handle and its device memory (and its stream if it owns one).
  * NULL-safe.  Does not free a caller-provided stream. */
 void lbm_free(lbm_handle *h);

@@ -391,3 +391,41 @@ cudaError_t launch_diag(lbm_handle *h, const double *r_ref) {
 }
 
 }  // namespace hlbm
+
+namespace hlbm {
+
+// The diagnostics kernels on caller-provided FP64 fields ([n | phi | u_x |
+// u_y (| u_z)], S doubles each) with caller-provided partials/result storage
+// and an explicit number of partial blocks.
+cudaError_t launch_diag_raw(const lbm_params &P, double phi0, const double *r_ref,
+                            const double *fields, double *partials, int nblocks, double *res,
+                            cudaStream_t stream) {
+  Geo g;
+  g.dims = P.dims;
+  g.Lx = P.Lx;
+  g.Ly = P.Ly;
+  g.Lz = P.dims == 3 ? P.Lz : 1;
+  g.S = (long long)g.Lx * g.Ly * g.Lz;
+  Stencil st;
+  st.N = P.N;
+  st.Q = P.Q;
+  if (P.dims == 2) {
+    st.M = (1.0 - 2.0 * P.N) / 4.0;
+    st.R = (1.0 - P.Q) / 2.0;
+    st.C0 = -4.0 * (st.Q + st.R);
+  } else {
+    st.M = (1.0 - 2.0 * P.N) / 8.0;
+    st.R = (1.0 - P.Q) / 4.0;
+    st.C0 = -(6.0 * st.Q + 12.0 * st.R);
+  }
+  diag_partial_kernel<<<nblocks, DIAG_THREADS, 0, stream>>>(g, phi0, r_ref[0], r_ref[1],
+                                                            r_ref[2], fields, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_finish_kernel<<<1, DIAG_THREADS, 0, stream>>>(g, st, P.a, P.b, P.kappa, P.T, r_ref[0],
+                                                     r_ref[1], r_ref[2], nblocks, partials,
+                                                     fields, res);
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

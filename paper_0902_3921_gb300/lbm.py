@@ -29,7 +29,8 @@ PRECISIONS = {"f64": LBM_F64, "f32dev": LBM_F32DEV, "f16dev": LBM_F16DEV}
 EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_populations",
            "lbm_lattice", "lbm_diagnostics", "lbm_synchronize", "lbm_time", "lbm_fd_substeps",
            "lbm_set_graphs", "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_save",
-           "lbm_load", "lbm_free", "lbm_last_error")
+           "lbm_load", "lbm_free", "lbm_last_error", "lbm_diagnostics_noalloc",
+           "lbm_noalloc_last_error")
 
 
 class c_lbm_params(ctypes.Structure):
@@ -92,6 +93,11 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_free.restype = None
     lib.lbm_last_error.argtypes = [H]
     lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_diagnostics_noalloc.argtypes = [ctypes.POINTER(c_lbm_params), vp, dp, vp,
+                                            ctypes.POINTER(c_lbm_diag)]
+    lib.lbm_diagnostics_noalloc.restype = ctypes.c_int
+    lib.lbm_noalloc_last_error.argtypes = []
+    lib.lbm_noalloc_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_populations",
                  "lbm_lattice", "lbm_diagnostics", "lbm_synchronize", "lbm_fd_substeps",
                  "lbm_set_graphs", "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_save",
@@ -224,6 +230,29 @@ def lbm_diagnostics(h, dims: int = 2):
             "momentum": list(d.momentum)[:dims], "u_max": d.u_max, "dp": d.dp,
             "r_cm": list(d.r_cm)[:dims], "v_f": list(d.v_f)[:dims], "area": d.area,
             "R_eff": d.R_eff, "nonfinite": d.nonfinite, "rc": rc}
+
+
+def lbm_diagnostics_noalloc(params: LbmParams, fields_device_ptr: int, r_ref=None,
+                            cuda_stream: int | None = None):
+    """Allocation-free diagnostics of caller-owned device fields
+    [n | phi | u*_x | u*_y (| u*_z)] (FP64); see include/hybrid_lbm.h.
+    Returns (rc, dict)."""
+    lib = load_library()
+    d = c_lbm_diag()
+    cp = params.to_c()
+    rr = None
+    if r_ref is not None:
+        rr_arr = (ctypes.c_double * 3)(*[float(x) for x in (list(r_ref) + [0.0] * 3)[:3]])
+        rr = ctypes.cast(rr_arr, ctypes.POINTER(ctypes.c_double))
+    rc = lib.lbm_diagnostics_noalloc(ctypes.byref(cp), ctypes.c_void_p(fields_device_ptr), rr,
+                                     ctypes.c_void_p(cuda_stream or 0), ctypes.byref(d))
+    if rc not in (LBM_OK, LBM_ENONFINITE):
+        raise LbmError(rc, lib.lbm_noalloc_last_error().decode())
+    dims = params.dims
+    return rc, {"sum_n": d.sum_n, "sum_phi": d.sum_phi, "momentum": list(d.momentum)[:dims],
+                "u_max": d.u_max, "dp": d.dp, "r_cm": list(d.r_cm)[:dims],
+                "v_f": list(d.v_f)[:dims], "area": d.area, "R_eff": d.R_eff,
+                "nonfinite": d.nonfinite}
 
 
 def lbm_synchronize(h):
