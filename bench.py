@@ -220,11 +220,12 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
     ms_max = float(t_local.item())
     value = world * S * LB_PER_STEP * args.steps / (ms_max / 1000.0) / 1e6
+    tuning = lbm.lbm_tuning(lat.handle)
     if args.quick:
         # profiling runs: the timed region only
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS",
-                              "lattice": side, "quick": True}), flush=True)
+                              "lattice": side, "quick": True, "tuning": tuning}), flush=True)
         lat.close()
         return
 
@@ -285,6 +286,7 @@ def run_ours(args, rank, world, local):
                        "lattice": [side, side], "lb_steps_per_timed_step":
                        LB_PER_STEP, "fd_substeps": M_SUB, "precision": "f32 deviations",
                        "params": CFG, "l2": "flushed (256 MiB write) between timed steps",
+                       "tuning": tuning,
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,

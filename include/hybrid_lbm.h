@@ -141,6 +141,17 @@ int lbm_diagnostics(lbm_handle *h, lbm_diag *out);
 int lbm_synchronize(lbm_handle *h);
 
 long long lbm_time(const lbm_handle *h);       /* current LB step t, or -1     */
+
+/* The launch shapes picked by the autotuner of lbm_create (2D; it times the
+ * candidates with CUDA events on the handle's own buffers): writes up to n of
+ * {FD substeps per launch, FD output rows per warp, FD columns per lane,
+ * collide sites per thread (0: asynchronous shared-memory staging), m, FD
+ * kernel (0: warp-marching; 32 or 64: shared-memory tile of that width)} into
+ * values and returns 6 (EINVAL on NULL).
+ * Environment: HLBM_TUNING="sub,rows,cols,collide_rows[,tile]" fixes the shapes
+ * instead of timing them (reproducible profiling); HLBM_TUNE_VERBOSE=1 prints
+ * every candidate's time to stderr. */
+int lbm_tuning(const lbm_handle *h, int *values, int n);
 int lbm_fd_substeps(const lbm_handle *h);      /* the m in use, or -1          */
 
 /* 1 (default) captures lbm_step into CUDA graphs; 0 launches kernels one by

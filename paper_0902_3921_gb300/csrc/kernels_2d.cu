@@ -5,7 +5,8 @@
 //               -> pull-streamed populations -> n, u* (Eqs. 12, 18) -> BGK with
 //               the Guo forcing term (Eqs. 15, 17, 29) -> populations and u*.
 //   fd2d      : `sub` substeps of the convection-diffusion update (Eqs. 32-36)
-//               temporally blocked in shared memory (halo 3 per substep).
+//               per launch, pipelined over rows by marching warps (halo 3 per
+//               substep), with the launch shape chosen by the runtime's autotuner.
 //   density2d : n - 1 of every site (only for T != 1/3, whose extra force
 //               needs n on the neighbours).
 //
@@ -13,6 +14,8 @@
 // streamed with the "pull" pattern: the buffer of time t holds the
 // post-collision values of step t-1 at their source site, so
 // f_i(r, t) = buf_i(r - e_i) and the kernel writes its own site only.
+#include <type_traits>
+
 #include "lbm_common.cuh"
 
 namespace hlbm {
@@ -20,14 +23,17 @@ namespace hlbm {
 namespace {
 
 constexpr int C2_TX = 32;  // tile width (one warp along x)
-constexpr int C2_TY = 16;  // tile height (block of 32 x 8 threads, 2 rows each)
-constexpr int C2_BY = 8;
+constexpr int C2_BY = 8;   // block of 32 x 8 threads, RY rows each (tile height 8 RY)
 
-template <typename S, typename C, bool TGEN, int MODE>
-__global__ void __launch_bounds__(256)
+// Wraps x in [-L, 2L) into [0, L).
+__device__ __forceinline__ int wrap1(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
+
+template <typename S, typename C, bool TGEN, int MODE, int RY>
+__global__ void __launch_bounds__(256, 2)
     collide2d_kernel(const S *__restrict__ hin, S *__restrict__ hout, const C *__restrict__ phi,
                      const C *__restrict__ dn, C *__restrict__ uout, double *__restrict__ stg,
                      KParams<C> p) {
+  constexpr int C2_TY = C2_BY * RY;              // tile height
   constexpr int PX = C2_TX + 4, PY = C2_TY + 4;  // phi tile + halo 2
   constexpr int MX = C2_TX + 2, MY = C2_TY + 2;  // mu tile + halo 1
   __shared__ C sphi[PY][PX];
@@ -36,12 +42,46 @@ __global__ void __launch_bounds__(256)
   const int Lx = p.Lx, Ly = p.Ly;
   const long long Sz = (long long)Lx * Ly;
   const int x0 = blockIdx.x * C2_TX, y0 = blockIdx.y * C2_TY;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int tx = threadIdx.x, tid = threadIdx.y * 32 + threadIdx.x;
 
-  for (int k = tid; k < PX * PY; k += 256) {
-    const int ry = k / PX, rx = k - ry * PX;
-    const int gx = wrapi(x0 + rx - 2, Lx), gy = wrapi(y0 + ry - 2, Ly);
-    sphi[ry][rx] = phi[(long long)gy * Lx + gx];
+  // 1. issue the pull loads f_i(r, t) = buf_i(r - e_i) of this thread's sites
+  //    first, so that they are in flight during the stencil phase
+  const int x = x0 + tx;
+  const bool xin = x < Lx;
+  const int xc = xin ? x : Lx - 1;
+  const int xm = xc == 0 ? Lx - 1 : xc - 1, xp = xc == Lx - 1 ? 0 : xc + 1;
+  C hv[RY][9];
+  long long site[RY];
+  bool ok[RY];
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const int y = y0 + threadIdx.y + C2_BY * r;
+    ok[r] = xin && y < Ly;
+    const int yc = y < Ly ? y : Ly - 1;
+    const long long rowc = (long long)yc * Lx;
+    const long long rowm = (long long)(yc == 0 ? Ly - 1 : yc - 1) * Lx;
+    const long long rowp = (long long)(yc == Ly - 1 ? 0 : yc + 1) * Lx;
+    site[r] = rowc + xc;
+    hv[r][0] = Store<S, C>::ld(hin + 0 * Sz + rowc + xc, p.inv_scale);
+    hv[r][1] = Store<S, C>::ld(hin + 1 * Sz + rowc + xm, p.inv_scale);
+    hv[r][2] = Store<S, C>::ld(hin + 2 * Sz + rowm + xc, p.inv_scale);
+    hv[r][3] = Store<S, C>::ld(hin + 3 * Sz + rowc + xp, p.inv_scale);
+    hv[r][4] = Store<S, C>::ld(hin + 4 * Sz + rowp + xc, p.inv_scale);
+    hv[r][5] = Store<S, C>::ld(hin + 5 * Sz + rowm + xm, p.inv_scale);
+    hv[r][6] = Store<S, C>::ld(hin + 6 * Sz + rowm + xp, p.inv_scale);
+    hv[r][7] = Store<S, C>::ld(hin + 7 * Sz + rowp + xp, p.inv_scale);
+    hv[r][8] = Store<S, C>::ld(hin + 8 * Sz + rowp + xm, p.inv_scale);
+  }
+
+  // 2. phi on the tile + halo 2 (periodic) and mu on the tile + 1
+  const bool big = Lx >= PX && Ly >= PY;  // one conditional wrap suffices
+  for (int ry = threadIdx.y; ry < PY; ry += C2_BY) {
+    const int gy = big ? wrap1(y0 + ry - 2, Ly) : wrapi(y0 + ry - 2, Ly);
+    const C *prow = phi + (long long)gy * Lx;
+    for (int rx = tx; rx < PX; rx += 32) {
+      const int gx = big ? wrap1(x0 + rx - 2, Lx) : wrapi(x0 + rx - 2, Lx);
+      sphi[ry][rx] = prow[gx];
+    }
   }
   if constexpr (TGEN) {
     for (int k = tid; k < MX * MY; k += 256) {
@@ -51,30 +91,211 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
-  // mu = a phi + b phi^3 - kappa lap_D phi on the tile + 1 (Eqs. 5, 31)
-  for (int k = tid; k < MX * MY; k += 256) {
-    const int my = k / MX, mx = k - my * MX;
-    const int cy = my + 1, cx = mx + 1;
-    const C c = sphi[cy][cx];
-    C lap = p.R * sphi[cy - 1][cx - 1];
-    lap += p.Q * sphi[cy - 1][cx];
-    lap += p.R * sphi[cy - 1][cx + 1];
-    lap += p.Q * sphi[cy][cx - 1];
-    lap += p.C0 * c;
-    lap += p.Q * sphi[cy][cx + 1];
-    lap += p.R * sphi[cy + 1][cx - 1];
-    lap += p.Q * sphi[cy + 1][cx];
-    lap += p.R * sphi[cy + 1][cx + 1];
-    smu[my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
-  }
+  // mu = a phi + b phi^3 - kappa lap_D phi (Eqs. 5, 31)
+  for (int my = threadIdx.y; my < MY; my += C2_BY)
+    for (int mx = tx; mx < MX; mx += 32) {
+      const int cy = my + 1, cx = mx + 1;
+      const C c = sphi[cy][cx];
+      C lap = p.R * sphi[cy - 1][cx - 1];
+      lap += p.Q * sphi[cy - 1][cx];
+      lap += p.R * sphi[cy - 1][cx + 1];
+      lap += p.Q * sphi[cy][cx - 1];
+      lap += p.C0 * c;
+      lap += p.Q * sphi[cy][cx + 1];
+      lap += p.R * sphi[cy + 1][cx - 1];
+      lap += p.Q * sphi[cy + 1][cx];
+      lap += p.R * sphi[cy + 1][cx + 1];
+      smu[my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
+    }
   __syncthreads();
 
-#pragma unroll 1
-  for (int r = 0; r < C2_TY / C2_BY; ++r) {
-    const int lx = threadIdx.x, ly = threadIdx.y + C2_BY * r;
-    const int x = x0 + lx, y = y0 + ly;
-    if (x >= Lx || y >= Ly) continue;
+  // 3. force, moments, collision and the writes of each site
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    if (!ok[r]) continue;
+    const int lx = tx, ly = threadIdx.y + C2_BY * r;
+    const int mx = lx + 1, my = ly + 1;
     // F = -phi d_D mu (Eqs. 28, 30)
+    C gmx = -p.M * smu[my - 1][mx - 1];
+    gmx += p.M * smu[my - 1][mx + 1];
+    gmx += -p.N * smu[my][mx - 1];
+    gmx += p.N * smu[my][mx + 1];
+    gmx += -p.M * smu[my + 1][mx - 1];
+    gmx += p.M * smu[my + 1][mx + 1];
+    C gmy = -p.M * smu[my - 1][mx - 1];
+    gmy += -p.N * smu[my - 1][mx];
+    gmy += -p.M * smu[my - 1][mx + 1];
+    gmy += p.M * smu[my + 1][mx - 1];
+    gmy += p.N * smu[my + 1][mx];
+    gmy += p.M * smu[my + 1][mx + 1];
+    const C ph = sphi[ly + 2][lx + 2];
+    C Fx = -ph * gmx, Fy = -ph * gmy;
+    if constexpr (TGEN) {
+      C px = -p.M * spn[my - 1][mx - 1];
+      px += p.M * spn[my - 1][mx + 1];
+      px += -p.N * spn[my][mx - 1];
+      px += p.N * spn[my][mx + 1];
+      px += -p.M * spn[my + 1][mx - 1];
+      px += p.M * spn[my + 1][mx + 1];
+      C py = -p.M * spn[my - 1][mx - 1];
+      py += -p.N * spn[my - 1][mx];
+      py += -p.M * spn[my - 1][mx + 1];
+      py += p.M * spn[my + 1][mx - 1];
+      py += p.N * spn[my + 1][mx];
+      py += p.M * spn[my + 1][mx + 1];
+      Fx += px;
+      Fy += py;
+    }
+    const C *h = hv[r];
+    // n - 1 and the momentum of the deviations (sum w_i e_i = 0)
+    C dens = h[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) dens += h[i];
+    const C jx = ((h[1] - h[3]) + (h[5] - h[7])) + (h[8] - h[6]);
+    const C jy = ((h[2] - h[4]) + (h[5] - h[7])) + (h[6] - h[8]);
+    const C n = C(1) + dens;
+    Fx += n * p.gx;
+    Fy += n * p.gy;
+    // u* (Eq. 18)
+    const C ux = (jx + C(0.5) * Fx) / n;
+    const C uy = (jy + C(0.5) * Fy) / n;
+    const long long s = site[r];
+    if constexpr (MODE == COLLIDE_MOMENTS) {
+      stg[s] = (double)n;
+      stg[Sz + s] = (double)ph;
+      stg[2 * Sz + s] = (double)ux;
+      stg[3 * Sz + s] = (double)uy;
+      continue;
+    }
+    const C usq = ux * ux + uy * uy;
+    const C uF = ux * Fx + uy * Fy;
+    const C om = p.tau_inv, keep = C(1) - p.tau_inv;
+    // rest population: feq_0 - w_0 (Eq. 15) and F_0 (Eq. 29)
+    {
+      const C w = C(q9_w(0));
+      const C heq = w * (dens - n * (C(1.5) * usq));
+      const C Fi = p.pref * w * (C(-3) * uF);
+      Store<S, C>::st(hout + s, keep * h[0] + om * heq + Fi, p.scale);
+    }
+    // opposite pairs (i, ibar) share the even parts of feq and F_i and have
+    // odd parts of opposite sign
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = k < 2 ? k + 1 : k + 3, ib = i + 2;  // (1,3) (2,4) (5,7) (6,8)
+      const C w = C(q9_w(i));
+      const C eu = C(q9_ex(i)) * ux + C(q9_ey(i)) * uy;
+      const C eF = C(q9_ex(i)) * Fx + C(q9_ey(i)) * Fy;
+      const C even = w * (dens + n * (C(4.5) * eu * eu - C(1.5) * usq));
+      const C odd = w * (n * (C(3) * eu));
+      const C Feven = p.pref * w * (C(9) * eu * eF - C(3) * uF);
+      const C Fodd = p.pref * w * (C(3) * eF);
+      Store<S, C>::st(hout + i * Sz + s, keep * h[i] + om * (even + odd) + (Feven + Fodd),
+                      p.scale);
+      Store<S, C>::st(hout + ib * Sz + s, keep * h[ib] + om * (even - odd) + (Feven - Fodd),
+                      p.scale);
+    }
+    uout[s] = ux;
+    uout[Sz + s] = uy;
+  }
+}
+
+// ---- collide with asynchronous staging (FP32 / FP64 populations) ----------------
+// The same arithmetic as collide2d_kernel, but every pulled population and the
+// phi tile are copied global -> shared with cp.async, so that the whole tile
+// (9 planes of 32 x 32 sites) is in flight at once without holding registers;
+// 4 CTAs per SM keep about 150 KB of loads outstanding per SM.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gsrc), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+constexpr int CA_TX = 32, CA_TY = 32, CA_RY = CA_TY / C2_BY;
+
+template <typename C>
+constexpr size_t collide_async_smem() {
+  return sizeof(C) * (9 * CA_TX * CA_TY + (CA_TX + 4) * (CA_TY + 4) + 2 * (CA_TX + 2) * (CA_TY + 2));
+}
+
+template <typename C, bool TGEN, int MODE>
+__global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
+    collide2d_async_kernel(const C *__restrict__ hin, C *__restrict__ hout,
+                           const C *__restrict__ phi, const C *__restrict__ dn,
+                           C *__restrict__ uout, double *__restrict__ stg, KParams<C> p) {
+  constexpr int PX = CA_TX + 4, PY = CA_TY + 4, MX = CA_TX + 2, MY = CA_TY + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C(*pops)[CA_TY][CA_TX] = reinterpret_cast<C(*)[CA_TY][CA_TX]>(smem_raw);
+  C(*sphi)[PX] = reinterpret_cast<C(*)[PX]>(smem_raw + sizeof(C) * 9 * CA_TX * CA_TY);
+  C(*smu)[MX] = reinterpret_cast<C(*)[MX]>(smem_raw + sizeof(C) * (9 * CA_TX * CA_TY + PX * PY));
+  C(*spn)[MX] = smu + MY;
+  const int Lx = p.Lx, Ly = p.Ly;
+  const long long Sz = (long long)Lx * Ly;
+  const int x0 = blockIdx.x * CA_TX, y0 = blockIdx.y * CA_TY;
+  const int tx = threadIdx.x, tid = threadIdx.y * 32 + threadIdx.x;
+  const int x = x0 + tx;
+  const int xm = x == 0 ? Lx - 1 : x - 1, xp = x >= Lx - 1 ? 0 : x + 1;
+  // 1. every pulled population f_i(r, t) = buf_i(r - e_i) of the tile
+#pragma unroll
+  for (int r = 0; r < CA_RY; ++r) {
+    const int ly = threadIdx.y + C2_BY * r, y = y0 + ly;
+    if (x >= Lx || y >= Ly) continue;
+    const long long rowc = (long long)y * Lx;
+    const long long rowm = (long long)(y == 0 ? Ly - 1 : y - 1) * Lx;
+    const long long rowp = (long long)(y == Ly - 1 ? 0 : y + 1) * Lx;
+    cp_async<sizeof(C)>(&pops[0][ly][tx], hin + 0 * Sz + rowc + x);
+    cp_async<sizeof(C)>(&pops[1][ly][tx], hin + 1 * Sz + rowc + xm);
+    cp_async<sizeof(C)>(&pops[2][ly][tx], hin + 2 * Sz + rowm + x);
+    cp_async<sizeof(C)>(&pops[3][ly][tx], hin + 3 * Sz + rowc + xp);
+    cp_async<sizeof(C)>(&pops[4][ly][tx], hin + 4 * Sz + rowp + x);
+    cp_async<sizeof(C)>(&pops[5][ly][tx], hin + 5 * Sz + rowm + xm);
+    cp_async<sizeof(C)>(&pops[6][ly][tx], hin + 6 * Sz + rowm + xp);
+    cp_async<sizeof(C)>(&pops[7][ly][tx], hin + 7 * Sz + rowp + xp);
+    cp_async<sizeof(C)>(&pops[8][ly][tx], hin + 8 * Sz + rowp + xm);
+  }
+  // 2. phi on the tile + halo 2 (periodic)
+  const bool big = Lx >= PX && Ly >= PY;
+  for (int ry = threadIdx.y; ry < PY; ry += C2_BY) {
+    const int gy = big ? wrap1(y0 + ry - 2, Ly) : wrapi(y0 + ry - 2, Ly);
+    const C *prow = phi + (long long)gy * Lx;
+    for (int rx = tx; rx < PX; rx += 32) {
+      const int gx = big ? wrap1(x0 + rx - 2, Lx) : wrapi(x0 + rx - 2, Lx);
+      cp_async<sizeof(C)>(&sphi[ry][rx], prow + gx);
+    }
+  }
+  if constexpr (TGEN) {
+    for (int k = tid; k < MX * MY; k += 256) {
+      const int ry = k / MX, rx = k - ry * MX;
+      const int gx = wrapi(x0 + rx - 1, Lx), gy = wrapi(y0 + ry - 1, Ly);
+      spn[ry][rx] = p.cs2mT * (C(1) + dn[(long long)gy * Lx + gx]);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // mu = a phi + b phi^3 - kappa lap_D phi (Eqs. 5, 31)
+  for (int my = threadIdx.y; my < MY; my += C2_BY)
+    for (int mx = tx; mx < MX; mx += 32) {
+      const int cy = my + 1, cx = mx + 1;
+      const C c = sphi[cy][cx];
+      C lap = p.R * sphi[cy - 1][cx - 1];
+      lap += p.Q * sphi[cy - 1][cx];
+      lap += p.R * sphi[cy - 1][cx + 1];
+      lap += p.Q * sphi[cy][cx - 1];
+      lap += p.C0 * c;
+      lap += p.Q * sphi[cy][cx + 1];
+      lap += p.R * sphi[cy + 1][cx - 1];
+      lap += p.Q * sphi[cy + 1][cx];
+      lap += p.R * sphi[cy + 1][cx + 1];
+      smu[my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
+    }
+  __syncthreads();
+#pragma unroll 1
+  for (int r = 0; r < CA_RY; ++r) {
+    const int lx = tx, ly = threadIdx.y + C2_BY * r, y = y0 + ly;
+    if (x >= Lx || y >= Ly) continue;
     const int mx = lx + 1, my = ly + 1;
     C gmx = -p.M * smu[my - 1][mx - 1];
     gmx += p.M * smu[my - 1][mx + 1];
@@ -106,34 +327,20 @@ __global__ void __launch_bounds__(256)
       Fx += px;
       Fy += py;
     }
-    // pull the populations f_i(r, t) = buf_i(r - e_i)
-    const int xm = x == 0 ? Lx - 1 : x - 1, xp = x == Lx - 1 ? 0 : x + 1;
-    const long long rowc = (long long)y * Lx;
-    const long long rowm = (long long)(y == 0 ? Ly - 1 : y - 1) * Lx;
-    const long long rowp = (long long)(y == Ly - 1 ? 0 : y + 1) * Lx;
-    C hv[9];
-    hv[0] = Store<S, C>::ld(hin + 0 * Sz + rowc + x, p.inv_scale);
-    hv[1] = Store<S, C>::ld(hin + 1 * Sz + rowc + xm, p.inv_scale);
-    hv[2] = Store<S, C>::ld(hin + 2 * Sz + rowm + x, p.inv_scale);
-    hv[3] = Store<S, C>::ld(hin + 3 * Sz + rowc + xp, p.inv_scale);
-    hv[4] = Store<S, C>::ld(hin + 4 * Sz + rowp + x, p.inv_scale);
-    hv[5] = Store<S, C>::ld(hin + 5 * Sz + rowm + xm, p.inv_scale);
-    hv[6] = Store<S, C>::ld(hin + 6 * Sz + rowm + xp, p.inv_scale);
-    hv[7] = Store<S, C>::ld(hin + 7 * Sz + rowp + xp, p.inv_scale);
-    hv[8] = Store<S, C>::ld(hin + 8 * Sz + rowp + xm, p.inv_scale);
-    // n - 1 and the momentum of the deviations (sum w_i e_i = 0)
-    C dens = hv[0];
+    C h[9];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) dens += hv[i];
-    const C jx = ((hv[1] - hv[3]) + (hv[5] - hv[7])) + (hv[8] - hv[6]);
-    const C jy = ((hv[2] - hv[4]) + (hv[5] - hv[7])) + (hv[6] - hv[8]);
+    for (int i = 0; i < 9; ++i) h[i] = pops[i][ly][lx];
+    C dens = h[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) dens += h[i];
+    const C jx = ((h[1] - h[3]) + (h[5] - h[7])) + (h[8] - h[6]);
+    const C jy = ((h[2] - h[4]) + (h[5] - h[7])) + (h[6] - h[8]);
     const C n = C(1) + dens;
     Fx += n * p.gx;
     Fy += n * p.gy;
-    // u* (Eq. 18)
     const C ux = (jx + C(0.5) * Fx) / n;
     const C uy = (jy + C(0.5) * Fy) / n;
-    const long long s = rowc + x;
+    const long long s = (long long)y * Lx + x;
     if constexpr (MODE == COLLIDE_MOMENTS) {
       stg[s] = (double)n;
       stg[Sz + s] = (double)ph;
@@ -143,122 +350,394 @@ __global__ void __launch_bounds__(256)
     }
     const C usq = ux * ux + uy * uy;
     const C uF = ux * Fx + uy * Fy;
+    const C om = p.tau_inv, keep = C(1) - p.tau_inv;
+    {
+      const C w = C(q9_w(0));
+      const C heq = w * (dens - n * (C(1.5) * usq));
+      const C Fi = p.pref * w * (C(-3) * uF);
+      hout[s] = keep * h[0] + om * heq + Fi;
+    }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      constexpr C three = C(3), four5 = C(4.5), one5 = C(1.5), nine = C(9);
-      const int ex = q9_ex(i), ey = q9_ey(i);
+    for (int k = 0; k < 4; ++k) {
+      const int i = k < 2 ? k + 1 : k + 3, ib = i + 2;  // (1,3) (2,4) (5,7) (6,8)
       const C w = C(q9_w(i));
-      const C eu = C(ex) * ux + C(ey) * uy;
-      const C eF = C(ex) * Fx + C(ey) * Fy;
-      // feq_i - w_i (Eq. 15) and the forcing term (Eq. 29)
-      const C heq = w * (dens + n * (three * eu + four5 * eu * eu - one5 * usq));
-      const C Fi = p.pref * w * (three * (eF - uF) + nine * eu * eF);
-      const C post = hv[i] - (hv[i] - heq) * p.tau_inv + Fi;
-      Store<S, C>::st(hout + i * Sz + s, post, p.scale);
+      const C eu = C(q9_ex(i)) * ux + C(q9_ey(i)) * uy;
+      const C eF = C(q9_ex(i)) * Fx + C(q9_ey(i)) * Fy;
+      const C even = w * (dens + n * (C(4.5) * eu * eu - C(1.5) * usq));
+      const C odd = w * (n * (C(3) * eu));
+      const C Feven = p.pref * w * (C(9) * eu * eF - C(3) * uF);
+      const C Fodd = p.pref * w * (C(3) * eF);
+      hout[i * Sz + s] = keep * h[i] + om * (even + odd) + (Feven + Fodd);
+      hout[ib * Sz + s] = keep * h[ib] + om * (even - odd) + (Feven - Fodd);
     }
     uout[s] = ux;
     uout[Sz + s] = uy;
   }
 }
 
-// ---- FD convection-diffusion, temporally blocked ---------------------------------
-// Tile TX x TY, `sub` substeps; each substep shrinks the valid region by 3:
-// advection needs phi, u at radius 1, psi = a phih + b phi^3 - kappa lap phih at
-// radius 1 of the output, and the output adds dt Gamma lap psi.  This is Eq. 36
-// with the three Laplacians regrouped into lap(a phih + b phi^3 - kappa lap phih)
-// (the operator is linear, so the two forms differ by rounding only).
-template <typename C, int TX, int TY>
+// ---- FD convection-diffusion: warp-marching temporal blocking -------------------
+// One warp owns a strip of W = 32 V columns (V consecutive columns per lane)
+// and marches down a tile of TY output rows, running SUB substeps of Eqs.
+// 32-36 as a software pipeline over rows.  When row r of phi is loaded:
+//   substep s advects row r - 1 - 3s, forms psi = a phih + b phi^3 -
+//   kappa lap phih on row r - 2 - 3s and the new phi on row r - 3 - 3s,
+// so every value lives in a 3-row register ring and the x neighbours come
+// from the adjacent lane by warp shuffles.  Each substep loses one column
+// (row) of validity per stencil, i.e. 3 per substep: the strip outputs its
+// middle OW = W - 2 HX columns and the tile reads 3 SUB extra rows on both
+// sides.  Eq. 36's three Laplacians are regrouped as
+// lap(a phih + b phi^3 - kappa lap phih) (the operator is linear).
+// The advection terms of a row (d_x u and d_y v of Eq. 33, u and v, or the
+// face velocities of the flux form) are computed once per launch and kept in
+// a per-lane shared-memory ring until the last substep has used them.
+template <typename C, int V>
+struct VecT;
+template <>
+struct VecT<float, 4> {
+  using T = float4;
+};
+template <>
+struct VecT<float, 2> {
+  using T = float2;
+};
+template <>
+struct VecT<double, 2> {
+  using T = double2;
+};
+
+template <typename C, int V>
+__device__ __forceinline__ void load_row(const C *__restrict__ row, const int (&gx)[V],
+                                         bool vec, C (&out)[V]) {
+  if (vec) {
+    using T = typename VecT<C, V>::T;
+    const T t = __ldg(reinterpret_cast<const T *>(row + gx[0]));
+    const C *tc = reinterpret_cast<const C *>(&t);
+#pragma unroll
+    for (int j = 0; j < V; ++j) out[j] = tc[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) out[j] = __ldg(row + gx[j]);
+  }
+}
+
+template <typename C, int V, int SUB>
+__global__ void __launch_bounds__(64)
+    fd2d_march_kernel(const C *__restrict__ phi_in, const C *__restrict__ u,
+                      C *__restrict__ phi_out, KParams<C> p, int TY, int nstrips, int ntiles) {
+  constexpr int H = 3 * SUB;                    // rows of halo per side
+  constexpr int HX = (H + V - 1) / V * V;       // columns of halo, a multiple of V
+  constexpr int W = 32 * V, OW = W - 2 * HX;    // strip width and output width
+  constexpr int RD = 3 * SUB - 2;               // rows of advection terms kept
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ __align__(16) C terms[2][RD][4][W];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * 2 + warp;
+  if (wid >= nstrips * ntiles) return;  // whole warp: no block barriers are used
+  const int sx = wid % nstrips, tyi = wid / nstrips;
+  const int Lx = p.Lx, Ly = p.Ly;
+  const long long Sz = (long long)Lx * Ly;
+  const int xs = sx * OW - HX;  // global column of local column 0
+  const int y0 = tyi * TY;
+  const int NR = TY + 2 * H;
+  int gx[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) gx[j] = wrapi(xs + V * lane + j, Lx);
+  const bool vec = (Lx % V) == 0;  // then a lane's V columns are contiguous and aligned
+  C (*T)[4][W] = terms[warp];
+
+  C ph[SUB][3][V], A[SUB][3][V], P[SUB][3][V], vr[3][V], ur[V];
+#pragma unroll
+  for (int s = 0; s < SUB; ++s)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < V; ++j) ph[s][k][j] = A[s][k][j] = P[s][k][j] = C(0);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    ur[j] = C(0);
+    vr[0][j] = vr[1][j] = vr[2][j] = C(0);
+  }
+  const C dt = p.dt, dtG = p.dtG, a = p.a, b = p.b, kappa = p.kappa;
+  const bool paper = p.adv_variant == LBM_ADV_PAPER, cubic_half = p.cubic_at_half != 0;
+  int tw = RD - 1;  // terms slot of row r - 1
+  int gy = wrapi(y0 - H, Ly);  // global row of the next load
+
+  auto row = [&](auto R3c, int r) {
+    constexpr int R3 = decltype(R3c)::value;
+    constexpr int S0 = R3, S1 = (R3 + 1) % 3, S2 = (R3 + 2) % 3;
+    // slots: row r -> S0, r - 1 -> S2, r - 2 -> S1 (rows are stored at row % 3)
+    const long long grow = (long long)gy * Lx;
+    gy = gy + 1 == Ly ? 0 : gy + 1;
+    C un[V];
+    load_row<C, V>(phi_in + grow, gx, vec, ph[0][S0]);
+    load_row<C, V>(u + grow, gx, vec, un);
+    load_row<C, V>(u + Sz + grow, gx, vec, vr[S0]);
+    tw = tw + 1 == RD ? 0 : tw + 1;
+    {  // advection terms of row r - 1
+      const C uL0 = __shfl_up_sync(FULL, ur[V - 1], 1);
+      const C uRV = __shfl_down_sync(FULL, ur[0], 1);
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const C uc = ur[j], uL = j == 0 ? uL0 : ur[j - 1], uR = j == V - 1 ? uRV : ur[j + 1];
+        const C vm = vr[S1][j], vc = vr[S2][j], vp = vr[S0][j];
+        C t0, t1, t2, t3 = C(0);
+        if (paper) {
+          // Eqs. 32-35 as phih = c0 phi + |dt u| phi_upx + |dt v| phi_upy with
+          // c0 = 1 - dt (d_x u + d_y v + |u| + |v|); the upwind side is the
+          // sign of dt u (dt v): positive -> x - 1 (y - 1), else x + 1 (y + 1)
+          const C div = (uR - uL) / C(2) + (vp - vm) / C(2);
+          t0 = C(1) - dt * (div + (fabs(uc) + fabs(vc)));
+          t1 = dt * uc;
+          t2 = dt * vc;
+        } else {
+          t0 = C(0.5) * (uc + uR);
+          t1 = C(0.5) * (uL + uc);
+          t2 = C(0.5) * (vc + vp);
+          t3 = C(0.5) * (vm + vc);
+        }
+        T[tw][0][V * lane + j] = t0;
+        T[tw][1][V * lane + j] = t1;
+        T[tw][2][V * lane + j] = t2;
+        if (!paper) T[tw][3][V * lane + j] = t3;
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) ur[j] = un[j];
+    }
+#pragma unroll
+    for (int s = 0; s < SUB; ++s) {
+      const int nw = r - 3 * s;  // newest row of the input of substep s
+      if (nw - 1 >= 0) {         // convective half step (Eqs. 32-35) on row nw - 1
+        int ts = tw - 3 * s;
+        if (ts < 0) ts += RD;
+        const C(&cur)[V] = ph[s][S2];
+        const C(&up)[V] = ph[s][S1];
+        const C(&dn)[V] = ph[s][S0];
+        const C l0 = __shfl_up_sync(FULL, cur[V - 1], 1);
+        const C rV = __shfl_down_sync(FULL, cur[0], 1);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const C pc = cur[j], pl = j == 0 ? l0 : cur[j - 1], pr = j == V - 1 ? rV : cur[j + 1];
+          const C t0 = T[ts][0][V * lane + j], t1 = T[ts][1][V * lane + j];
+          const C t2 = T[ts][2][V * lane + j];
+          if (paper) {
+            const C upx = t1 > C(0) ? pl : pr;   // u = 0 contributes nothing
+            const C upy = t2 > C(0) ? up[j] : dn[j];
+            A[s][S2][j] = t0 * pc + fabs(t1) * upx + fabs(t2) * upy;
+          } else {
+            const C t3 = T[ts][3][V * lane + j];
+            const C Jpx = t0 > C(0) ? t0 * pc : t0 * pr;
+            const C Jmx = t1 > C(0) ? t1 * pl : t1 * pc;
+            const C Jpy = t2 > C(0) ? t2 * pc : t2 * dn[j];
+            const C Jmy = t3 > C(0) ? t3 * up[j] : t3 * pc;
+            C tend = Jpx - Jmx;
+            tend += Jpy - Jmy;
+            A[s][S2][j] = pc - dt * tend;
+          }
+        }
+      }
+      if (nw - 2 >= 0) {  // psi on row nw - 2 (Eq. 36)
+        const C(&Ac)[V] = A[s][S1];
+        const C l0 = __shfl_up_sync(FULL, Ac[V - 1], 1);
+        const C rV = __shfl_down_sync(FULL, Ac[0], 1);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const C hk = Ac[j];
+          C lap = A[s][S0][j];
+          lap += j == 0 ? l0 : Ac[j - 1];
+          lap += C(-4) * hk;
+          lap += j == V - 1 ? rV : Ac[j + 1];
+          lap += A[s][S2][j];
+          const C c = cubic_half ? hk : ph[s][S1][j];
+          P[s][S1][j] = a * hk + b * (c * c * c) - kappa * lap;
+        }
+      }
+      if (nw - 3 >= 0) {  // phi of the next substep on row nw - 3
+        const C(&Pc)[V] = P[s][S0];
+        const C l0 = __shfl_up_sync(FULL, Pc[V - 1], 1);
+        const C rV = __shfl_down_sync(FULL, Pc[0], 1);
+        C F[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          C lap = P[s][S2][j];
+          lap += j == 0 ? l0 : Pc[j - 1];
+          lap += C(-4) * Pc[j];
+          lap += j == V - 1 ? rV : Pc[j + 1];
+          lap += P[s][S1][j];
+          F[j] = A[s][S0][j] + dtG * lap;
+        }
+        if (s + 1 < SUB) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) ph[s + 1 < SUB ? s + 1 : 0][S0][j] = F[j];
+        } else {
+          const int orow = nw - 3 - H;  // output row within the tile
+          const int gy = y0 + orow;
+          if (orow >= 0 && orow < TY && gy < Ly) {
+            C *dst = phi_out + (long long)gy * Lx;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+              const int c = V * lane + j;
+              const int x = sx * OW + c - HX;
+              if (c >= HX && c < HX + OW && x < Lx) dst[x] = F[j];
+            }
+          }
+        }
+      }
+    }
+  };
+  for (int r = 0; r < NR; r += 3) {
+    row(std::integral_constant<int, 0>{}, r);
+    if (r + 1 < NR) row(std::integral_constant<int, 1>{}, r + 1);
+    if (r + 2 < NR) row(std::integral_constant<int, 2>{}, r + 2);
+  }
+}
+
+// ---- FD convection-diffusion: shared-memory tile, SUB substeps per launch ----------
+// A block of 32 x 8 threads owns a region RXW (a multiple of 32) wide and
+// TY + 2H high (H = 3 SUB) whose inner TX = RXW - 2H columns are written.
+// phi, u and v are staged once; the advection coefficients of Eqs. 32-35
+// (printed form: c0, dt u, dt v; flux form: the four face velocities) are
+// kept in registers for the thread's sites, and each substep runs three
+// phases (phih, psi, new phi) over a region that shrinks by one site per
+// phase, with a block barrier between phases.
+template <typename C, int RXW, int SUB>
+struct FDTile {
+  static constexpr int H = 3 * SUB, TX = RXW - 2 * H, TY = 32, RY = TY + 2 * H;
+  static constexpr int NXI = RXW / 32, NYI = (RY + 7) / 8;
+  static constexpr size_t smem = sizeof(C) * 3 * (size_t)RXW * RY;
+};
+
+template <typename C, int RXW, int SUB>
 __global__ void __launch_bounds__(256)
-    fd2d_kernel(const C *__restrict__ phi_in, const C *__restrict__ u, C *__restrict__ phi_out,
-                KParams<C> p, int sub) {
+    fd2d_tile_kernel(const C *__restrict__ phi_in, const C *__restrict__ u,
+                     C *__restrict__ phi_out, KParams<C> p) {
+  using G = FDTile<C, RXW, SUB>;
+  constexpr int H = G::H, TX = G::TX, TY = G::TY, RY = G::RY, NXI = G::NXI, NYI = G::NYI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *sm = reinterpret_cast<C *>(smem_raw);
-  const int H = 3 * sub, RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
-  C *sp = sm, *sh = sm + R, *sq = sm + 2 * R, *su = sm + 3 * R, *sv = sm + 4 * R;
+  C *sp = reinterpret_cast<C *>(smem_raw);
+  C *sa = sp + RXW * RY;
+  C *sq = sa + RXW * RY;
   const int Lx = p.Lx, Ly = p.Ly;
   const long long Sz = (long long)Lx * Ly;
   const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool big = Lx >= RXW && Ly >= RY;
+  // 1. stage phi -> sp, u -> sa, v -> sq on the whole region
   for (int ry = ty; ry < RY; ry += 8) {
-    const long long row = (long long)wrapi(y0 + ry, Ly) * Lx;
-    for (int rx = tx; rx < RX; rx += 32) {
-      const long long g = row + wrapi(x0 + rx, Lx);
-      sp[ry * RX + rx] = phi_in[g];
-      su[ry * RX + rx] = u[g];
-      sv[ry * RX + rx] = u[Sz + g];
+    const int gy = big ? wrap1(y0 + ry, Ly) : wrapi(y0 + ry, Ly);
+    const long long row = (long long)gy * Lx;
+#pragma unroll
+    for (int xi = 0; xi < NXI; ++xi) {
+      const int rx = tx + 32 * xi;
+      const int gx = big ? wrap1(x0 + rx, Lx) : wrapi(x0 + rx, Lx);
+      const int k = ry * RXW + rx;
+      sp[k] = __ldg(phi_in + row + gx);
+      sa[k] = __ldg(u + row + gx);
+      sq[k] = __ldg(u + Sz + row + gx);
     }
   }
   __syncthreads();
-  const C dt = p.dt, dtG = p.dtG;
-#pragma unroll 1
-  for (int s = 1; s <= sub; ++s) {
-    // convective half step (Eqs. 32-35) on the region shrunk by 3s - 2
+  // 2. advection coefficients of this thread's sites (registers)
+  const bool paper = p.adv_variant == LBM_ADV_PAPER, cubic_half = p.cubic_at_half != 0;
+  const C dt = p.dt, dtG = p.dtG, a = p.a, b = p.b, kappa = p.kappa;
+  C c0[NYI][NXI], c1[NYI][NXI], c2[NYI][NXI], c3[NYI][NXI];
+#pragma unroll
+  for (int yi = 0; yi < NYI; ++yi)
+#pragma unroll
+    for (int xi = 0; xi < NXI; ++xi) {
+      const int ry = ty + 8 * yi, rx = tx + 32 * xi;
+      c0[yi][xi] = c1[yi][xi] = c2[yi][xi] = c3[yi][xi] = C(0);
+      if (ry < 1 || ry >= RY - 1 || rx < 1 || rx >= RXW - 1) continue;
+      const int k = ry * RXW + rx;
+      const C uc = sa[k], uL = sa[k - 1], uR = sa[k + 1];
+      const C vc = sq[k], vm = sq[k - RXW], vp = sq[k + RXW];
+      if (paper) {
+        // phih = c0 phi + |dt u| phi_upx + |dt v| phi_upy (Eqs. 32-35)
+        const C div = (uR - uL) / C(2) + (vp - vm) / C(2);
+        c0[yi][xi] = C(1) - dt * (div + (fabs(uc) + fabs(vc)));
+        c1[yi][xi] = dt * uc;
+        c2[yi][xi] = dt * vc;
+      } else {
+        c0[yi][xi] = C(0.5) * (uc + uR);
+        c1[yi][xi] = C(0.5) * (uL + uc);
+        c2[yi][xi] = C(0.5) * (vc + vp);
+        c3[yi][xi] = C(0.5) * (vm + vc);
+      }
+    }
+  __syncthreads();
+  // 3. SUB substeps of Eqs. 32-36
+#pragma unroll
+  for (int s = 1; s <= SUB; ++s) {
     int lo = 3 * s - 2;
-    for (int ry = lo + ty; ry < RY - lo; ry += 8)
-      for (int rx = lo + tx; rx < RX - lo; rx += 32) {
-        const int k = ry * RX + rx;
-        const C ph = sp[k];
-        C tend;
-        if (p.adv_variant == LBM_ADV_PAPER) {
-          const C ua = su[k], va = sv[k];
-          const C dux = (su[k + 1] - su[k - 1]) / C(2);
-          const C dpx = ua < C(0) ? sp[k + 1] - ph : ph - sp[k - 1];
-          const C duy = (sv[k + RX] - sv[k - RX]) / C(2);
-          const C dpy = va < C(0) ? sp[k + RX] - ph : ph - sp[k - RX];
-          tend = (ph * dux + ua * dpx);
-          tend += (ph * duy + va * dpy);
+#pragma unroll
+    for (int yi = 0; yi < NYI; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < NXI; ++xi) {
+        const int ry = ty + 8 * yi, rx = tx + 32 * xi;
+        if (ry < lo || ry >= RY - lo || rx < lo || rx >= RXW - lo) continue;
+        const int k = ry * RXW + rx;
+        const C pc = sp[k];
+        if (paper) {
+          const C t1 = c1[yi][xi], t2 = c2[yi][xi];
+          const C upx = t1 > C(0) ? sp[k - 1] : sp[k + 1];
+          const C upy = t2 > C(0) ? sp[k - RXW] : sp[k + RXW];
+          sa[k] = c0[yi][xi] * pc + fabs(t1) * upx + fabs(t2) * upy;
         } else {
-          const C Upx = C(0.5) * (su[k] + su[k + 1]);
-          const C Umx = C(0.5) * (su[k - 1] + su[k]);
-          const C Jpx = Upx > C(0) ? Upx * ph : Upx * sp[k + 1];
-          const C Jmx = Umx > C(0) ? Umx * sp[k - 1] : Umx * ph;
-          const C Upy = C(0.5) * (sv[k] + sv[k + RX]);
-          const C Umy = C(0.5) * (sv[k - RX] + sv[k]);
-          const C Jpy = Upy > C(0) ? Upy * ph : Upy * sp[k + RX];
-          const C Jmy = Umy > C(0) ? Umy * sp[k - RX] : Umy * ph;
-          tend = Jpx - Jmx;
+          const C Upx = c0[yi][xi], Umx = c1[yi][xi], Upy = c2[yi][xi], Umy = c3[yi][xi];
+          const C Jpx = Upx > C(0) ? Upx * pc : Upx * sp[k + 1];
+          const C Jmx = Umx > C(0) ? Umx * sp[k - 1] : Umx * pc;
+          const C Jpy = Upy > C(0) ? Upy * pc : Upy * sp[k + RXW];
+          const C Jmy = Umy > C(0) ? Umy * sp[k - RXW] : Umy * pc;
+          C tend = Jpx - Jmx;
           tend += Jpy - Jmy;
+          sa[k] = pc - dt * tend;
         }
-        sh[k] = ph - dt * tend;
       }
     __syncthreads();
-    // psi = a phih + b (phi^n)^3 - kappa lap phih (5-point Laplacian, Eq. 36)
-    lo = 3 * s - 1;
-    for (int ry = lo + ty; ry < RY - lo; ry += 8)
-      for (int rx = lo + tx; rx < RX - lo; rx += 32) {
-        const int k = ry * RX + rx;
-        const C hk = sh[k];
-        const C c = p.cubic_at_half ? hk : sp[k];
-        C lap = sh[k - RX];
-        lap += sh[k - 1];
+    lo = 3 * s - 1;  // psi = a phih + b phi^3 - kappa lap phih (Eq. 36)
+#pragma unroll
+    for (int yi = 0; yi < NYI; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < NXI; ++xi) {
+        const int ry = ty + 8 * yi, rx = tx + 32 * xi;
+        if (ry < lo || ry >= RY - lo || rx < lo || rx >= RXW - lo) continue;
+        const int k = ry * RXW + rx;
+        const C hk = sa[k];
+        const C c = cubic_half ? hk : sp[k];
+        C lap = sa[k - RXW];
+        lap += sa[k - 1];
         lap += C(-4) * hk;
-        lap += sh[k + 1];
-        lap += sh[k + RX];
-        sq[k] = p.a * hk + p.b * (c * c * c) - p.kappa * lap;
+        lap += sa[k + 1];
+        lap += sa[k + RXW];
+        sq[k] = a * hk + b * (c * c * c) - kappa * lap;
       }
     __syncthreads();
-    // phi^{n+1} = phih + dt Gamma lap psi
-    lo = 3 * s;
-    for (int ry = lo + ty; ry < RY - lo; ry += 8)
-      for (int rx = lo + tx; rx < RX - lo; rx += 32) {
-        const int k = ry * RX + rx;
-        C lap = sq[k - RX];
+    lo = 3 * s;  // phi^{n+1} = phih + dt Gamma lap psi
+#pragma unroll
+    for (int yi = 0; yi < NYI; ++yi)
+#pragma unroll
+      for (int xi = 0; xi < NXI; ++xi) {
+        const int ry = ty + 8 * yi, rx = tx + 32 * xi;
+        if (ry < lo || ry >= RY - lo || rx < lo || rx >= RXW - lo) continue;
+        const int k = ry * RXW + rx;
+        C lap = sq[k - RXW];
         lap += sq[k - 1];
         lap += C(-4) * sq[k];
         lap += sq[k + 1];
-        lap += sq[k + RX];
-        sp[k] = sh[k] + dtG * lap;
+        lap += sq[k + RXW];
+        sp[k] = sa[k] + dtG * lap;
       }
     __syncthreads();
   }
-  for (int ry = H + ty; ry < H + TY; ry += 8) {
-    const int gy = y0 + ry;
-    if (gy >= Ly) break;
-    for (int rx = H + tx; rx < H + TX; rx += 32) {
-      const int gx = x0 + rx;
-      if (gx < Lx) phi_out[(long long)gy * Lx + gx] = sp[ry * RX + rx];
+  // 4. write the inner TX x TY sites
+#pragma unroll
+  for (int yi = 0; yi < NYI; ++yi)
+#pragma unroll
+    for (int xi = 0; xi < NXI; ++xi) {
+      const int ry = ty + 8 * yi, rx = tx + 32 * xi;
+      if (ry < H || ry >= H + TY || rx < H || rx >= H + TX) continue;
+      const int gx = x0 + rx, gy = y0 + ry;
+      if (gx < Lx && gy < Ly) phi_out[(long long)gy * Lx + gx] = sp[ry * RXW + rx];
     }
-  }
 }
 
 template <typename S, typename C>
@@ -285,8 +764,9 @@ __global__ void __launch_bounds__(256)
   dn[rowc + x] = d;
 }
 
-template <typename S, typename C>
-cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
+template <typename S, typename C, int RY>
+cudaError_t collide2d_ry(lbm_handle *h, int in, int force_on, int mode) {
+  constexpr int C2_TY = C2_BY * RY;
   KParams<C> p = make_params<C>(h, force_on);
   dim3 grid((p.Lx + C2_TX - 1) / C2_TX, (p.Ly + C2_TY - 1) / C2_TY), block(32, C2_BY);
   const S *hin = static_cast<const S *>(h->h[in]);
@@ -297,36 +777,135 @@ cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
   const bool tgen = p.cs2mT != C(0);
   if (mode == COLLIDE_STEP) {
     if (tgen)
-      collide2d_kernel<S, C, true, COLLIDE_STEP>
+      collide2d_kernel<S, C, true, COLLIDE_STEP, RY>
           <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
     else
-      collide2d_kernel<S, C, false, COLLIDE_STEP>
+      collide2d_kernel<S, C, false, COLLIDE_STEP, RY>
           <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   } else {
     if (tgen)
-      collide2d_kernel<S, C, true, COLLIDE_MOMENTS>
+      collide2d_kernel<S, C, true, COLLIDE_MOMENTS, RY>
           <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
     else
-      collide2d_kernel<S, C, false, COLLIDE_MOMENTS>
+      collide2d_kernel<S, C, false, COLLIDE_MOMENTS, RY>
           <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   }
   return cudaGetLastError();
 }
 
-template <typename C, int TX, int TY>
+template <typename C>
+cudaError_t collide2d_async(lbm_handle *h, int in, int force_on, int mode) {
+  KParams<C> p = make_params<C>(h, force_on);
+  dim3 grid((p.Lx + CA_TX - 1) / CA_TX, (p.Ly + CA_TY - 1) / CA_TY), block(32, C2_BY);
+  const C *hin = static_cast<const C *>(h->h[in]);
+  C *hout = static_cast<C *>(h->h[1 - in]);
+  const C *phi = static_cast<const C *>(h->phi[in]);
+  const C *dn = static_cast<const C *>(h->dn);
+  C *u = static_cast<C *>(h->u);
+  const size_t smem = collide_async_smem<C>();
+  const bool tgen = p.cs2mT != C(0);
+  if (mode == COLLIDE_STEP) {
+    if (tgen)
+      collide2d_async_kernel<C, true, COLLIDE_STEP>
+          <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+    else
+      collide2d_async_kernel<C, false, COLLIDE_STEP>
+          <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+  } else {
+    if (tgen)
+      collide2d_async_kernel<C, true, COLLIDE_MOMENTS>
+          <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+    else
+      collide2d_async_kernel<C, false, COLLIDE_MOMENTS>
+          <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+  }
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t collide2d_async_configure() {
+  const int smem = (int)collide_async_smem<C>();
+  cudaError_t e = cudaSuccess;
+  for (auto fn : {collide2d_async_kernel<C, true, COLLIDE_STEP>,
+                  collide2d_async_kernel<C, false, COLLIDE_STEP>,
+                  collide2d_async_kernel<C, true, COLLIDE_MOMENTS>,
+                  collide2d_async_kernel<C, false, COLLIDE_MOMENTS>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+template <typename S, typename C>
+cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
+  if constexpr (std::is_same<S, C>::value) {
+    if (h->collide_rows == 0) return collide2d_async<C>(h, in, force_on, mode);
+  }
+  return h->collide_rows == 4 ? collide2d_ry<S, C, 4>(h, in, force_on, mode)
+                              : collide2d_ry<S, C, 2>(h, in, force_on, mode);
+}
+
+template <typename C, int V, int SUB>
+cudaError_t fd2d_launch_one(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int TY) {
+  constexpr int H = 3 * SUB, HX = (H + V - 1) / V * V, OW = 32 * V - 2 * HX;
+  const int nstrips = (p.Lx + OW - 1) / OW, ntiles = (p.Ly + TY - 1) / TY;
+  const int warps = nstrips * ntiles;
+  fd2d_march_kernel<C, V, SUB><<<(warps + 1) / 2, 64, 0, h->stream>>>(
+      src, static_cast<const C *>(h->u), dst, p, TY, nstrips, ntiles);
+  return cudaGetLastError();
+}
+
+template <typename C, int RXW, int SUB>
+cudaError_t fd2d_tile_one(lbm_handle *h, const KParams<C> &p, const C *src, C *dst) {
+  using G = FDTile<C, RXW, SUB>;
+  dim3 grid((p.Lx + G::TX - 1) / G::TX, (p.Ly + G::TY - 1) / G::TY), block(32, 8);
+  fd2d_tile_kernel<C, RXW, SUB><<<grid, block, G::smem, h->stream>>>(
+      src, static_cast<const C *>(h->u), dst, p);
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t fd2d_tile(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub) {
+  if (h->fd_tile_w == 32) return fd2d_tile_one<C, 32, 1>(h, p, src, dst);  // one substep
+  return sub >= 2 ? fd2d_tile_one<C, 64, 2>(h, p, src, dst) : fd2d_tile_one<C, 64, 1>(h, p, src, dst);
+}
+
+template <typename C>
+cudaError_t fd2d_tile_configure() {
+  cudaError_t e = cudaFuncSetAttribute(fd2d_tile_kernel<C, 32, 1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)FDTile<C, 32, 1>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd2d_tile_kernel<C, 64, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FDTile<C, 64, 1>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd2d_tile_kernel<C, 64, 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FDTile<C, 64, 2>::smem);
+  return e;
+}
+
+template <typename C, int V>
+cudaError_t fd2d_sub(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub, int TY) {
+  if (h->fd_tile_w > 0) return fd2d_tile<C>(h, p, src, dst, sub);
+  switch (sub) {
+    case 1: return fd2d_launch_one<C, V, 1>(h, p, src, dst, TY);
+    case 2: return fd2d_launch_one<C, V, 2>(h, p, src, dst, TY);
+    case 3: return fd2d_launch_one<C, V, 3>(h, p, src, dst, TY);
+    default: return fd2d_launch_one<C, V, 4>(h, p, src, dst, TY);
+  }
+}
+
+// m substeps as ceil(m / sub) launches; the last launch takes the remainder.
+template <typename C, int V>
 cudaError_t fd2d(lbm_handle *h, int in) {
   KParams<C> p = make_params<C>(h, 0);
-  dim3 grid((p.Lx + TX - 1) / TX, (p.Ly + TY - 1) / TY), block(32, 8);
   const int launches = (h->m + h->sub - 1) / h->sub;
-  const C *u = static_cast<const C *>(h->u);
   const C *src = static_cast<const C *>(h->phi[in]);
   for (int j = 0; j < launches; ++j) {
     const int sub = (j == launches - 1) ? h->m - h->sub * (launches - 1) : h->sub;
     C *dst = static_cast<C *>(((launches - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
-    const int H = 3 * sub;
-    const size_t smem = sizeof(C) * 5 * (size_t)(TX + 2 * H) * (TY + 2 * H);
-    fd2d_kernel<C, TX, TY><<<grid, block, smem, h->stream>>>(src, u, dst, p, sub);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = fd2d_sub<C, V>(h, p, src, dst, sub, h->fd_rows);
     if (e != cudaSuccess) return e;
     src = dst;
   }
@@ -334,23 +913,6 @@ cudaError_t fd2d(lbm_handle *h, int in) {
 }
 
 }  // namespace
-
-// FD tile per compute type: FP32 64 x 32, FP64 32 x 32 (shared memory budget).
-constexpr int FD2_TX_F = 64, FD2_TY_F = 32, FD2_TX_D = 32, FD2_TY_D = 32;
-
-size_t fd2d_smem_bytes(int precision, int sub) {
-  const int H = 3 * sub;
-  if (precision == LBM_F64) return sizeof(double) * 5 * (size_t)(FD2_TX_D + 2 * H) * (FD2_TY_D + 2 * H);
-  return sizeof(float) * 5 * (size_t)(FD2_TX_F + 2 * H) * (FD2_TY_F + 2 * H);
-}
-
-cudaError_t fd2d_configure(int precision, size_t smem) {
-  if (precision == LBM_F64)
-    return cudaFuncSetAttribute(fd2d_kernel<double, FD2_TX_D, FD2_TY_D>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(fd2d_kernel<float, FD2_TX_F, FD2_TY_F>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
 
 cudaError_t collide2d_launch(lbm_handle *h, int in, int force_on, int mode) {
   switch (h->P.precision) {
@@ -360,9 +922,17 @@ cudaError_t collide2d_launch(lbm_handle *h, int in, int force_on, int mode) {
   }
 }
 
+cudaError_t collide2d_configure(int precision) {
+  cudaError_t e = precision == LBM_F64 ? fd2d_tile_configure<double>() : fd2d_tile_configure<float>();
+  if (e != cudaSuccess) return e;
+  if (precision == LBM_F64) return collide2d_async_configure<double>();
+  if (precision == LBM_F32DEV) return collide2d_async_configure<float>();
+  return cudaSuccess;
+}
+
 cudaError_t fd2d_launch(lbm_handle *h, int in) {
-  if (h->P.precision == LBM_F64) return fd2d<double, FD2_TX_D, FD2_TY_D>(h, in);
-  return fd2d<float, FD2_TX_F, FD2_TY_F>(h, in);
+  if (h->P.precision == LBM_F64) return fd2d<double, 2>(h, in);
+  return h->fd_cols == 2 ? fd2d<float, 2>(h, in) : fd2d<float, 4>(h, in);
 }
 
 cudaError_t density2d_launch(lbm_handle *h, int in) {

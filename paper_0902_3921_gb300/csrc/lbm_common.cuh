@@ -108,6 +108,10 @@ struct EventPair {
 struct lbm_handle {
   lbm_params P;
   int dims = 2, q = 9, m = 1, sub = 1;  // sub = FD substeps fused per launch
+  int fd_rows = 32;                     // output rows per warp of the 2D FD kernel
+  int fd_cols = 4;                      // columns per lane of the 2D FD kernel (FP32)
+  int fd_tile_w = 0;                    // 0: marching FD kernel; 32/64: tile kernel width
+  int collide_rows = 2;                 // sites per thread of the 2D collide kernel
   long long S = 0, t = 0;
   bool inited = false;
   cudaStream_t stream = nullptr;

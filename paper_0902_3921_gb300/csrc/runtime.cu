@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -15,8 +16,7 @@ namespace hlbm {
 cudaError_t collide2d_launch(lbm_handle *h, int in, int force_on, int mode);
 cudaError_t fd2d_launch(lbm_handle *h, int in);
 cudaError_t density2d_launch(lbm_handle *h, int in);
-size_t fd2d_smem_bytes(int precision, int sub);
-cudaError_t fd2d_configure(int precision, size_t smem);
+cudaError_t collide2d_configure(int precision);
 cudaError_t collide3d_launch(lbm_handle *h, int in, int force_on, int mode);
 cudaError_t fd3d_launch(lbm_handle *h, int in);
 cudaError_t density3d_launch(lbm_handle *h, int in);
@@ -295,6 +295,122 @@ bool same_params(const lbm_params &a, const lbm_params &b) {
          a.f16_scale_log2 == b.f16_scale_log2;
 }
 
+// Times fn() (three launches after one warm-up) with CUDA events on the
+// handle's stream; returns milliseconds or a negative value on error.
+template <typename F>
+float time_launches(lbm_handle *h, cudaEvent_t e0, cudaEvent_t e1, F &&fn) {
+  cudaError_t e = fn();
+  float ms = -1.f;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+  for (int k = 0; k < 3 && e == cudaSuccess; k++) e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  return e == cudaSuccess ? ms : -1.f;
+}
+
+// Autotuner of the 2D launch shapes, timed with CUDA events on the handle's
+// own (zeroed) buffers: for the FD kernel the columns per lane (FP32: 2 or
+// 4), the substeps per launch (<= 4) and the output rows per warp; for the
+// collide kernel the sites per thread (2 or 4).
+int autotune_2d(lbm_handle *h) {
+  if (const char *fixed = std::getenv("HLBM_TUNING")) {
+    int v[5] = {h->sub, h->fd_rows, h->fd_cols, h->collide_rows, 0};
+    const int nv = std::sscanf(fixed, "%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4]);
+    if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64))) && v[0] >= 1 &&
+        v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
+        (v[3] == 2 || v[3] == 4 || (v[3] == 0 && h->P.precision != LBM_F16DEV))) {
+      h->sub = std::min(v[0], h->m);
+      h->fd_rows = v[1];
+      h->fd_cols = h->P.precision == LBM_F64 ? 2 : v[2];
+      h->collide_rows = v[3];
+      h->fd_tile_w = v[4];
+      if (h->fd_tile_w == 32) h->sub = 1;
+      if (h->fd_tile_w == 64) h->sub = std::min(h->sub, 2);
+      return LBM_OK;
+    }
+    return fail(h, LBM_EINVAL, "HLBM_TUNING must be 'sub,rows,cols,collide_rows[,tile]'");
+  }
+  const bool verbose = std::getenv("HLBM_TUNE_VERBOSE") != nullptr;
+  const size_t cb = compute_bytes(h->P.precision);
+  CK(h, cudaMemsetAsync(h->phi[0], 0, cb * (size_t)h->S, h->stream), "cudaMemset");
+  CK(h, cudaMemsetAsync(h->u, 0, cb * h->dims * (size_t)h->S, h->stream), "cudaMemset");
+  CK(h, cudaMemsetAsync(h->h[0], 0, h->hbytes, h->stream), "cudaMemset");
+  struct FdShape {
+    int tile_w, cols, sub, rows;
+  };
+  std::vector<FdShape> cands;
+  // shared-memory tile kernel: 64 wide with 1 or 2 substeps, 32 wide with 1
+  cands.push_back({32, 4, 1, 32});
+  cands.push_back({64, 4, 1, 32});
+  if (h->m >= 2) cands.push_back({64, 4, 2, 32});
+  // warp-marching kernel: columns per lane, substeps per launch, rows per warp
+  const int subs[3] = {std::min(h->m, 4), std::min(h->m, 2), 1};
+  const int rows[5] = {8, 16, 32, 64, 128};
+  for (int cols : {4, 2}) {
+    if (cols == 4 && h->P.precision == LBM_F64) continue;
+    for (int si = 0; si < 3; si++) {
+      if (si > 0 && subs[si] == subs[si - 1]) continue;
+      for (int ri = 0; ri < 5; ri++) {
+        if (ri > 0 && rows[ri - 1] >= h->P.Ly) break;  // taller tiles change nothing
+        cands.push_back({0, cols, subs[si], rows[ri]});
+      }
+    }
+  }
+  cudaEvent_t e0, e1;
+  CK(h, cudaEventCreate(&e0), "cudaEventCreate");
+  CK(h, cudaEventCreate(&e1), "cudaEventCreate");
+  float best = 1e30f;
+  FdShape bestc = cands[0];
+  for (const FdShape &c : cands) {
+    h->fd_tile_w = c.tile_w;
+    h->fd_cols = c.cols;
+    h->sub = c.sub;
+    h->fd_rows = c.rows;
+    const float ms = time_launches(h, e0, e1, [&] { return launch_fd(h, 0); });
+    if (verbose)
+      std::fprintf(stderr, "hlbm tune fd %dx%d tile=%d cols=%d sub=%d rows=%d: %.1f us\n",
+                   h->P.Lx, h->P.Ly, c.tile_w, c.cols, c.sub, c.rows, ms * 1000.f / 3);
+    if (ms < 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(h, cudaGetLastError(), "FD autotuning");
+    }
+    if (ms < best) {
+      best = ms;
+      bestc = c;
+    }
+  }
+  h->fd_tile_w = bestc.tile_w;
+  h->fd_cols = bestc.cols;
+  h->sub = bestc.sub;
+  h->fd_rows = bestc.rows;
+  best = 1e30f;
+  int best_cr = 2;
+  for (int cr : {0, 2, 4}) {
+    if (cr == 0 && h->P.precision == LBM_F16DEV) continue;  // cp.async moves >= 4 bytes
+    h->collide_rows = cr;
+    const float ms =
+        time_launches(h, e0, e1, [&] { return launch_collide(h, 0, 0, COLLIDE_STEP); });
+    if (verbose)
+      std::fprintf(stderr, "hlbm tune collide %dx%d rows=%d: %.1f us\n", h->P.Lx, h->P.Ly, cr,
+                   ms * 1000.f / 3);
+    if (ms < 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(h, cudaGetLastError(), "collide autotuning");
+    }
+    if (ms < best) {
+      best = ms;
+      best_cr = cr;
+    }
+  }
+  h->collide_rows = best_cr;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -384,11 +500,18 @@ int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out) {
     cudaError_t e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc"));
   }
-  // opt in to the largest FD tile any handle may launch (the attribute is
-  // per kernel, shared by all handles of the process)
-  cudaError_t e = h->dims == 2 ? fd2d_configure(P.precision, fd2d_smem_bytes(P.precision, 4))
-                               : fd3d_configure(P.precision, fd3d_smem_bytes(P.precision, 1));
-  if (e != cudaSuccess) return bail(cuda_fail(h, e, "FD shared-memory configuration"));
+  cudaError_t e = cudaSuccess;
+  if (h->dims == 3) {
+    // opt in to the largest FD tile any handle may launch (the attribute is
+    // per kernel, shared by all handles of the process)
+    e = fd3d_configure(P.precision, fd3d_smem_bytes(P.precision, 1));
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "FD shared-memory configuration"));
+  } else {
+    e = collide2d_configure(P.precision);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "collide shared-memory configuration"));
+    int rc2 = autotune_2d(h);
+    if (rc2) return bail(rc2);
+  }
   *out = h;
   return LBM_OK;
 }
@@ -496,6 +619,13 @@ int lbm_synchronize(lbm_handle *h) {
 }
 
 long long lbm_time(const lbm_handle *h) { return h ? h->t : -1; }
+
+int lbm_tuning(const lbm_handle *h, int *values, int n) {
+  if (h == nullptr || values == nullptr || n < 0) return LBM_EINVAL;
+  const int v[6] = {h->sub, h->fd_rows, h->fd_cols, h->collide_rows, h->m, h->fd_tile_w};
+  for (int k = 0; k < n && k < 6; k++) values[k] = v[k];
+  return 6;
+}
 int lbm_fd_substeps(const lbm_handle *h) { return h ? h->m : -1; }
 
 int lbm_set_graphs(lbm_handle *h, int enable) {

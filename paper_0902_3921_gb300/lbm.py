@@ -29,7 +29,7 @@ PRECISIONS = {"f64": LBM_F64, "f32dev": LBM_F32DEV, "f16dev": LBM_F16DEV}
 EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_populations",
            "lbm_lattice", "lbm_diagnostics", "lbm_synchronize", "lbm_time", "lbm_fd_substeps",
            "lbm_set_graphs", "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_save",
-           "lbm_load", "lbm_free", "lbm_last_error", "lbm_diagnostics_noalloc",
+           "lbm_load", "lbm_free", "lbm_last_error", "lbm_tuning", "lbm_diagnostics_noalloc",
            "lbm_noalloc_last_error")
 
 
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_time.argtypes = [H]
     lib.lbm_time.restype = ctypes.c_longlong
     lib.lbm_fd_substeps.argtypes = [H]
+    lib.lbm_tuning.argtypes = [H, ctypes.POINTER(ctypes.c_int), ip]
+    lib.lbm_tuning.restype = ctypes.c_int
     lib.lbm_set_graphs.argtypes = [H, ip]
     lib.lbm_set_kernel_timing.argtypes = [H, ip]
     lib.lbm_kernel_times.argtypes = [H, dp, ctypes.POINTER(ctypes.c_longlong), ip]
@@ -265,6 +267,13 @@ def lbm_time(h) -> int:
 
 def lbm_fd_substeps(h) -> int:
     return load_library().lbm_fd_substeps(h)
+
+
+def lbm_tuning(h) -> dict:
+    v = (ctypes.c_int * 6)()
+    load_library().lbm_tuning(h, v, 6)
+    return {"fd_substeps_per_launch": v[0], "fd_rows_per_warp": v[1], "fd_cols_per_lane": v[2],
+            "collide_sites_per_thread": v[3], "m": v[4], "fd_tile_width": v[5]}
 
 
 def lbm_set_graphs(h, enable: bool):

@@ -343,3 +343,41 @@ def test_nonfinite_is_reported():
     d = lat.diagnostics()
     assert d["nonfinite"] == 1 and d["rc"] == lbm.LBM_ENONFINITE
     lat.step(1)  # still usable
+
+
+# every launch shape the autotuner can pick, pinned through HLBM_TUNING
+# ("FD substeps per launch, rows per warp, columns per lane, collide sites per
+# thread, FD tile width")
+SHAPES = ["4,16,4,2,0", "4,8,2,4,0", "2,32,4,0,0", "3,16,4,2,0", "1,64,2,0,0",
+          "1,32,4,0,32", "1,32,4,2,64", "2,32,4,4,64"]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("precision", [lbm.LBM_F64, lbm.LBM_F32DEV])
+def test_every_launch_shape(shape, precision, monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", shape)
+    kw = dict(CFG1)
+    op, lp = _pair(70, 45, m=5, precision=precision, **kw)  # m = 5: a remainder launch
+    phi = I.drop(2, 70, 45, R=12, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 70, 45)
+    u = u + 0.003 * np.sin(np.arange(70) / 4.0)[None, None, :]
+    ref, lat = _run_both(op, lp, n, phi, u, 25)
+    dphi, du, dn = _errors(ref, lat)
+    if precision == lbm.LBM_F64:
+        assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (shape, dphi, du, dn)
+    else:
+        assert dphi <= 2e-6 and du <= 1e-7 and dn <= 1e-6, (shape, dphi, du, dn)
+    t = lbm.lbm_tuning(lat.handle)
+    assert t["fd_tile_width"] == int(shape.split(",")[4])
+
+
+@pytest.mark.parametrize("shape", ["4,16,4,2,0", "1,32,4,0,32", "2,32,4,0,64"])
+def test_launch_shapes_flux_variant(shape, monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", shape)
+    op, lp = _pair(64, 40, m=4, adv_variant=1, cubic_at_half=1, **CFG1)
+    phi = I.drop(2, 64, 40, R=10, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 64, 40)
+    u = u + 0.003 * np.cos(np.arange(40) / 3.0)[None, :, None]
+    ref, lat = _run_both(op, lp, n, phi, u, 20)
+    dphi, du, dn = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (shape, dphi, du, dn)
