@@ -462,16 +462,32 @@ __global__ void __launch_bounds__(64)
   int tw = RD - 1;  // terms slot of row r - 1
   int gy = wrapi(y0 - H, Ly);  // global row of the next load
 
+  // row r + 1 is loaded while row r is processed
+  C nph[V], nu[V], nv[V];
+  {
+    const long long grow = (long long)gy * Lx;
+    load_row<C, V>(phi_in + grow, gx, vec, nph);
+    load_row<C, V>(u + grow, gx, vec, nu);
+    load_row<C, V>(u + Sz + grow, gx, vec, nv);
+  }
   auto row = [&](auto R3c, int r) {
     constexpr int R3 = decltype(R3c)::value;
     constexpr int S0 = R3, S1 = (R3 + 1) % 3, S2 = (R3 + 2) % 3;
     // slots: row r -> S0, r - 1 -> S2, r - 2 -> S1 (rows are stored at row % 3)
-    const long long grow = (long long)gy * Lx;
-    gy = gy + 1 == Ly ? 0 : gy + 1;
     C un[V];
-    load_row<C, V>(phi_in + grow, gx, vec, ph[0][S0]);
-    load_row<C, V>(u + grow, gx, vec, un);
-    load_row<C, V>(u + Sz + grow, gx, vec, vr[S0]);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      ph[0][S0][j] = nph[j];
+      un[j] = nu[j];
+      vr[S0][j] = nv[j];
+    }
+    if (r + 1 < NR) {
+      gy = gy + 1 == Ly ? 0 : gy + 1;
+      const long long grow = (long long)gy * Lx;
+      load_row<C, V>(phi_in + grow, gx, vec, nph);
+      load_row<C, V>(u + grow, gx, vec, nu);
+      load_row<C, V>(u + Sz + grow, gx, vec, nv);
+    }
     tw = tw + 1 == RD ? 0 : tw + 1;
     {  // advection terms of row r - 1
       const C uL0 = __shfl_up_sync(FULL, ur[V - 1], 1);
@@ -506,7 +522,8 @@ __global__ void __launch_bounds__(64)
 #pragma unroll
     for (int s = 0; s < SUB; ++s) {
       const int nw = r - 3 * s;  // newest row of the input of substep s
-      if (nw - 1 >= 0) {         // convective half step (Eqs. 32-35) on row nw - 1
+      // rows of substep s outside [3s + 1, NR - 3s - 1) never reach the output
+      if (nw - 1 >= 3 * s + 1) {  // convective half step (Eqs. 32-35) on row nw - 1
         int ts = tw - 3 * s;
         if (ts < 0) ts += RD;
         const C(&cur)[V] = ph[s][S2];
@@ -535,7 +552,7 @@ __global__ void __launch_bounds__(64)
           }
         }
       }
-      if (nw - 2 >= 0) {  // psi on row nw - 2 (Eq. 36)
+      if (nw - 2 >= 3 * s + 2) {  // psi on row nw - 2 (Eq. 36)
         const C(&Ac)[V] = A[s][S1];
         const C l0 = __shfl_up_sync(FULL, Ac[V - 1], 1);
         const C rV = __shfl_down_sync(FULL, Ac[0], 1);
@@ -551,7 +568,7 @@ __global__ void __launch_bounds__(64)
           P[s][S1][j] = a * hk + b * (c * c * c) - kappa * lap;
         }
       }
-      if (nw - 3 >= 0) {  // phi of the next substep on row nw - 3
+      if (nw - 3 >= 3 * s + 3) {  // phi of the next substep on row nw - 3
         const C(&Pc)[V] = P[s][S0];
         const C l0 = __shfl_up_sync(FULL, Pc[V - 1], 1);
         const C rV = __shfl_down_sync(FULL, Pc[0], 1);

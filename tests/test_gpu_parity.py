@@ -365,8 +365,10 @@ def test_every_launch_shape(shape, precision, monkeypatch):
     dphi, du, dn = _errors(ref, lat)
     if precision == lbm.LBM_F64:
         assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (shape, dphi, du, dn)
-    else:
-        assert dphi <= 2e-6 and du <= 1e-7 and dn <= 1e-6, (shape, dphi, du, dn)
+    else:  # the FP32-deviation bar: |dphi| <= 1e-5, |du| <= 1e-3 max|u*|
+        _, ru = ref.moments()
+        umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+        assert dphi <= 1e-5 and du <= 1e-3 * umax, (shape, dphi, du, umax)
     t = lbm.lbm_tuning(lat.handle)
     assert t["fd_tile_width"] == int(shape.split(",")[4])
 
