@@ -172,6 +172,44 @@ int lbm_kernel_times(lbm_handle *h, double *ms, long long *launches, int reset);
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
 
+/* ---- batches of independent lattices --------------------------------------
+ * Many independent periodic 2D (D2Q9) lattices of uneven size, all with the
+ * common parameters of `common` (T = 1/3, FP64 or FP32-deviation storage)
+ * and each with its own size and body force G = n g while t < force_steps
+ * (Sec. III), advanced together by ONE persistent kernel launch per
+ * lbm_batch_step call (captured in a CUDA graph).  Each instance is owned by
+ * one CTA, so no CTA ever waits for another.  The CTA shape (threads x CTAs
+ * per SM) is timed at creation on a zeroed state and the fastest kept
+ * (HLBM_BATCH_SHAPE="threads,ctas_per_sm" fixes it; HLBM_TUNE_VERBOSE=1 prints
+ * the candidates).  Every instance starts at rest (phi = 0, n = 1, u = 0). */
+typedef struct {
+  int Lx, Ly;            /* periodic lattice of this instance, each >= 3        */
+  double g[2];           /* body force per unit density                         */
+  long long force_steps; /* g acts at steps t = 0 .. force_steps-1             */
+} lbm_instance;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Validates and allocates; returns the batch in *out (NULL and the error text
+ * in lbm_batch_last_error(NULL) on failure).  cuda_stream as in lbm_create. */
+int lbm_batch_create(const lbm_params *common, const lbm_instance *inst, int count,
+                     void *cuda_stream, lbm_batch **out);
+/* Initial fields of instance k (host FP64 arrays of Lx*Ly values), as in
+ * lbm_init_fields.  Resets the batch clock to t = 0: initialise every instance
+ * that should not start at rest before the first lbm_batch_step. */
+int lbm_batch_init_fields(lbm_batch *b, int k, const double *n, const double *phi,
+                          const double *ux, const double *uy);
+/* Advances every instance by nsteps LB steps (one persistent launch). */
+int lbm_batch_step(lbm_batch *b, long long nsteps);
+/* n, phi, u* of instance k at the current t into host arrays (NULL skips). */
+int lbm_batch_moments(lbm_batch *b, int k, double *n, double *phi, double *ux, double *uy);
+int lbm_batch_set_graphs(lbm_batch *b, int enable);
+/* Threads per CTA, CTAs and total sites of the batch (any pointer may be NULL). */
+int lbm_batch_shape(const lbm_batch *b, int *threads, int *ctas, long long *sites);
+int lbm_batch_synchronize(lbm_batch *b);
+void lbm_batch_free(lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 /* Allocation-free diagnostics.  The paper has no counterpart to this entry
  * point: it exists for callers that cannot allocate device memory, such as a
  * host framework that owns all device memory through its own allocator and

@@ -30,7 +30,9 @@ EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_popu
            "lbm_lattice", "lbm_diagnostics", "lbm_synchronize", "lbm_time", "lbm_fd_substeps",
            "lbm_set_graphs", "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_save",
            "lbm_load", "lbm_free", "lbm_last_error", "lbm_tuning", "lbm_diagnostics_noalloc",
-           "lbm_noalloc_last_error")
+           "lbm_noalloc_last_error", "lbm_batch_create", "lbm_batch_init_fields",
+           "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_graphs", "lbm_batch_shape",
+           "lbm_batch_synchronize", "lbm_batch_free", "lbm_batch_last_error")
 
 
 class c_lbm_params(ctypes.Structure):
@@ -51,6 +53,11 @@ class c_lbm_diag(ctypes.Structure):
                 ("r_cm", ctypes.c_double * 3), ("v_f", ctypes.c_double * 3),
                 ("area", ctypes.c_double), ("R_eff", ctypes.c_double),
                 ("nonfinite", ctypes.c_int)]
+
+
+class c_lbm_instance(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("g", ctypes.c_double * 2),
+                ("force_steps", ctypes.c_longlong)]
 
 
 class LbmError(RuntimeError):
@@ -100,6 +107,23 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_diagnostics_noalloc.restype = ctypes.c_int
     lib.lbm_noalloc_last_error.argtypes = []
     lib.lbm_noalloc_last_error.restype = ctypes.c_char_p
+    B = ctypes.c_void_p
+    lib.lbm_batch_create.argtypes = [ctypes.POINTER(c_lbm_params), ctypes.POINTER(c_lbm_instance),
+                                     ip, vp, ctypes.POINTER(B)]
+    lib.lbm_batch_init_fields.argtypes = [B, ip, dp, dp, dp, dp]
+    lib.lbm_batch_step.argtypes = [B, ctypes.c_longlong]
+    lib.lbm_batch_moments.argtypes = [B, ip, dp, dp, dp, dp]
+    lib.lbm_batch_set_graphs.argtypes = [B, ip]
+    lib.lbm_batch_shape.argtypes = [B, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_batch_synchronize.argtypes = [B]
+    lib.lbm_batch_free.argtypes = [B]
+    lib.lbm_batch_free.restype = None
+    lib.lbm_batch_last_error.argtypes = [B]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_moments",
+                 "lbm_batch_set_graphs", "lbm_batch_shape", "lbm_batch_synchronize"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_populations",
                  "lbm_lattice", "lbm_diagnostics", "lbm_synchronize", "lbm_fd_substeps",
                  "lbm_set_graphs", "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_save",
@@ -351,6 +375,76 @@ class Lattice:
     def close(self):
         if self.handle:
             lbm_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning wrapper around one lbm_batch: independent 2D lattices advanced by
+    one persistent launch.  `instances` is a list of (Lx, Ly, (gx, gy),
+    force_steps)."""
+
+    def __init__(self, common: LbmParams, instances, stream: int | None = None):
+        lib = load_library()
+        self.common = common
+        self.instances = [tuple(i) for i in instances]
+        arr = (c_lbm_instance * len(instances))()
+        for k, (Lx, Ly, g, fs) in enumerate(self.instances):
+            arr[k].Lx, arr[k].Ly = int(Lx), int(Ly)
+            arr[k].g = (ctypes.c_double * 2)(float(g[0]), float(g[1]))
+            arr[k].force_steps = int(fs)
+        self.handle = ctypes.c_void_p()
+        cp = common.to_c()
+        rc = lib.lbm_batch_create(ctypes.byref(cp), arr, len(instances),
+                                  ctypes.c_void_p(stream or 0), ctypes.byref(self.handle))
+        if rc != LBM_OK:
+            self.handle = None
+            raise LbmError(rc, lib.lbm_batch_last_error(None).decode())
+
+    def _check(self, rc, what):
+        if rc != LBM_OK:
+            raise LbmError(rc, what + ": " + load_library().lbm_batch_last_error(self.handle).decode())
+
+    def init_fields(self, k, n, phi, u):
+        Lx, Ly = self.instances[k][:2]
+        S = Lx * Ly
+        n, phi = _f64(n, S), _f64(phi, S)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(2, S)
+        self._check(load_library().lbm_batch_init_fields(self.handle, k, _dptr(n), _dptr(phi),
+                                                         _dptr(u[0]), _dptr(u[1])),
+                    "lbm_batch_init_fields")
+
+    def step(self, nsteps):
+        self._check(load_library().lbm_batch_step(self.handle, int(nsteps)), "lbm_batch_step")
+        return self
+
+    def moments(self, k):
+        Lx, Ly = self.instances[k][:2]
+        S = Lx * Ly
+        n, phi, u = np.empty(S), np.empty(S), np.empty((2, S))
+        self._check(load_library().lbm_batch_moments(self.handle, k, _dptr(n), _dptr(phi),
+                                                     _dptr(u[0]), _dptr(u[1])), "lbm_batch_moments")
+        return n.reshape(Ly, Lx), phi.reshape(Ly, Lx), u.reshape(2, Ly, Lx)
+
+    def set_graphs(self, enable):
+        load_library().lbm_batch_set_graphs(self.handle, int(enable))
+
+    def shape(self):
+        t, c, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        load_library().lbm_batch_shape(self.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(st))
+        return {"threads": t.value, "ctas": c.value, "sites": st.value}
+
+    def synchronize(self):
+        self._check(load_library().lbm_batch_synchronize(self.handle), "lbm_batch_synchronize")
+
+    def close(self):
+        if self.handle:
+            load_library().lbm_batch_free(self.handle)
             self.handle = None
 
     def __del__(self):

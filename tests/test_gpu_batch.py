@@ -1,0 +1,119 @@
+"""GPU parity of the batched persistent engine (independent lattices of
+uneven size in one launch) against the FP64 oracle, instance by instance."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0902_3921_gb300 import inputs as I
+from paper_0902_3921_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+CFG1 = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_0902_3921_gb300 import build as B
+    B.build()
+    lbm.load_library()
+
+
+def _instance_fields(Lx, Ly, R, seed):
+    op = O.Params(Lx=Lx, Ly=Ly, **CFG1)
+    phi = I.drop(2, Lx, Ly, R=R, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    phi = phi + 0.01 * (I.uniform01(seed, Lx * Ly).reshape(Ly, Lx) - 0.5)
+    n, u = I.rest(2, Lx, Ly)
+    return n, phi, u
+
+
+def _oracle_run(Lx, Ly, g, fs, fields, steps, m=4):
+    op = O.Params(Lx=Lx, Ly=Ly, m=m, g=(g[0], g[1], 0.0), force_steps=fs, **CFG1)
+    st = O.State.create(op, *fields)
+    st.run(steps)
+    n, u = st.moments()
+    return n, st.phi, u
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_batch_fp64_matches_oracle(graphs):
+    insts = [(37, 23, (2e-5, 0.0), 12), (3, 3, (0.0, 0.0), 0), (64, 48, (0.0, 1e-5), 40),
+             (5, 70, (0.0, 0.0), 0), (96, 33, (1e-5, -1e-5), 7), (32, 32, (0.0, 0.0), 0),
+             (130, 17, (3e-5, 0.0), 100)]
+    common = lbm.LbmParams(precision=lbm.LBM_F64, fd_substeps=4, **CFG1)
+    b = lbm.Batch(common, insts)
+    b.set_graphs(graphs)
+    fields = []
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        f = _instance_fields(Lx, Ly, R=min(Lx, Ly) / 4, seed=k)
+        fields.append(f)
+        b.init_fields(k, *f)
+    b.step(9).step(21)  # the force of some instances switches off inside a call
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        rn, rphi, ru = _oracle_run(Lx, Ly, g, fs, fields[k], 30)
+        gn, gphi, gu = b.moments(k)
+        assert np.max(np.abs(gphi - rphi)) <= 1e-11, k
+        assert np.max(np.abs(gu - ru)) <= 1e-12, k
+        assert np.max(np.abs(gn - rn)) <= 1e-11, k
+    b.close()
+
+
+def test_batch_config_fp32_sampled_instances():
+    """512 instances, sides in {32, 48, ..., 256}, drop radius in [6, side/3],
+    half of them pushed by g_x = 1e-5 (here for the first 40 of 60 steps).
+    Eight sampled instances are compared with the oracle at the FP32 bar."""
+    desc = I.batch_instances(512, seed=0)
+    insts = [(d["side"], d["side"], (1e-5 if d["forced"] else 0.0, 0.0),
+              40 if d["forced"] else 0) for d in desc]
+    common = lbm.LbmParams(precision=lbm.LBM_F32DEV, fd_substeps=4, **CFG1)
+    b = lbm.Batch(common, insts)
+    sample = sorted(range(512), key=lambda k: desc[k]["side"])[:6] + [7, 300]
+    fields = {}
+    for k in range(512):
+        d = desc[k]
+        f = _instance_fields(d["side"], d["side"], d["R"], seed=k)
+        if k in sample:
+            fields[k] = f
+        b.init_fields(k, *f)
+    b.step(30).step(30)
+    shape = b.shape()
+    assert shape["sites"] == sum(d["side"] ** 2 for d in desc)
+    for k in sample:
+        Lx, Ly, g, fs = insts[k]
+        rn, rphi, ru = _oracle_run(Lx, Ly, g, fs, fields[k], 60)
+        gn, gphi, gu = b.moments(k)
+        umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+        assert np.max(np.abs(gphi - rphi)) <= 1e-5, k
+        assert np.max(np.abs(gu - ru)) <= 1e-3 * umax, k
+    b.close()
+
+
+def test_batch_equals_single_lattices_fp64():
+    insts = [(48, 40, (1e-5, 0.0), 5), (33, 50, (0.0, 0.0), 0)]
+    common = lbm.LbmParams(precision=lbm.LBM_F64, fd_substeps=4, **CFG1)
+    b = lbm.Batch(common, insts)
+    outs = []
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        f = _instance_fields(Lx, Ly, R=8, seed=10 + k)
+        b.init_fields(k, *f)
+        lat = lbm.Lattice(lbm.LbmParams(Lx=Lx, Ly=Ly, precision=lbm.LBM_F64, fd_substeps=4,
+                                        g=(g[0], g[1], 0.0), force_steps=fs, **CFG1))
+        lat.init_fields(*f).step(20)
+        outs.append(lat.moments())
+        lat.close()
+    b.step(20)
+    for k in range(2):
+        for x, y in zip(b.moments(k), outs[k]):
+            np.testing.assert_allclose(x, y, rtol=0, atol=1e-12)
+
+
+def test_batch_rejects_bad_instances():
+    common = lbm.LbmParams(precision=lbm.LBM_F32DEV, **CFG1)
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch(common, [(2, 10, (0.0, 0.0), 0)])
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch(lbm.LbmParams(precision=lbm.LBM_F16DEV, **CFG1), [(10, 10, (0.0, 0.0), 0)])
+    b = lbm.Batch(common, [(10, 10, (0.0, 0.0), 0)])
+    with pytest.raises(lbm.LbmError):
+        b.step(1)  # not initialised
+    b.close()
