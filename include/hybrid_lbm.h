@@ -210,6 +210,59 @@ int lbm_batch_synchronize(lbm_batch *b);
 void lbm_batch_free(lbm_batch *b);
 const char *lbm_batch_last_error(const lbm_batch *b);
 
+/* ---- learned surrogate ------------------------------------------------------
+ * A stack of periodic 3x3 convolutions (4 -> C -> ... -> C -> 4 channels, ReLU
+ * between layers) that predicts, from the state x_t = (phi, u*_x, u*_y, n - 1)
+ * of a 2D lattice, the state one window of k LB steps later:
+ *   x_{t+k} = x_t + out_std * Net((x_t - in_mean) / in_std).
+ * BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
+ * master weights and Adam.  The paper has no counterpart: this is the learned
+ * extension of the method, judged by the paper's observables (structure
+ * factor, domain size, mass).  States are device FP32 arrays [N][H][W][4];
+ * H must be a multiple of 8 and W of 16. */
+typedef struct lbm_net lbm_net;
+
+/* channels 16 or 32, layers 2..8; He-normal weights from `seed`, zero biases. */
+int lbm_net_create(int channels, int layers, unsigned long long seed, lbm_net **out);
+/* Number of parameters in the flat order [layer][W[co][3][3][ci] then b[co]]. */
+long long lbm_net_param_count(const lbm_net *net);
+/* Copies the FP32 master parameters to (set = 0) or from (set = 1) a host
+ * array of lbm_net_param_count floats. */
+int lbm_net_params(lbm_net *net, float *host, long long n, int set);
+/* The gradients of the last lbm_net_train_step, same order. */
+int lbm_net_grads(lbm_net *net, float *host, long long n);
+/* Per-channel normalisation: in_mean[4], in_std[4] of x_t and out_std[4] of
+ * x_{t+k} - x_t (host arrays). */
+int lbm_net_set_normalisation(lbm_net *net, const float *in_mean, const float *in_std,
+                              const float *out_std);
+int lbm_net_normalisation(const lbm_net *net, float *out12);
+/* x1 = prediction of the state one window after x0 (device arrays). */
+int lbm_net_forward(lbm_net *net, const float *x0, int N, int H, int W, float *x1,
+                    void *cuda_stream);
+/* One training step on pairs (x0, x1): MSE between Net(x0) and the normalised
+ * change, backward pass, and (update != 0) one Adam step with rate lr.  *loss
+ * (may be NULL) receives the loss before the update; waits for the stream. */
+int lbm_net_train_step(lbm_net *net, const float *x0, const float *x1, int N, int H, int W,
+                       float lr, int update, double *loss, void *cuda_stream);
+/* The network state of lattice h at its current time into a device array
+ * [Ly][Lx][4] (queued on h's stream). */
+int lbm_surrogate_state(lbm_handle *h, float *out);
+/* Advances h by `windows` windows of `window_steps` LB steps each with the
+ * network: state -> prediction -> residual check (mean change of phi per site
+ * |d sum phi| / sites <= mass_tol; max |phi| <= max(1.1 phi0, 1.05 max|phi_t|);
+ * max |u*| <= max(1.5 max|u*_t|, 0.01 c_s), with _t the state the window starts
+ * from; HLBM_SURROGATE_VERBOSE=1 prints the values per window); a passing
+ * prediction becomes the new state (populations rebuilt as f_eq(n, u* - F/2n)
+ * with phi shifted to keep sum phi if conserve_mass), a failing one is
+ * replaced by window_steps plain LB steps.  phi_clamp > 0 first clips the
+ * predicted phi to |phi| <= phi_clamp * max|phi_t|.  *fallbacks counts the
+ * plain windows.  The body force must be off; t advances by
+ * windows * window_steps. */
+int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_steps,
+                          double mass_tol, int conserve_mass, double phi_clamp, int *fallbacks);
+void lbm_net_free(lbm_net *net);
+const char *lbm_net_last_error(const lbm_net *net);
+
 /* Allocation-free diagnostics.  The paper has no counterpart to this entry
  * point: it exists for callers that cannot allocate device memory, such as a
  * host framework that owns all device memory through its own allocator and

@@ -413,6 +413,11 @@ int autotune_2d(lbm_handle *h) {
 
 }  // namespace
 
+namespace hlbm {
+// n(t), phi(t), u*(t) as FP64 in the handle's staging buffer (surrogate coupling)
+int queue_moments_for(lbm_handle *h) { return queue_moments(h); }
+}  // namespace hlbm
+
 extern "C" {
 
 int lbm_lattice(int dims, int *e, double *w) {

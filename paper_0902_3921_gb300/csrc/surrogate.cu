@@ -1,0 +1,823 @@
+// surrogate.cu -- the learned surrogate: a stack of periodic 3x3 convolutions
+// (4 -> C -> ... -> C -> 4 channels, ReLU between layers) that maps the
+// normalised state x_t = (phi, u*_x, u*_y, n - 1) of a 2D lattice to the
+// normalised change x_{t+k} - x_t, with BF16 weights and activations and FP32
+// accumulation on the tensor cores, its backward pass and Adam training, and
+// the coupling to a lattice handle (pack the state, advance by the network,
+// check a residual, fall back to the plain scheme).  The paper has no
+// counterpart; the network is judged by the paper's observables.
+//
+// Layouts: activations NHWC with padded channel counts (the 4-channel input
+// is padded to 16, hidden layers C = 32, the last layer's outputs to 8);
+// weights [Cout_p][KS] with K = 9 Cin_p ordered (tap, ci), tap = (dy+1)*3 +
+// (dx+1), KS = K + 8 (bank-conflict padding, always zero).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "lbm_common.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+using namespace hlbm;
+
+constexpr int TILE_H = 8, TILE_W = 16;  // pixels per CTA (8 warps x one row of 16)
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned ld32(const bf16 *p) {
+  return *reinterpret_cast<const unsigned *>(p);
+}
+
+enum { EPI_RELU = 0, EPI_LINEAR_F32 = 1, EPI_MASK = 2 };
+
+// out[p, co] = sum_{tap, ci} in[p + tap, ci] w[co][tap, ci] (periodic), then
+//   EPI_RELU:       bf16 max(. + bias, 0)
+//   EPI_LINEAR_F32: fp32 . + bias
+//   EPI_MASK:       bf16 . * (mask[p, co] > 0)    (backward through a ReLU)
+template <int CINP, int COUTP, int EPI>
+__global__ void __launch_bounds__(256)
+    conv_mma_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w,
+                    const float *__restrict__ bias, const bf16 *__restrict__ mask, int H, int W,
+                    bf16 *__restrict__ out_bf, float *__restrict__ out_f) {
+  constexpr int PS = CINP + 8;          // pixel stride in shared memory (bf16)
+  constexpr int KS = 9 * CINP + 8;      // weight row stride (bf16)
+  constexpr int RH = TILE_H + 2, RW = TILE_W + 2;
+  __shared__ __align__(16) bf16 sin[RH * RW * PS];
+  __shared__ __align__(16) bf16 sw[COUTP * KS];
+  const int x0 = blockIdx.x * TILE_W, y0 = blockIdx.y * TILE_H, n = blockIdx.z;
+  const int tid = threadIdx.x;
+  const long long img = (long long)n * H * W;
+  // input tile with a periodic halo of 1, 16-byte copies
+  constexpr int VPP = CINP / 8;  // 16-byte vectors per pixel
+  for (int k = tid; k < RH * RW * VPP; k += 256) {
+    const int pix = k / VPP, v = k - pix * VPP;
+    const int r = pix / RW, c = pix - r * RW;
+    int gy = y0 + r - 1, gx = x0 + c - 1;
+    gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
+    gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
+    const uint4 val = *reinterpret_cast<const uint4 *>(in + (img + (long long)gy * W + gx) * CINP + v * 8);
+    *reinterpret_cast<uint4 *>(sin + pix * PS + v * 8) = val;
+  }
+  for (int k = tid; k < COUTP * KS / 8; k += 256)
+    reinterpret_cast<uint4 *>(sw)[k] = reinterpret_cast<const uint4 *>(w)[k];
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  float acc[COUTP / 8][4];
+#pragma unroll
+  for (int j = 0; j < COUTP / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ty = tap / 3, tx = tap % 3;
+    const bf16 *pa0 = sin + ((warp + ty) * RW + g + tx) * PS + 2 * t;
+    const bf16 *pa1 = pa0 + 8 * PS;
+#pragma unroll
+    for (int kb = 0; kb < CINP / 16; ++kb) {
+      const unsigned a0 = ld32(pa0 + kb * 16), a1 = ld32(pa1 + kb * 16);
+      const unsigned a2 = ld32(pa0 + kb * 16 + 8), a3 = ld32(pa1 + kb * 16 + 8);
+#pragma unroll
+      for (int j = 0; j < COUTP / 8; ++j) {
+        const bf16 *pb = sw + (j * 8 + g) * KS + tap * CINP + kb * 16 + 2 * t;
+        mma_bf16(acc[j], a0, a1, a2, a3, ld32(pb), ld32(pb + 8));
+      }
+    }
+  }
+  // rows g and g + 8 of the warp's 16 pixels; columns 2t, 2t + 1 of each n-tile
+  const int y = y0 + warp;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const long long p = img + (long long)y * W + x0 + g + 8 * half;
+#pragma unroll
+    for (int j = 0; j < COUTP / 8; ++j) {
+      const int co = j * 8 + 2 * t;
+      float v0 = acc[j][2 * half], v1 = acc[j][2 * half + 1];
+      if constexpr (EPI == EPI_LINEAR_F32) {
+        *reinterpret_cast<float2 *>(out_f + p * COUTP + co) = make_float2(v0 + bias[co], v1 + bias[co + 1]);
+      } else {
+        if constexpr (EPI == EPI_RELU) {
+          v0 = fmaxf(v0 + bias[co], 0.f);
+          v1 = fmaxf(v1 + bias[co + 1], 0.f);
+        } else {
+          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + p * COUTP + co);
+          v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+          v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(out_bf + p * COUTP + co) = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+// Partial weight and bias gradients of one layer over a grid-stride set of
+// pixel tiles: dW[co][tap, ci] += dz[p, co] x[p + tap, ci], db[co] += dz[p, co].
+// Thread (co, ci4) owns 9 taps x 4 input channels; FP32 throughout.
+template <int CINP, int COUTP, int DZS>
+__global__ void __launch_bounds__(256)
+    conv_wgrad_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int N, int H, int W,
+                      float *__restrict__ partial) {
+  // dz has DZS channels per pixel, of which the first COUTP are this layer's
+  constexpr int RH = TILE_H + 2, RW = TILE_W + 2;
+  constexpr int NT = COUTP * (CINP / 4);  // active threads
+  static_assert(NT <= 256, "too many outputs");
+  __shared__ float sx[RH * RW][CINP + 1];
+  __shared__ float sd[TILE_H * TILE_W][COUTP + 1];
+  const int tid = threadIdx.x;
+  const int co = tid / (CINP / 4), c4 = (tid % (CINP / 4)) * 4;
+  float acc[9][4];
+  float accb = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+  const int tiles_x = W / TILE_W, tiles_y = H / TILE_H;
+  const long long ntiles = (long long)tiles_x * tiles_y * N;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = (int)(tile / ((long long)tiles_x * tiles_y));
+    const int rem = (int)(tile - (long long)n * tiles_x * tiles_y);
+    const int y0 = (rem / tiles_x) * TILE_H, x0 = (rem % tiles_x) * TILE_W;
+    const long long img = (long long)n * H * W;
+    __syncthreads();
+    for (int k = tid; k < RH * RW * CINP; k += 256) {
+      const int pix = k / CINP, c = k - pix * CINP;
+      const int r = pix / RW, cc = pix - r * RW;
+      int gy = y0 + r - 1, gx = x0 + cc - 1;
+      gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
+      gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
+      sx[pix][c] = __bfloat162float(x[(img + (long long)gy * W + gx) * CINP + c]);
+    }
+    for (int k = tid; k < TILE_H * TILE_W * COUTP; k += 256) {
+      const int pix = k / COUTP, c = k - pix * COUTP;
+      const int r = pix / TILE_W, cc = pix - r * TILE_W;
+      sd[pix][c] = __bfloat162float(dz[(img + (long long)(y0 + r) * W + x0 + cc) * DZS + c]);
+    }
+    __syncthreads();
+    if (tid < NT) {
+      for (int p = 0; p < TILE_H * TILE_W; ++p) {
+        const int r = p / TILE_W, c = p - r * TILE_W;
+        const float d = sd[p][co];
+        accb += d;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const float *xr = sx[(r + tap / 3) * RW + c + tap % 3] + c4;
+          acc[tap][0] += d * xr[0];
+          acc[tap][1] += d * xr[1];
+          acc[tap][2] += d * xr[2];
+          acc[tap][3] += d * xr[3];
+        }
+      }
+    }
+  }
+  if (tid < NT) {
+    float *out = partial + (size_t)blockIdx.x * (COUTP * 9 * CINP + COUTP);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out[(co * 9 + tap) * CINP + c4 + k] = acc[tap][k];
+    if (c4 == 0) out[COUTP * 9 * CINP + co] = accb;
+  }
+}
+
+// Sums the per-CTA partials in a fixed order into the padded weight (KS
+// stride) and bias gradients.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ partial, int nparts, int cinp,
+                                    int coutp, int ks, float *__restrict__ gw, float *__restrict__ gb) {
+  const int per = coutp * 9 * cinp + coutp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * per + i];
+  if (i < coutp * 9 * cinp) {
+    const int co = i / (9 * cinp), k = i - co * 9 * cinp;
+    gw[co * ks + k] = (float)s;
+  } else {
+    gb[i - coutp * 9 * cinp] = (float)s;
+  }
+}
+
+// raw FP32 state [p][4] -> normalised BF16 input [p][16] (channels 4..15 zero)
+__global__ void normalise_kernel(const float *__restrict__ x, long long P, const float *__restrict__ nrm,
+                                 bf16 *__restrict__ out) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  __align__(16) bf16 v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = __float2bfloat16((x[p * 4 + c] - nrm[c]) / nrm[4 + c]);
+  uint4 *o = reinterpret_cast<uint4 *>(out + p * 16);
+  o[0] = reinterpret_cast<uint4 *>(v)[0];
+  o[1] = reinterpret_cast<uint4 *>(v)[1];
+}
+
+// MSE of the network output y [p][8] (4 used) against (x1 - x0) / out_std;
+// writes the gradient dL/dy as BF16 [p][16] and per-block partial sums.
+__global__ void __launch_bounds__(256)
+    mse_kernel(const float *__restrict__ y, const float *__restrict__ x0, const float *__restrict__ x1,
+               long long P, const float *__restrict__ nrm, bf16 *__restrict__ dz, double *__restrict__ part) {
+  __shared__ double red[256];
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const double inv = 1.0 / (4.0 * (double)P);
+  double acc = 0.0;
+  if (p < P) {
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float target = (x1[p * 4 + c] - x0[p * 4 + c]) / nrm[8 + c];
+      const float e = y[p * 8 + c] - target;
+      acc += (double)e * e;
+      v[c] = __float2bfloat16((float)(2.0 * inv) * e);
+    }
+    uint4 *o = reinterpret_cast<uint4 *>(dz + p * 16);
+    o[0] = reinterpret_cast<uint4 *>(v)[0];
+    o[1] = reinterpret_cast<uint4 *>(v)[1];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0] * inv;
+}
+
+// x1 = x0 + y * out_std (prediction of the state after one window)
+__global__ void predict_kernel(const float *__restrict__ y, const float *__restrict__ x0, long long P,
+                               const float *__restrict__ nrm, float *__restrict__ x1) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) x1[p * 4 + c] = x0[p * 4 + c] + y[p * 8 + c] * nrm[8 + c];
+}
+
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long long n, float lr, float b1, float b2,
+                            float c1, float c2, float eps) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void cast_kernel(const float *__restrict__ a, bf16 *__restrict__ b, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+
+// transposed, tap-flipped copy for the backward data pass:
+// wt[ci][tap'][co] = w[co][tap][ci], tap' = 8 - tap, co padded to cinp_t
+__global__ void transpose_kernel(const float *__restrict__ w, int cinp, int coutp, int ks, int cinp_t,
+                                 int ks_t, bf16 *__restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cinp * ks_t) return;
+  const int ci = i / ks_t, k = i - ci * ks_t;
+  float v = 0.f;
+  if (k < 9 * cinp_t) {
+    const int tap = k / cinp_t, co = k - tap * cinp_t;
+    if (co < coutp) v = w[co * ks + (8 - tap) * cinp + ci];
+  }
+  wt[i] = __float2bfloat16(v);
+}
+
+// n, phi, u* of a lattice (FP64 staging) -> state [p][4] = (phi, ux, uy, n - 1)
+__global__ void state_from_staging_kernel(const double *__restrict__ stg, long long S,
+                                          float *__restrict__ x) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  x[s * 4 + 0] = (float)stg[S + s];
+  x[s * 4 + 1] = (float)stg[2 * S + s];
+  x[s * 4 + 2] = (float)stg[3 * S + s];
+  x[s * 4 + 3] = (float)(stg[s] - 1.0);
+}
+
+// predicted state -> FP64 staging (n, phi, ux, uy); optionally shifts phi so
+// that sum phi equals `target_sum` (mass correction by a uniform shift)
+__global__ void staging_from_state_kernel(const float *__restrict__ x, long long S, double shift,
+                                          double *__restrict__ stg) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  stg[s] = 1.0 + (double)x[s * 4 + 3];
+  stg[S + s] = (double)x[s * 4 + 0] - shift;
+  stg[2 * S + s] = (double)x[s * 4 + 1];
+  stg[3 * S + s] = (double)x[s * 4 + 2];
+}
+
+// |phi| <= cap on the predicted state (the bulk value of the state the
+// window starts from bounds phi under the Cahn-Hilliard dynamics)
+__global__ void clamp_phi_kernel(float *__restrict__ x, long long S, float cap) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < S) x[s * 4] = fminf(fmaxf(x[s * 4], -cap), cap);
+}
+
+// per-block partials of sum phi, sum |phi|, max |phi|, max |u| over a state
+__global__ void __launch_bounds__(256)
+    state_stats_kernel(const float *__restrict__ x, long long S, double *__restrict__ part) {
+  __shared__ double r[4][256];
+  double sp = 0, sa = 0, mp = 0, mu = 0;
+  for (long long s = blockIdx.x * 256LL + threadIdx.x; s < S; s += (long long)gridDim.x * 256) {
+    const double ph = x[s * 4], ux = x[s * 4 + 1], uy = x[s * 4 + 2];
+    sp += ph;
+    sa += fabs(ph);
+    mp = fmax(mp, fabs(ph));
+    mu = fmax(mu, sqrt(ux * ux + uy * uy));
+    if (!isfinite(ph) || !isfinite(ux) || !isfinite(uy)) mp = INFINITY;
+  }
+  r[0][threadIdx.x] = sp;
+  r[1][threadIdx.x] = sa;
+  r[2][threadIdx.x] = mp;
+  r[3][threadIdx.x] = mu;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      r[0][threadIdx.x] += r[0][threadIdx.x + k];
+      r[1][threadIdx.x] += r[1][threadIdx.x + k];
+      r[2][threadIdx.x] = fmax(r[2][threadIdx.x], r[2][threadIdx.x + k]);
+      r[3][threadIdx.x] = fmax(r[3][threadIdx.x], r[3][threadIdx.x + k]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = r[threadIdx.x][0];
+}
+
+struct Layer {
+  int cin, cout, cinp, coutp, ks, cinp_t, ks_t;
+  size_t woff, boff, wtoff;
+};
+
+unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+namespace hlbm {
+int queue_moments_for(lbm_handle *h);
+}
+
+struct lbm_net {
+  int C = 32, layers = 6;
+  std::vector<Layer> L;
+  size_t nw = 0, nb = 0, nwt = 0;
+  float *w32 = nullptr, *b32 = nullptr, *gw = nullptr, *gb = nullptr;
+  float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
+  bf16 *wbf = nullptr, *wtbf = nullptr;
+  float *nrm = nullptr;  // in_mean[4], in_std[4], out_std[4]
+  float hnrm[12];
+  long long cap = 0;     // pixels the workspace holds
+  bf16 *act[8] = {nullptr};
+  float *yout = nullptr, *x0 = nullptr, *x1 = nullptr;
+  bf16 *dz[2] = {nullptr, nullptr};
+  float *partial = nullptr;
+  double *dpart = nullptr;
+  int wgrad_ctas = 0;
+  long long adam_t = 0;
+  std::string msg;
+};
+
+namespace {
+
+thread_local std::string g_net_error;
+
+int nfail(lbm_net *net, int code, const std::string &m) {
+  if (net) net->msg = m;
+  else g_net_error = m;
+  return code;
+}
+
+#define NCK(net, call, what)                                                   \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return nfail(net, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, \
+                   std::string(what) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+int ensure_workspace(lbm_net *net, long long P) {
+  if (P <= net->cap) return LBM_OK;
+  for (auto &a : net->act) if (a) cudaFree(a);
+  for (auto &d : net->dz) if (d) cudaFree(d);
+  cudaFree(net->yout);
+  cudaFree(net->x0);
+  cudaFree(net->x1);
+  cudaFree(net->dpart);
+  for (auto &a : net->act) a = nullptr;
+  for (int l = 0; l < net->layers; l++) {
+    const int ch = net->L[l].cinp;
+    NCK(net, cudaMalloc(&net->act[l], sizeof(bf16) * ch * P), "cudaMalloc");
+  }
+  NCK(net, cudaMalloc(&net->yout, sizeof(float) * 8 * P), "cudaMalloc");
+  NCK(net, cudaMalloc(&net->x0, sizeof(float) * 4 * P), "cudaMalloc");
+  NCK(net, cudaMalloc(&net->x1, sizeof(float) * 4 * P), "cudaMalloc");
+  for (auto &d : net->dz) NCK(net, cudaMalloc(&d, sizeof(bf16) * std::max(net->C, 16) * P), "cudaMalloc");
+  NCK(net, cudaMalloc(&net->dpart, sizeof(double) * (nblk(P, 256) + 4096)), "cudaMalloc");
+  net->cap = P;
+  return LBM_OK;
+}
+
+template <int CINP, int COUTP, int EPI>
+cudaError_t conv(const bf16 *in, const bf16 *w, const float *bias, const bf16 *mask, int N, int H,
+                 int W, bf16 *ob, float *of, cudaStream_t s) {
+  dim3 grid(W / TILE_W, H / TILE_H, N);
+  conv_mma_kernel<CINP, COUTP, EPI><<<grid, 256, 0, s>>>(in, w, bias, mask, H, W, ob, of);
+  return cudaGetLastError();
+}
+
+// dispatch on the padded channel counts used by the network (C = 32 or 16)
+cudaError_t conv_any(int cinp, int coutp, int epi, const bf16 *in, const bf16 *w, const float *bias,
+                     const bf16 *mask, int N, int H, int W, bf16 *ob, float *of, cudaStream_t s) {
+#define CASE(CI, CO, E)                                               \
+  if (cinp == CI && coutp == CO && epi == E)                          \
+    return conv<CI, CO, E>(in, w, bias, mask, N, H, W, ob, of, s);
+  CASE(16, 32, EPI_RELU) CASE(32, 32, EPI_RELU) CASE(32, 8, EPI_LINEAR_F32)
+  CASE(16, 16, EPI_RELU) CASE(16, 8, EPI_LINEAR_F32)
+  CASE(16, 32, EPI_MASK) CASE(32, 32, EPI_MASK) CASE(16, 16, EPI_MASK)
+#undef CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t wgrad_any(int cinp, int coutp, int dzs, const bf16 *x, const bf16 *dz, int N, int H,
+                      int W, float *partial, int ctas, cudaStream_t s) {
+#define CASE(CI, CO, DS)                                                               \
+  if (cinp == CI && coutp == CO && dzs == DS) {                                        \
+    conv_wgrad_kernel<CI, CO, DS><<<ctas, 256, 0, s>>>(x, dz, N, H, W, partial);       \
+    return cudaGetLastError();                                                         \
+  }
+  CASE(16, 32, 32) CASE(32, 32, 32) CASE(32, 8, 16) CASE(16, 16, 16) CASE(16, 8, 16)
+#undef CASE
+  return cudaErrorInvalidValue;
+}
+
+int refresh_bf16(lbm_net *net, cudaStream_t s) {
+  cast_kernel<<<nblk(net->nw, 256), 256, 0, s>>>(net->w32, net->wbf, (long long)net->nw);
+  NCK(net, cudaGetLastError(), "cast kernel");
+  for (const Layer &l : net->L) {
+    if (l.wtoff == (size_t)-1) continue;
+    transpose_kernel<<<nblk((long long)l.cinp * l.ks_t, 256), 256, 0, s>>>(
+        net->w32 + l.woff, l.cinp, l.coutp, l.ks, l.cinp_t, l.ks_t, net->wtbf + l.wtoff);
+    NCK(net, cudaGetLastError(), "transpose kernel");
+  }
+  return LBM_OK;
+}
+
+int check_shape(lbm_net *net, int N, int H, int W) {
+  if (N < 1 || H < TILE_H || W < TILE_W || H % TILE_H || W % TILE_W)
+    return nfail(net, LBM_EINVAL, "N >= 1, H a multiple of 8 and W a multiple of 16 are required");
+  return LBM_OK;
+}
+
+// forward pass on net->x0 (raw state, P pixels) -> net->yout
+int forward_raw(lbm_net *net, int N, int H, int W, cudaStream_t s) {
+  const long long P = (long long)N * H * W;
+  normalise_kernel<<<nblk(P, 256), 256, 0, s>>>(net->x0, P, net->nrm, net->act[0]);
+  NCK(net, cudaGetLastError(), "normalise kernel");
+  for (int l = 0; l < net->layers; l++) {
+    const Layer &Ly = net->L[l];
+    const bool last = l == net->layers - 1;
+    NCK(net, conv_any(Ly.cinp, Ly.coutp, last ? EPI_LINEAR_F32 : EPI_RELU, net->act[l],
+                      net->wbf + Ly.woff, net->b32 + Ly.boff, nullptr, N, H, W,
+                      last ? nullptr : net->act[l + 1], last ? net->yout : nullptr, s),
+        "conv forward");
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_net_create(int channels, int layers, unsigned long long seed, lbm_net **out) {
+  if (!out) return nfail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if ((channels != 16 && channels != 32) || layers < 2 || layers > 8)
+    return nfail(nullptr, LBM_EINVAL, "channels must be 16 or 32 and layers 2..8");
+  lbm_net *net = new lbm_net();
+  net->C = channels;
+  net->layers = layers;
+  size_t wo = 0, bo = 0, wto = 0;
+  for (int l = 0; l < layers; l++) {
+    Layer Ly;
+    Ly.cin = l == 0 ? 4 : channels;
+    Ly.cout = l == layers - 1 ? 4 : channels;
+    Ly.cinp = l == 0 ? 16 : channels;
+    Ly.coutp = l == layers - 1 ? 8 : channels;
+    Ly.ks = 9 * Ly.cinp + 8;
+    Ly.cinp_t = std::max(16, Ly.coutp);
+    Ly.ks_t = 9 * Ly.cinp_t + 8;
+    Ly.woff = wo;
+    Ly.boff = bo;
+    Ly.wtoff = l == 0 ? (size_t)-1 : wto;  // the input needs no gradient
+    wo += (size_t)Ly.coutp * Ly.ks;
+    bo += Ly.coutp;
+    if (l > 0) wto += (size_t)Ly.cinp * Ly.ks_t;
+    net->L.push_back(Ly);
+  }
+  net->nw = wo;
+  net->nb = bo;
+  net->nwt = wto;
+  auto bail = [&](int code) {
+    g_net_error = net->msg;
+    lbm_net_free(net);
+    return code;
+  };
+  float **f32s[] = {&net->w32, &net->gw, &net->mw, &net->vw};
+  for (float **p : f32s)
+    if (cudaMalloc(p, sizeof(float) * wo) != cudaSuccess || cudaMemset(*p, 0, sizeof(float) * wo))
+      return bail(nfail(net, LBM_ENOMEM, "cudaMalloc"));
+  float **b32s[] = {&net->b32, &net->gb, &net->mb, &net->vb};
+  for (float **p : b32s)
+    if (cudaMalloc(p, sizeof(float) * bo) != cudaSuccess || cudaMemset(*p, 0, sizeof(float) * bo))
+      return bail(nfail(net, LBM_ENOMEM, "cudaMalloc"));
+  if (cudaMalloc(&net->wbf, sizeof(bf16) * wo) != cudaSuccess ||
+      cudaMalloc(&net->wtbf, sizeof(bf16) * std::max<size_t>(wto, 8)) != cudaSuccess ||
+      cudaMalloc(&net->nrm, sizeof(float) * 12) != cudaSuccess)
+    return bail(nfail(net, LBM_ENOMEM, "cudaMalloc"));
+  // He-normal initial weights (the last layer scaled by 0.1), zero biases
+  std::vector<float> hw(wo, 0.f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < layers; l++) {
+    const Layer &Ly = net->L[l];
+    std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (9.f * Ly.cin)) * (l == layers - 1 ? 0.1f : 1.f));
+    for (int co = 0; co < Ly.cout; co++)
+      for (int tap = 0; tap < 9; tap++)
+        for (int ci = 0; ci < Ly.cin; ci++) hw[Ly.woff + (size_t)co * Ly.ks + tap * Ly.cinp + ci] = nd(rng);
+  }
+  if (cudaMemcpy(net->w32, hw.data(), sizeof(float) * wo, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(nfail(net, LBM_ECUDA, "host-to-device copy"));
+  const float unit[12] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1};
+  std::memcpy(net->hnrm, unit, sizeof unit);
+  if (cudaMemcpy(net->nrm, unit, sizeof unit, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(nfail(net, LBM_ECUDA, "host-to-device copy"));
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  net->wgrad_ctas = 2 * sms;
+  const size_t per = (size_t)channels * 9 * channels + channels;
+  if (cudaMalloc(&net->partial, sizeof(float) * per * net->wgrad_ctas) != cudaSuccess)
+    return bail(nfail(net, LBM_ENOMEM, "cudaMalloc"));
+  if (refresh_bf16(net, 0)) return bail(LBM_ECUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(nfail(net, LBM_ECUDA, "initialisation"));
+  *out = net;
+  return LBM_OK;
+}
+
+long long lbm_net_param_count(const lbm_net *net) {
+  if (!net) return -1;
+  long long n = 0;
+  for (const Layer &l : net->L) n += (long long)l.cout * 9 * l.cin + l.cout;
+  return n;
+}
+
+static int net_params_io(lbm_net *net, float *host, long long n, int set, bool grads) {
+  if (!net || !host) return LBM_EINVAL;
+  if (n != lbm_net_param_count(net)) return nfail(net, LBM_EINVAL, "wrong parameter count");
+  std::vector<float> w(net->nw), b(net->nb);
+  float *dw = grads ? net->gw : net->w32, *db = grads ? net->gb : net->b32;
+  NCK(net, cudaDeviceSynchronize(), "synchronize");
+  NCK(net, cudaMemcpy(w.data(), dw, sizeof(float) * net->nw, cudaMemcpyDeviceToHost), "copy");
+  NCK(net, cudaMemcpy(b.data(), db, sizeof(float) * net->nb, cudaMemcpyDeviceToHost), "copy");
+  long long k = 0;
+  for (const Layer &l : net->L) {
+    for (int co = 0; co < l.cout; co++)
+      for (int tap = 0; tap < 9; tap++)
+        for (int ci = 0; ci < l.cin; ci++) {
+          float &slot = w[l.woff + (size_t)co * l.ks + tap * l.cinp + ci];
+          if (set) slot = host[k]; else host[k] = slot;
+          k++;
+        }
+    for (int co = 0; co < l.cout; co++) {
+      float &slot = b[l.boff + co];
+      if (set) slot = host[k]; else host[k] = slot;
+      k++;
+    }
+  }
+  if (set) {
+    NCK(net, cudaMemcpy(dw, w.data(), sizeof(float) * net->nw, cudaMemcpyHostToDevice), "copy");
+    NCK(net, cudaMemcpy(db, b.data(), sizeof(float) * net->nb, cudaMemcpyHostToDevice), "copy");
+    if (!grads) {
+      int rc = refresh_bf16(net, 0);
+      if (rc) return rc;
+      NCK(net, cudaDeviceSynchronize(), "synchronize");
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_net_params(lbm_net *net, float *host, long long n, int set) {
+  return net_params_io(net, host, n, set, false);
+}
+
+int lbm_net_grads(lbm_net *net, float *host, long long n) {
+  return net_params_io(net, host, n, 0, true);
+}
+
+int lbm_net_set_normalisation(lbm_net *net, const float *in_mean, const float *in_std,
+                              const float *out_std) {
+  if (!net || !in_mean || !in_std || !out_std) return LBM_EINVAL;
+  for (int c = 0; c < 4; c++) {
+    if (!(in_std[c] > 0.f) || !(out_std[c] > 0.f)) return nfail(net, LBM_EINVAL, "std must be > 0");
+    net->hnrm[c] = in_mean[c];
+    net->hnrm[4 + c] = in_std[c];
+    net->hnrm[8 + c] = out_std[c];
+  }
+  NCK(net, cudaMemcpy(net->nrm, net->hnrm, sizeof(float) * 12, cudaMemcpyHostToDevice), "copy");
+  return LBM_OK;
+}
+
+int lbm_net_normalisation(const lbm_net *net, float *out12) {
+  if (!net || !out12) return LBM_EINVAL;
+  std::memcpy(out12, net->hnrm, sizeof(float) * 12);
+  return LBM_OK;
+}
+
+int lbm_net_forward(lbm_net *net, const float *x0, int N, int H, int W, float *x1, void *cuda_stream) {
+  if (!net || !x0 || !x1) return LBM_EINVAL;
+  int rc = check_shape(net, N, H, W);
+  if (rc) return rc;
+  const long long P = (long long)N * H * W;
+  rc = ensure_workspace(net, P);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  NCK(net, cudaMemcpyAsync(net->x0, x0, sizeof(float) * 4 * P, cudaMemcpyDeviceToDevice, s), "copy");
+  rc = forward_raw(net, N, H, W, s);
+  if (rc) return rc;
+  predict_kernel<<<nblk(P, 256), 256, 0, s>>>(net->yout, net->x0, P, net->nrm, x1);
+  NCK(net, cudaGetLastError(), "predict kernel");
+  return LBM_OK;
+}
+
+int lbm_net_train_step(lbm_net *net, const float *x0, const float *x1, int N, int H, int W, float lr,
+                       int update, double *loss, void *cuda_stream) {
+  if (!net || !x0 || !x1) return LBM_EINVAL;
+  int rc = check_shape(net, N, H, W);
+  if (rc) return rc;
+  const long long P = (long long)N * H * W;
+  rc = ensure_workspace(net, P);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  NCK(net, cudaMemcpyAsync(net->x0, x0, sizeof(float) * 4 * P, cudaMemcpyDeviceToDevice, s), "copy");
+  rc = forward_raw(net, N, H, W, s);
+  if (rc) return rc;
+  const unsigned nb = nblk(P, 256);
+  mse_kernel<<<nb, 256, 0, s>>>(net->yout, net->x0, x1, P, net->nrm, net->dz[0], net->dpart);
+  NCK(net, cudaGetLastError(), "mse kernel");
+  // backward: dz holds dL/dz of layer l (BF16, cinp_t of layer l channels)
+  int cur = 0;
+  for (int l = net->layers - 1; l >= 0; l--) {
+    const Layer &Ly = net->L[l];
+    // weight and bias gradients of layer l
+    NCK(net, wgrad_any(Ly.cinp, Ly.coutp, Ly.cinp_t, net->act[l], net->dz[cur], N, H, W,
+                       net->partial, net->wgrad_ctas, s),
+        "wgrad");
+    const int per = Ly.coutp * 9 * Ly.cinp + Ly.coutp;
+    wgrad_reduce_kernel<<<nblk(per, 256), 256, 0, s>>>(net->partial, net->wgrad_ctas, Ly.cinp, Ly.coutp,
+                                                      Ly.ks, net->gw + Ly.woff, net->gb + Ly.boff);
+    NCK(net, cudaGetLastError(), "wgrad reduce");
+    if (l == 0) break;
+    // dL/dz of layer l - 1 = (flipped, transposed conv of dz) * relu'(act[l])
+    NCK(net, conv_any(Ly.cinp_t, Ly.cinp, EPI_MASK, net->dz[cur], net->wtbf + Ly.wtoff, nullptr,
+                      net->act[l], N, H, W, net->dz[1 - cur], nullptr, s),
+        "conv backward");
+    cur = 1 - cur;
+  }
+  if (update) {
+    net->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)net->adam_t), c2 = 1.f - std::pow(b2, (float)net->adam_t);
+    adam_kernel<<<nblk(net->nw, 256), 256, 0, s>>>(net->w32, net->gw, net->mw, net->vw, net->nw, lr, b1,
+                                                   b2, c1, c2, 1e-8f);
+    adam_kernel<<<nblk(net->nb, 256), 256, 0, s>>>(net->b32, net->gb, net->mb, net->vb, net->nb, lr, b1,
+                                                   b2, c1, c2, 1e-8f);
+    NCK(net, cudaGetLastError(), "adam kernel");
+    rc = refresh_bf16(net, s);
+    if (rc) return rc;
+  }
+  if (loss) {
+    std::vector<double> part(nb);
+    NCK(net, cudaMemcpyAsync(part.data(), net->dpart, sizeof(double) * nb, cudaMemcpyDeviceToHost, s),
+        "copy");
+    NCK(net, cudaStreamSynchronize(s), "synchronize");
+    double acc = 0.0;
+    for (double v : part) acc += v;
+    *loss = acc;
+  }
+  return LBM_OK;
+}
+
+// The network's state (FP32 [S][4]: phi, u*_x, u*_y, n - 1) of a 2D lattice
+// at its current time; `out` is a device pointer.
+int lbm_surrogate_state(lbm_handle *h, float *out) {
+  if (!h || !out) return LBM_EINVAL;
+  if (h->err) return h->err;
+  if (!h->inited || h->dims != 2) return LBM_ESTATE;
+  int rc = hlbm::queue_moments_for(h);
+  if (rc) return rc;
+  state_from_staging_kernel<<<nblk(h->S, 256), 256, 0, h->stream>>>(h->staging, h->S, out);
+  if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+  return LBM_OK;
+}
+
+int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_steps,
+                          double mass_tol, int conserve_mass, double phi_clamp, int *fallbacks) {
+  if (!h || !net || windows < 0 || window_steps < 1) return LBM_EINVAL;
+  if (h->err) return h->err;
+  if (!h->inited || h->dims != 2) return LBM_ESTATE;
+  if (h->P.force_steps > h->t) return nfail(net, LBM_EINVAL, "the surrogate needs the body force off");
+  int rc = check_shape(net, 1, h->P.Ly, h->P.Lx);
+  if (rc) return rc;
+  const long long S = h->S;
+  rc = ensure_workspace(net, S);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  const int sb = 512;
+  int nfb = 0;
+  for (int w = 0; w < windows; w++) {
+    rc = lbm_surrogate_state(h, net->x0);
+    if (rc) return rc;
+    rc = forward_raw(net, 1, h->P.Ly, h->P.Lx, s);
+    if (rc) return rc;
+    predict_kernel<<<nblk(S, 256), 256, 0, s>>>(net->yout, net->x0, S, net->nrm, net->x1);
+    NCK(net, cudaGetLastError(), "surrogate kernels");
+    double st[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    std::vector<double> part(4 * sb);
+    for (int k = 0; k < 2; k++) {
+      state_stats_kernel<<<sb, 256, 0, s>>>(k == 0 ? net->x0 : net->x1, S, net->dpart);
+      NCK(net, cudaGetLastError(), "surrogate kernels");
+      NCK(net, cudaMemcpyAsync(part.data(), net->dpart, sizeof(double) * 4 * sb,
+                               cudaMemcpyDeviceToHost, s),
+          "copy");
+      NCK(net, cudaStreamSynchronize(s), "synchronize");
+      for (int b = 0; b < sb; b++) {
+        const double *q = &part[b * 4];
+        st[k][0] += q[0];
+        st[k][1] += q[1];
+        st[k][2] = std::max(st[k][2], q[2]);
+        st[k][3] = std::max(st[k][3], q[3]);
+      }
+      if (k == 0 && phi_clamp > 0.0) {
+        clamp_phi_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, (float)(phi_clamp * st[0][2]));
+        NCK(net, cudaGetLastError(), "clamp kernel");
+      }
+    }
+    // residual check: the mean change of phi per site, and bounds on |phi| and
+    // |u*| relative to the state the window starts from (an unbounded or
+    // runaway prediction fails them)
+    const double drift = std::fabs(st[1][0] - st[0][0]) / (double)S;
+    const double phi_cap = std::max(1.1 * h->phi0, 1.05 * st[0][2]);
+    const double u_cap = std::max(1.5 * st[0][3], 0.01 / std::sqrt(3.0));
+    const bool ok = std::isfinite(st[1][2]) && std::isfinite(st[1][3]) && drift <= mass_tol &&
+                    st[1][2] <= phi_cap && st[1][3] <= u_cap;
+    if (std::getenv("HLBM_SURROGATE_VERBOSE"))
+      std::fprintf(stderr,
+                   "hlbm surrogate t=%lld mean dphi %.3e max|phi| %.4f (state %.4f) max|u| %.3e "
+                   "(state %.3e) -> %s\n",
+                   h->t, drift, st[1][2], st[0][2], st[1][3], st[0][3], ok ? "accepted" : "plain steps");
+    if (ok) {
+      const double shift = conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0;
+      staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift, h->staging);
+      NCK(net, cudaGetLastError(), "staging kernel");
+      if (launch_init(h, h->cur) != cudaSuccess) return LBM_ECUDA;
+      h->t += window_steps;
+    } else {
+      nfb++;
+      rc = lbm_step(h, window_steps);
+      if (rc) return rc;
+    }
+  }
+  if (fallbacks) *fallbacks = nfb;
+  NCK(net, cudaStreamSynchronize(s), "synchronize");
+  return LBM_OK;
+}
+
+void lbm_net_free(lbm_net *net) {
+  if (!net) return;
+  cudaDeviceSynchronize();
+  void *ptrs[] = {net->w32, net->b32, net->gw, net->gb, net->mw, net->vw, net->mb, net->vb, net->wbf,
+                  net->wtbf, net->nrm, net->yout, net->x0, net->x1, net->dz[0], net->dz[1],
+                  net->partial, net->dpart};
+  for (void *p : ptrs) if (p) cudaFree(p);
+  for (auto &a : net->act) if (a) cudaFree(a);
+  delete net;
+}
+
+const char *lbm_net_last_error(const lbm_net *net) {
+  return net ? net->msg.c_str() : g_net_error.c_str();
+}
+
+}  // extern "C"

@@ -32,7 +32,10 @@ EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_popu
            "lbm_load", "lbm_free", "lbm_last_error", "lbm_tuning", "lbm_diagnostics_noalloc",
            "lbm_noalloc_last_error", "lbm_batch_create", "lbm_batch_init_fields",
            "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_graphs", "lbm_batch_shape",
-           "lbm_batch_synchronize", "lbm_batch_free", "lbm_batch_last_error")
+           "lbm_batch_synchronize", "lbm_batch_free", "lbm_batch_last_error", "lbm_net_create",
+           "lbm_net_param_count", "lbm_net_params", "lbm_net_grads", "lbm_net_set_normalisation",
+           "lbm_net_normalisation", "lbm_net_forward", "lbm_net_train_step", "lbm_surrogate_state",
+           "lbm_surrogate_advance", "lbm_net_free", "lbm_net_last_error")
 
 
 class c_lbm_params(ctypes.Structure):
@@ -121,6 +124,29 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_batch_free.restype = None
     lib.lbm_batch_last_error.argtypes = [B]
     lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    Nt = ctypes.c_void_p
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.lbm_net_create.argtypes = [ip, ip, ctypes.c_ulonglong, ctypes.POINTER(Nt)]
+    lib.lbm_net_param_count.argtypes = [Nt]
+    lib.lbm_net_param_count.restype = ctypes.c_longlong
+    lib.lbm_net_params.argtypes = [Nt, fp, ctypes.c_longlong, ip]
+    lib.lbm_net_grads.argtypes = [Nt, fp, ctypes.c_longlong]
+    lib.lbm_net_set_normalisation.argtypes = [Nt, fp, fp, fp]
+    lib.lbm_net_normalisation.argtypes = [Nt, fp]
+    lib.lbm_net_forward.argtypes = [Nt, vp, ip, ip, ip, vp, vp]
+    lib.lbm_net_train_step.argtypes = [Nt, vp, vp, ip, ip, ip, ctypes.c_float, ip,
+                                       ctypes.POINTER(ctypes.c_double), vp]
+    lib.lbm_surrogate_state.argtypes = [H, vp]
+    lib.lbm_surrogate_advance.argtypes = [H, Nt, ip, ip, ctypes.c_double, ip, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_net_free.argtypes = [Nt]
+    lib.lbm_net_free.restype = None
+    lib.lbm_net_last_error.argtypes = [Nt]
+    lib.lbm_net_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_net_create", "lbm_net_params", "lbm_net_grads", "lbm_net_set_normalisation",
+                 "lbm_net_normalisation", "lbm_net_forward", "lbm_net_train_step",
+                 "lbm_surrogate_state", "lbm_surrogate_advance"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_moments",
                  "lbm_batch_set_graphs", "lbm_batch_shape", "lbm_batch_synchronize"):
         getattr(lib, name).restype = ctypes.c_int
@@ -452,3 +478,93 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Net:
+    """Owning wrapper around one lbm_net (the learned surrogate).  Device
+    arrays are passed as integer pointers (e.g. torch.Tensor.data_ptr())."""
+
+    def __init__(self, channels=32, layers=6, seed=0):
+        lib = load_library()
+        self.handle = ctypes.c_void_p()
+        rc = lib.lbm_net_create(int(channels), int(layers), int(seed), ctypes.byref(self.handle))
+        if rc != LBM_OK:
+            self.handle = None
+            raise LbmError(rc, lib.lbm_net_last_error(None).decode())
+        self.channels, self.layers = channels, layers
+
+    def _check(self, rc, what):
+        if rc != LBM_OK:
+            raise LbmError(rc, what + ": " + load_library().lbm_net_last_error(self.handle).decode())
+
+    @property
+    def nparams(self):
+        return load_library().lbm_net_param_count(self.handle)
+
+    def get_params(self):
+        a = np.empty(self.nparams, dtype=np.float32)
+        self._check(load_library().lbm_net_params(self.handle, a.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), a.size, 0), "lbm_net_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        self._check(load_library().lbm_net_params(self.handle, a.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), a.size, 1), "lbm_net_params")
+
+    def get_grads(self):
+        a = np.empty(self.nparams, dtype=np.float32)
+        self._check(load_library().lbm_net_grads(self.handle, a.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), a.size), "lbm_net_grads")
+        return a
+
+    def set_normalisation(self, in_mean, in_std, out_std):
+        arrs = [np.ascontiguousarray(v, dtype=np.float32) for v in (in_mean, in_std, out_std)]
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in arrs]
+        self._check(load_library().lbm_net_set_normalisation(self.handle, *ptrs),
+                    "lbm_net_set_normalisation")
+
+    def normalisation(self):
+        a = np.empty(12, dtype=np.float32)
+        self._check(load_library().lbm_net_normalisation(self.handle, a.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float))), "lbm_net_normalisation")
+        return a[:4], a[4:8], a[8:]
+
+    def forward(self, x0_ptr, N, H, W, x1_ptr, stream=None):
+        self._check(load_library().lbm_net_forward(self.handle, ctypes.c_void_p(x0_ptr), N, H, W,
+                                                   ctypes.c_void_p(x1_ptr),
+                                                   ctypes.c_void_p(stream or 0)), "lbm_net_forward")
+
+    def train_step(self, x0_ptr, x1_ptr, N, H, W, lr, update=True, stream=None):
+        loss = ctypes.c_double()
+        self._check(load_library().lbm_net_train_step(
+            self.handle, ctypes.c_void_p(x0_ptr), ctypes.c_void_p(x1_ptr), N, H, W, float(lr),
+            int(update), ctypes.byref(loss), ctypes.c_void_p(stream or 0)), "lbm_net_train_step")
+        return loss.value
+
+    def close(self):
+        if self.handle:
+            load_library().lbm_net_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_surrogate_state(h, out_ptr):
+    _check(h, load_library().lbm_surrogate_state(h, ctypes.c_void_p(out_ptr)), "lbm_surrogate_state")
+
+
+def lbm_surrogate_advance(h, net: Net, windows, window_steps, mass_tol=2e-3, conserve_mass=True,
+                          phi_clamp=0.0):
+    fb = ctypes.c_int()
+    rc = load_library().lbm_surrogate_advance(h, net.handle, int(windows), int(window_steps),
+                                              float(mass_tol), int(conserve_mass), float(phi_clamp),
+                                              ctypes.byref(fb))
+    if rc != LBM_OK:
+        msg = load_library().lbm_net_last_error(net.handle).decode() or lbm_last_error(h)
+        raise LbmError(rc, "lbm_surrogate_advance: " + msg)
+    return fb.value

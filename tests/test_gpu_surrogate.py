@@ -1,0 +1,196 @@
+"""GPU checks of the learned surrogate's kernels against the FP64 reference
+(oracle/surrogate.py): forward pass, gradients, one Adam step, and the
+coupling to a lattice (state packing, fallback to the plain scheme).
+BF16 weights and activations: relative errors of about 1e-2 are expected."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as OS
+from paper_0902_3921_gb300 import inputs as I
+from paper_0902_3921_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_0902_3921_gb300 import build as B
+    B.build()
+    lbm.load_library()
+
+
+def _layers(C, L):
+    chans = [4] + [C] * (L - 1) + [4]
+    return list(zip(chans[:-1], chans[1:]))
+
+
+def _flat_to_params(flat, C, L):
+    params, k = [], 0
+    for ci, co in _layers(C, L):
+        W = flat[k:k + co * 9 * ci].reshape(co, 3, 3, ci).astype(np.float64)
+        k += co * 9 * ci
+        b = flat[k:k + co].astype(np.float64)
+        k += co
+        params.append((W, b))
+    return params
+
+
+def _params_to_flat(params):
+    return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in params]).astype(np.float32)
+
+
+def _random_net(C=32, L=6, seed=0):
+    rng = np.random.default_rng(seed)
+    params = []
+    for ci, co in _layers(C, L):
+        params.append((rng.standard_normal((co, 3, 3, ci)) * np.sqrt(2.0 / (9 * ci)),
+                       0.05 * rng.standard_normal(co)))
+    net = lbm.Net(C, L, seed=1)
+    net.set_params(_params_to_flat(params))
+    # the reference uses the BF16-rounded weights the GPU multiplies with
+    rounded = torch.from_numpy(_params_to_flat(params)).to(torch.bfloat16).float().numpy()
+    return net, _flat_to_params(rounded.astype(np.float64), C, L)
+
+
+NORM = (np.array([0.01, 0.0, 0.0, 0.0]), np.array([0.6, 2e-3, 2e-3, 3e-3]),
+        np.array([0.05, 1e-3, 1e-3, 1e-3]))
+
+
+def _inputs(N, H, W, seed):
+    rng = np.random.default_rng(seed)
+    x0 = np.stack([0.8 * np.tanh(3 * rng.standard_normal((N, H, W))),
+                   2e-3 * rng.standard_normal((N, H, W)),
+                   2e-3 * rng.standard_normal((N, H, W)),
+                   3e-3 * rng.standard_normal((N, H, W))], axis=-1)
+    x1 = x0 + np.stack([0.05, 1e-3, 1e-3, 1e-3]) * rng.standard_normal((N, H, W, 4))
+    return x0, x1
+
+
+@pytest.mark.parametrize("C,L", [(32, 6), (16, 3)])
+def test_forward_matches_reference(C, L):
+    net, params = _random_net(C, L)
+    net.set_normalisation(*NORM)
+    x0, _ = _inputs(2, 16, 32, 3)
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.empty_like(d0)
+    net.forward(d0.data_ptr(), 2, 16, 32, d1.data_ptr())
+    torch.cuda.synchronize()
+    xn = (x0 - NORM[0]) / NORM[1]
+    xn = torch.from_numpy(xn).to(torch.bfloat16).double().numpy()  # the GPU's BF16 input
+    y, _, _ = OS.forward(params, xn)
+    ref = x0 + y * NORM[2]
+    got = d1.cpu().numpy()
+    for c in range(4):
+        err = np.max(np.abs(got[..., c] - ref[..., c]))
+        scale = np.max(np.abs(y[..., c] * NORM[2][c]))
+        assert err <= 3e-2 * scale, (c, err, scale)
+    net.close()
+
+
+def test_gradients_and_loss_match_reference():
+    C, L = 32, 6
+    net, params = _random_net(C, L, seed=5)
+    net.set_normalisation(*NORM)
+    x0, x1 = _inputs(2, 16, 32, 4)
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.from_numpy(x1.astype(np.float32)).cuda()
+    loss = net.train_step(d0.data_ptr(), d1.data_ptr(), 2, 16, 32, lr=0.0, update=False)
+    g = _flat_to_params(net.get_grads().astype(np.float64), C, L)
+    xn = torch.from_numpy((x0 - NORM[0]) / NORM[1]).to(torch.bfloat16).double().numpy()
+    target = ((x1.astype(np.float32) - x0.astype(np.float32)) / NORM[2]).astype(np.float64)
+    ref_loss, ref_g = OS.loss_and_grads(params, xn, target)
+    assert loss == pytest.approx(ref_loss, rel=2e-2)
+    for li, ((gw, gb), (rw, rb)) in enumerate(zip(g, ref_g)):
+        ew = np.linalg.norm(gw - rw) / np.linalg.norm(rw)
+        eb = np.linalg.norm(gb - rb) / max(np.linalg.norm(rb), 1e-30)
+        assert ew <= 4e-2 and eb <= 4e-2, (li, ew, eb)
+    net.close()
+
+
+def test_adam_step_matches_reference():
+    C, L = 16, 3
+    net, _ = _random_net(C, L, seed=7)
+    net.set_normalisation(*NORM)
+    x0, x1 = _inputs(1, 8, 16, 9)
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.from_numpy(x1.astype(np.float32)).cuda()
+    w0 = net.get_params().astype(np.float64)
+    net.train_step(d0.data_ptr(), d1.data_ptr(), 1, 8, 16, lr=1e-3, update=True)
+    g = net.get_grads().astype(np.float64)
+    w1 = net.get_params().astype(np.float64)
+    ref, _, _ = OS.adam_step(w0, g, np.zeros_like(g), np.zeros_like(g), t=1, lr=1e-3)
+    np.testing.assert_allclose(w1, ref, rtol=1e-5, atol=1e-7)
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    net = lbm.Net(16, 3, seed=3)
+    net.set_normalisation(*NORM)
+    rng = np.random.default_rng(0)
+    x0 = np.zeros((2, 16, 32, 4))
+    x0[..., 0] = np.tanh(3 * rng.standard_normal((2, 16, 32)))
+    # a learnable change: diffusion of phi by the 5-point Laplacian
+    lap = (np.roll(x0[..., 0], 1, 1) + np.roll(x0[..., 0], -1, 1) + np.roll(x0[..., 0], 1, 2)
+           + np.roll(x0[..., 0], -1, 2) - 4 * x0[..., 0])
+    x1 = x0.copy()
+    x1[..., 0] += 0.02 * lap
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.from_numpy(x1.astype(np.float32)).cuda()
+    losses = [net.train_step(d0.data_ptr(), d1.data_ptr(), 2, 16, 32, lr=3e-3) for _ in range(300)]
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    net.close()
+
+
+def test_surrogate_state_and_fallback():
+    cfg = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    p = lbm.LbmParams(Lx=64, Ly=32, precision=lbm.LBM_F32DEV, fd_substeps=4, **cfg)
+    phi = I.spinodal(2, 64, 32, seed=4, amp=0.1)
+    n, u = I.rest(2, 64, 32)
+    a = lbm.Lattice(p).init_fields(n, phi, u)
+    b = lbm.Lattice(p).init_fields(n, phi, u)
+    a.step(20)
+    b.step(20)
+    x = torch.empty((32, 64, 4), dtype=torch.float32, device="cuda")
+    lbm.lbm_surrogate_state(a.handle, x.data_ptr())
+    a.synchronize()
+    gn, gphi, gu = a.moments()
+    xs = x.cpu().numpy()
+    np.testing.assert_allclose(xs[..., 0], gphi, atol=1e-7)
+    np.testing.assert_allclose(xs[..., 1], gu[0], atol=1e-9)
+    np.testing.assert_allclose(xs[..., 3], gn - 1, atol=1e-7)
+    # an untrained network's predictions fail the residual check (tight mass
+    # tolerance): every window falls back to the plain scheme
+    net = lbm.Net(16, 3, seed=11)
+    net.set_normalisation(*NORM)
+    fb = lbm.lbm_surrogate_advance(a.handle, net, windows=3, window_steps=10, mass_tol=1e-12,
+                                   conserve_mass=False)
+    b.step(30)
+    assert fb == 3 and a.t == b.t == 50
+    for xa, xb in zip(a.moments(), b.moments()):
+        assert np.array_equal(xa, xb)
+    # a network with all-zero parameters predicts "no change": accepted, and
+    # the state keeps its moments (populations rebuilt from them)
+    net.set_params(np.zeros(net.nparams, dtype=np.float32))
+    before = a.moments()
+    fb = lbm.lbm_surrogate_advance(a.handle, net, windows=2, window_steps=50, mass_tol=1e-3)
+    after = a.moments()
+    assert fb == 0 and a.t == 150
+    np.testing.assert_allclose(after[1], before[1], atol=1e-6)
+    net.close()
+
+
+def test_train_and_evaluate_end_to_end():
+    """A short version of the training/evaluation pipeline: the loss falls
+    and the surrogate-advanced lattice keeps its mass and domain size close
+    to the plain scheme's."""
+    from paper_0902_3921_gb300 import surrogate as SG
+    net, hist = SG.train(side=64, lattices=4, generations=1, iters=60, window=50, t_start=2000,
+                         lr=1e-3, channels=16, layers=4)
+    assert hist["loss_last10"] < hist["loss_first"]
+    res = SG.evaluate(net, side=128, seed=7, t_start=2000, checkpoints=(2500, 3000), window=50)
+    last = res["checkpoints"][-1]
+    assert np.isfinite(last["L_surrogate"])
+    assert abs(last["sum_phi_surrogate"] - last["sum_phi_plain"]) <= 0.02 * 128 * 128
+    assert 0.5 < last["L_surrogate"] / last["L_plain"] < 2.0
+    net.close()
