@@ -145,7 +145,8 @@ long long lbm_time(const lbm_handle *h);       /* current LB step t, or -1     *
 /* The launch shapes picked by the autotuner of lbm_create (2D; it times the
  * candidates with CUDA events on the handle's own buffers): writes up to n of
  * {FD substeps per launch, FD output rows per warp, FD columns per lane,
- * collide sites per thread (0: asynchronous shared-memory staging), m, FD
+ * collide sites per thread (0 / 1: asynchronous shared-memory staging sized
+ * for 4 / 3 CTAs per SM), m, FD
  * kernel (0: warp-marching; 32 or 64: shared-memory tile of that width)} into
  * values and returns 6 (EINVAL on NULL).
  * Environment: HLBM_TUNING="sub,rows,cols,collide_rows[,tile]" fixes the shapes

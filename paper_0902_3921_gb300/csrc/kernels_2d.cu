@@ -221,11 +221,13 @@ constexpr size_t collide_async_smem() {
   return sizeof(C) * (9 * CA_TX * CA_TY + (CA_TX + 4) * (CA_TY + 4) + 2 * (CA_TX + 2) * (CA_TY + 2));
 }
 
-template <typename C, bool TGEN, int MODE>
-__global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
+template <typename C, bool TGEN, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     collide2d_async_kernel(const C *__restrict__ hin, C *__restrict__ hout,
                            const C *__restrict__ phi, const C *__restrict__ dn,
                            C *__restrict__ uout, double *__restrict__ stg, KParams<C> p) {
+  // thread (tx, ty) owns column tx, rows 4 ty .. 4 ty + 3 of the 32 x 32 tile,
+  // so the 3 x 3 stencils reuse rows from registers
   constexpr int PX = CA_TX + 4, PY = CA_TY + 4, MX = CA_TX + 2, MY = CA_TY + 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C(*pops)[CA_TY][CA_TX] = reinterpret_cast<C(*)[CA_TY][CA_TX]>(smem_raw);
@@ -235,13 +237,14 @@ __global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
   const int Lx = p.Lx, Ly = p.Ly;
   const long long Sz = (long long)Lx * Ly;
   const int x0 = blockIdx.x * CA_TX, y0 = blockIdx.y * CA_TY;
-  const int tx = threadIdx.x, tid = threadIdx.y * 32 + threadIdx.x;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ly0 = 4 * ty;
   const int x = x0 + tx;
   const int xm = x == 0 ? Lx - 1 : x - 1, xp = x >= Lx - 1 ? 0 : x + 1;
   // 1. every pulled population f_i(r, t) = buf_i(r - e_i) of the tile
 #pragma unroll
   for (int r = 0; r < CA_RY; ++r) {
-    const int ly = threadIdx.y + C2_BY * r, y = y0 + ly;
+    const int ly = ly0 + r, y = y0 + ly;
     if (x >= Lx || y >= Ly) continue;
     const long long rowc = (long long)y * Lx;
     const long long rowm = (long long)(y == 0 ? Ly - 1 : y - 1) * Lx;
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
   }
   // 2. phi on the tile + halo 2 (periodic)
   const bool big = Lx >= PX && Ly >= PY;
-  for (int ry = threadIdx.y; ry < PY; ry += C2_BY) {
+  for (int ry = ty; ry < PY; ry += C2_BY) {
     const int gy = big ? wrap1(y0 + ry - 2, Ly) : wrapi(y0 + ry - 2, Ly);
     const C *prow = phi + (long long)gy * Lx;
     for (int rx = tx; rx < PX; rx += 32) {
@@ -275,43 +278,88 @@ __global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
   }
   cp_async_wait_all();
   __syncthreads();
-  // mu = a phi + b phi^3 - kappa lap_D phi (Eqs. 5, 31)
-  for (int my = threadIdx.y; my < MY; my += C2_BY)
-    for (int mx = tx; mx < MX; mx += 32) {
-      const int cy = my + 1, cx = mx + 1;
-      const C c = sphi[cy][cx];
-      C lap = p.R * sphi[cy - 1][cx - 1];
-      lap += p.Q * sphi[cy - 1][cx];
-      lap += p.R * sphi[cy - 1][cx + 1];
-      lap += p.Q * sphi[cy][cx - 1];
-      lap += p.C0 * c;
-      lap += p.Q * sphi[cy][cx + 1];
-      lap += p.R * sphi[cy + 1][cx - 1];
-      lap += p.Q * sphi[cy + 1][cx];
-      lap += p.R * sphi[cy + 1][cx + 1];
-      smu[my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
+  // mu = a phi + b phi^3 - kappa lap_D phi (Eqs. 5, 31) on the tile + 1:
+  // the 32 x 32 interior four rows per thread with rows reused from
+  // registers, then the one-site frame (132 sites) flat
+  auto mu_at = [&](C (&w)[3][3]) {  // explicitly rounded: evaluated in two places
+    C lap = rn_mul(p.R, w[0][0]);
+    lap = rn_fma(p.Q, w[0][1], lap);
+    lap = rn_fma(p.R, w[0][2], lap);
+    lap = rn_fma(p.Q, w[1][0], lap);
+    lap = rn_fma(p.C0, w[1][1], lap);
+    lap = rn_fma(p.Q, w[1][2], lap);
+    lap = rn_fma(p.R, w[2][0], lap);
+    lap = rn_fma(p.Q, w[2][1], lap);
+    lap = rn_fma(p.R, w[2][2], lap);
+    const C c = w[1][1];
+    const C c3 = rn_mul(rn_mul(c, c), c);
+    return rn_fma(p.a, c, rn_fma(p.b, c3, rn_mul(-p.kappa, lap)));
+  };
+  {
+    // interior mu rows my = ly0 + 1 .. ly0 + 4, column mx = tx + 1 (phi rows my - 1 .. my + 1
+    // of the phi tile are rows my .. my + 2, columns tx + 1 .. tx + 3)
+    C w[3][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) w[k + 1][j] = sphi[ly0 + 1 + k][tx + 1 + j];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        w[0][j] = w[1][j];
+        w[1][j] = w[2][j];
+        w[2][j] = sphi[ly0 + 3 + r][tx + 1 + j];
+      }
+      smu[ly0 + 1 + r][tx + 1] = mu_at(w);
     }
+    for (int k = tid; k < 2 * MX + 2 * (MY - 2); k += 256) {
+      int my, mx;
+      if (k < MX) { my = 0; mx = k; }
+      else if (k < 2 * MX) { my = MY - 1; mx = k - MX; }
+      else { const int q = k - 2 * MX; my = 1 + (q >> 1); mx = (q & 1) ? MX - 1 : 0; }
+      C v[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2) v[a][b2] = sphi[my + a][mx + b2];
+      smu[my][mx] = mu_at(v);
+    }
+  }
   __syncthreads();
+  // 3. force, moments, collision; mu rows reused from registers
+  C m3[3][3];  // mu rows (ly - 1 .. ly + 1) x columns (tx - 1 .. tx + 1), tile + 1 coordinates
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m3[k + 1][j] = smu[ly0 + k][tx + j];
+  const C om = p.tau_inv, keep = C(1) - p.tau_inv;
 #pragma unroll 1
   for (int r = 0; r < CA_RY; ++r) {
-    const int lx = tx, ly = threadIdx.y + C2_BY * r, y = y0 + ly;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      m3[0][j] = m3[1][j];
+      m3[1][j] = m3[2][j];
+      m3[2][j] = smu[ly0 + r + 2][tx + j];
+    }
+    const int lx = tx, ly = ly0 + r, y = y0 + ly;
     if (x >= Lx || y >= Ly) continue;
-    const int mx = lx + 1, my = ly + 1;
-    C gmx = -p.M * smu[my - 1][mx - 1];
-    gmx += p.M * smu[my - 1][mx + 1];
-    gmx += -p.N * smu[my][mx - 1];
-    gmx += p.N * smu[my][mx + 1];
-    gmx += -p.M * smu[my + 1][mx - 1];
-    gmx += p.M * smu[my + 1][mx + 1];
-    C gmy = -p.M * smu[my - 1][mx - 1];
-    gmy += -p.N * smu[my - 1][mx];
-    gmy += -p.M * smu[my - 1][mx + 1];
-    gmy += p.M * smu[my + 1][mx - 1];
-    gmy += p.N * smu[my + 1][mx];
-    gmy += p.M * smu[my + 1][mx + 1];
+    C gmx = -p.M * m3[0][0];
+    gmx += p.M * m3[0][2];
+    gmx += -p.N * m3[1][0];
+    gmx += p.N * m3[1][2];
+    gmx += -p.M * m3[2][0];
+    gmx += p.M * m3[2][2];
+    C gmy = -p.M * m3[0][0];
+    gmy += -p.N * m3[0][1];
+    gmy += -p.M * m3[0][2];
+    gmy += p.M * m3[2][0];
+    gmy += p.N * m3[2][1];
+    gmy += p.M * m3[2][2];
     const C ph = sphi[ly + 2][lx + 2];
     C Fx = -ph * gmx, Fy = -ph * gmy;
     if constexpr (TGEN) {
+      const int mx = lx + 1, my = ly + 1;
       C px = -p.M * spn[my - 1][mx - 1];
       px += p.M * spn[my - 1][mx + 1];
       px += -p.N * spn[my][mx - 1];
@@ -338,8 +386,9 @@ __global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
     const C n = C(1) + dens;
     Fx += n * p.gx;
     Fy += n * p.gy;
-    const C ux = (jx + C(0.5) * Fx) / n;
-    const C uy = (jy + C(0.5) * Fy) / n;
+    const C inv_n = C(1) / n;
+    const C ux = (jx + C(0.5) * Fx) * inv_n;
+    const C uy = (jy + C(0.5) * Fy) * inv_n;
     const long long s = (long long)y * Lx + x;
     if constexpr (MODE == COLLIDE_MOMENTS) {
       stg[s] = (double)n;
@@ -350,23 +399,25 @@ __global__ void __launch_bounds__(256, sizeof(C) == 4 ? 4 : 2)
     }
     const C usq = ux * ux + uy * uy;
     const C uF = ux * Fx + uy * Fy;
-    const C om = p.tau_inv, keep = C(1) - p.tau_inv;
     {
       const C w = C(q9_w(0));
       const C heq = w * (dens - n * (C(1.5) * usq));
       const C Fi = p.pref * w * (C(-3) * uF);
       hout[s] = keep * h[0] + om * heq + Fi;
     }
+    const C base = dens - n * (C(1.5) * usq);  // the u-independent and |u|^2 parts
+    const C n3 = C(3) * n, n45 = C(4.5) * n;
+    const C pF3 = C(3) * p.pref, pF9 = C(9) * p.pref, puF = C(3) * p.pref * uF;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = k < 2 ? k + 1 : k + 3, ib = i + 2;  // (1,3) (2,4) (5,7) (6,8)
       const C w = C(q9_w(i));
       const C eu = C(q9_ex(i)) * ux + C(q9_ey(i)) * uy;
       const C eF = C(q9_ex(i)) * Fx + C(q9_ey(i)) * Fy;
-      const C even = w * (dens + n * (C(4.5) * eu * eu - C(1.5) * usq));
-      const C odd = w * (n * (C(3) * eu));
-      const C Feven = p.pref * w * (C(9) * eu * eF - C(3) * uF);
-      const C Fodd = p.pref * w * (C(3) * eF);
+      const C even = w * (base + n45 * eu * eu);
+      const C odd = w * (n3 * eu);
+      const C Feven = w * (pF9 * eu * eF - puF);
+      const C Fodd = w * (pF3 * eF);
       hout[i * Sz + s] = keep * h[i] + om * (even + odd) + (Feven + Fodd);
       hout[ib * Sz + s] = keep * h[ib] + om * (even - odd) + (Feven - Fodd);
     }
@@ -810,7 +861,9 @@ cudaError_t collide2d_ry(lbm_handle *h, int in, int force_on, int mode) {
   return cudaGetLastError();
 }
 
-template <typename C>
+// MINB: CTAs per SM the register budget is sized for (4: no headroom, 3: none
+// of the FP32 variants spill)
+template <typename C, int MINB>
 cudaError_t collide2d_async(lbm_handle *h, int in, int force_on, int mode) {
   KParams<C> p = make_params<C>(h, force_on);
   dim3 grid((p.Lx + CA_TX - 1) / CA_TX, (p.Ly + CA_TY - 1) / CA_TY), block(32, C2_BY);
@@ -823,39 +876,51 @@ cudaError_t collide2d_async(lbm_handle *h, int in, int force_on, int mode) {
   const bool tgen = p.cs2mT != C(0);
   if (mode == COLLIDE_STEP) {
     if (tgen)
-      collide2d_async_kernel<C, true, COLLIDE_STEP>
+      collide2d_async_kernel<C, true, COLLIDE_STEP, MINB>
           <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
     else
-      collide2d_async_kernel<C, false, COLLIDE_STEP>
+      collide2d_async_kernel<C, false, COLLIDE_STEP, MINB>
           <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   } else {
     if (tgen)
-      collide2d_async_kernel<C, true, COLLIDE_MOMENTS>
+      collide2d_async_kernel<C, true, COLLIDE_MOMENTS, MINB>
           <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
     else
-      collide2d_async_kernel<C, false, COLLIDE_MOMENTS>
+      collide2d_async_kernel<C, false, COLLIDE_MOMENTS, MINB>
           <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   }
   return cudaGetLastError();
 }
 
-template <typename C>
-cudaError_t collide2d_async_configure() {
+template <typename C, int MINB>
+cudaError_t collide2d_async_configure_one() {
   const int smem = (int)collide_async_smem<C>();
   cudaError_t e = cudaSuccess;
-  for (auto fn : {collide2d_async_kernel<C, true, COLLIDE_STEP>,
-                  collide2d_async_kernel<C, false, COLLIDE_STEP>,
-                  collide2d_async_kernel<C, true, COLLIDE_MOMENTS>,
-                  collide2d_async_kernel<C, false, COLLIDE_MOMENTS>})
+  for (auto fn : {collide2d_async_kernel<C, true, COLLIDE_STEP, MINB>,
+                  collide2d_async_kernel<C, false, COLLIDE_STEP, MINB>,
+                  collide2d_async_kernel<C, true, COLLIDE_MOMENTS, MINB>,
+                  collide2d_async_kernel<C, false, COLLIDE_MOMENTS, MINB>})
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+template <typename C>
+cudaError_t collide2d_async_configure() {
+  cudaError_t e = collide2d_async_configure_one<C, 2>();
+  if (e == cudaSuccess) e = collide2d_async_configure_one<C, 3>();
+  if (e == cudaSuccess && sizeof(C) == 4) e = collide2d_async_configure_one<C, 4>();
   return e;
 }
 
 template <typename S, typename C>
 cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
   if constexpr (std::is_same<S, C>::value) {
-    if (h->collide_rows == 0) return collide2d_async<C>(h, in, force_on, mode);
+    // 0: asynchronous staging sized for 4 CTAs per SM (FP64: 2), 1: for 3
+    if (h->collide_rows == 0)
+      return sizeof(C) == 4 ? collide2d_async<C, 4>(h, in, force_on, mode)
+                            : collide2d_async<C, 2>(h, in, force_on, mode);
+    if (h->collide_rows == 1) return collide2d_async<C, 3>(h, in, force_on, mode);
   }
   return h->collide_rows == 4 ? collide2d_ry<S, C, 4>(h, in, force_on, mode)
                               : collide2d_ry<S, C, 2>(h, in, force_on, mode);

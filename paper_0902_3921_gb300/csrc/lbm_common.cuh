@@ -71,6 +71,14 @@ struct Store<__half, float> {
   }
 };
 
+// Explicitly rounded operations: code that evaluates one formula in more than
+// one place uses them so that every site gets bit-identical results whatever
+// contraction the compiler chooses elsewhere.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 __device__ __forceinline__ int wrapi(int x, int L) {
   x %= L;
   return x < 0 ? x + L : x;

@@ -319,7 +319,7 @@ int autotune_2d(lbm_handle *h) {
     const int nv = std::sscanf(fixed, "%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4]);
     if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
-        (v[3] == 2 || v[3] == 4 || (v[3] == 0 && h->P.precision != LBM_F16DEV))) {
+        (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV))) {
       h->sub = std::min(v[0], h->m);
       h->fd_rows = v[1];
       h->fd_cols = h->P.precision == LBM_F64 ? 2 : v[2];
@@ -387,8 +387,8 @@ int autotune_2d(lbm_handle *h) {
   h->fd_rows = bestc.rows;
   best = 1e30f;
   int best_cr = 2;
-  for (int cr : {0, 2, 4}) {
-    if (cr == 0 && h->P.precision == LBM_F16DEV) continue;  // cp.async moves >= 4 bytes
+  for (int cr : {0, 1, 2, 4}) {
+    if (cr < 2 && h->P.precision == LBM_F16DEV) continue;  // cp.async moves >= 4 bytes
     h->collide_rows = cr;
     const float ms =
         time_launches(h, e0, e1, [&] { return launch_collide(h, 0, 0, COLLIDE_STEP); });

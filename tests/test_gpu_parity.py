@@ -348,8 +348,8 @@ def test_nonfinite_is_reported():
 # every launch shape the autotuner can pick, pinned through HLBM_TUNING
 # ("FD substeps per launch, rows per warp, columns per lane, collide sites per
 # thread, FD tile width")
-SHAPES = ["4,16,4,2,0", "4,8,2,4,0", "2,32,4,0,0", "3,16,4,2,0", "1,64,2,0,0",
-          "1,32,4,0,32", "1,32,4,2,64", "2,32,4,4,64"]
+SHAPES = ["4,16,4,2,0", "4,8,2,4,0", "2,32,4,0,0", "3,16,4,2,0", "1,64,2,1,0",
+          "1,32,4,0,32", "1,32,4,2,64", "2,32,4,4,64", "4,16,2,1,0"]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
