@@ -441,6 +441,12 @@ __global__ void __launch_bounds__(256, MINB)
 // The advection terms of a row (d_x u and d_y v of Eq. 33, u and v, or the
 // face velocities of the flux form) are computed once per launch and kept in
 // a per-lane shared-memory ring until the last substep has used them.
+// packed FP32 pairs (two columns of a lane) for the FD stages
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 template <typename C, int V>
 struct VecT;
 template <>
@@ -582,24 +588,46 @@ __global__ void __launch_bounds__(64)
         const C(&dn)[V] = ph[s][S0];
         const C l0 = __shfl_up_sync(FULL, cur[V - 1], 1);
         const C rV = __shfl_down_sync(FULL, cur[0], 1);
+        bool packed = false;
+        if constexpr (std::is_same<C, float>::value) {
+          if (paper) {  // two columns per packed FP32x2 instruction
+            packed = true;
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-          const C pc = cur[j], pl = j == 0 ? l0 : cur[j - 1], pr = j == V - 1 ? rV : cur[j + 1];
-          const C t0 = T[ts][0][V * lane + j], t1 = T[ts][1][V * lane + j];
-          const C t2 = T[ts][2][V * lane + j];
-          if (paper) {
-            const C upx = t1 > C(0) ? pl : pr;   // u = 0 contributes nothing
-            const C upy = t2 > C(0) ? up[j] : dn[j];
-            A[s][S2][j] = t0 * pc + fabs(t1) * upx + fabs(t2) * upy;
-          } else {
-            const C t3 = T[ts][3][V * lane + j];
-            const C Jpx = t0 > C(0) ? t0 * pc : t0 * pr;
-            const C Jmx = t1 > C(0) ? t1 * pl : t1 * pc;
-            const C Jpy = t2 > C(0) ? t2 * pc : t2 * dn[j];
-            const C Jmy = t3 > C(0) ? t3 * up[j] : t3 * pc;
-            C tend = Jpx - Jmx;
-            tend += Jpy - Jmy;
-            A[s][S2][j] = pc - dt * tend;
+            for (int j = 0; j < V; j += 2) {
+              const float2 t0 = *reinterpret_cast<const float2 *>(&T[ts][0][V * lane + j]);
+              const float2 t1 = *reinterpret_cast<const float2 *>(&T[ts][1][V * lane + j]);
+              const float2 t2 = *reinterpret_cast<const float2 *>(&T[ts][2][V * lane + j]);
+              const float pl = j == 0 ? l0 : cur[j - 1], pr = j + 1 == V - 1 ? rV : cur[j + 2];
+              const float2 upx = f2(t1.x > 0.f ? pl : cur[j + 1], t1.y > 0.f ? cur[j] : pr);
+              const float2 upy = f2(t2.x > 0.f ? up[j] : dn[j], t2.y > 0.f ? up[j + 1] : dn[j + 1]);
+              const float2 r = fma2(f2(fabsf(t2.x), fabsf(t2.y)), upy,
+                                    fma2(f2(fabsf(t1.x), fabsf(t1.y)), upx,
+                                         mul2(t0, f2(cur[j], cur[j + 1]))));
+              A[s][S2][j] = r.x;
+              A[s][S2][j + 1] = r.y;
+            }
+          }
+        }
+        if (!packed) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            const C pc = cur[j], pl = j == 0 ? l0 : cur[j - 1], pr = j == V - 1 ? rV : cur[j + 1];
+            const C t0 = T[ts][0][V * lane + j], t1 = T[ts][1][V * lane + j];
+            const C t2 = T[ts][2][V * lane + j];
+            if (paper) {
+              const C upx = t1 > C(0) ? pl : pr;  // u = 0 contributes nothing
+              const C upy = t2 > C(0) ? up[j] : dn[j];
+              A[s][S2][j] = t0 * pc + fabs(t1) * upx + fabs(t2) * upy;
+            } else {
+              const C t3 = T[ts][3][V * lane + j];
+              const C Jpx = t0 > C(0) ? t0 * pc : t0 * pr;
+              const C Jmx = t1 > C(0) ? t1 * pl : t1 * pc;
+              const C Jpy = t2 > C(0) ? t2 * pc : t2 * dn[j];
+              const C Jmy = t3 > C(0) ? t3 * up[j] : t3 * pc;
+              C tend = Jpx - Jmx;
+              tend += Jpy - Jmy;
+              A[s][S2][j] = pc - dt * tend;
+            }
           }
         }
       }
@@ -607,16 +635,34 @@ __global__ void __launch_bounds__(64)
         const C(&Ac)[V] = A[s][S1];
         const C l0 = __shfl_up_sync(FULL, Ac[V - 1], 1);
         const C rV = __shfl_down_sync(FULL, Ac[0], 1);
+        if constexpr (std::is_same<C, float>::value) {
+          const float2 a2 = f2(a, a), b2 = f2(b, b), mk2 = f2(-kappa, -kappa), m4 = f2(-4.f, -4.f);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-          const C hk = Ac[j];
-          C lap = A[s][S0][j];
-          lap += j == 0 ? l0 : Ac[j - 1];
-          lap += C(-4) * hk;
-          lap += j == V - 1 ? rV : Ac[j + 1];
-          lap += A[s][S2][j];
-          const C c = cubic_half ? hk : ph[s][S1][j];
-          P[s][S1][j] = a * hk + b * (c * c * c) - kappa * lap;
+          for (int j = 0; j < V; j += 2) {
+            const float2 hk = f2(Ac[j], Ac[j + 1]);
+            const float2 left = f2(j == 0 ? l0 : Ac[j - 1], Ac[j]);
+            const float2 right = f2(Ac[j + 1], j + 1 == V - 1 ? rV : Ac[j + 2]);
+            float2 lap = add2(f2(A[s][S0][j], A[s][S0][j + 1]), left);
+            lap = fma2(m4, hk, lap);
+            lap = add2(lap, right);
+            lap = add2(lap, f2(A[s][S2][j], A[s][S2][j + 1]));
+            const float2 c = cubic_half ? hk : f2(ph[s][S1][j], ph[s][S1][j + 1]);
+            const float2 r = fma2(a2, hk, fma2(b2, mul2(mul2(c, c), c), mul2(mk2, lap)));
+            P[s][S1][j] = r.x;
+            P[s][S1][j + 1] = r.y;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            const C hk = Ac[j];
+            C lap = A[s][S0][j];
+            lap += j == 0 ? l0 : Ac[j - 1];
+            lap += C(-4) * hk;
+            lap += j == V - 1 ? rV : Ac[j + 1];
+            lap += A[s][S2][j];
+            const C c = cubic_half ? hk : ph[s][S1][j];
+            P[s][S1][j] = a * hk + b * (c * c * c) - kappa * lap;
+          }
         }
       }
       if (nw - 3 >= 3 * s + 3) {  // phi of the next substep on row nw - 3
@@ -624,14 +670,29 @@ __global__ void __launch_bounds__(64)
         const C l0 = __shfl_up_sync(FULL, Pc[V - 1], 1);
         const C rV = __shfl_down_sync(FULL, Pc[0], 1);
         C F[V];
+        if constexpr (std::is_same<C, float>::value) {
+          const float2 g2 = f2(dtG, dtG), m4 = f2(-4.f, -4.f);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-          C lap = P[s][S2][j];
-          lap += j == 0 ? l0 : Pc[j - 1];
-          lap += C(-4) * Pc[j];
-          lap += j == V - 1 ? rV : Pc[j + 1];
-          lap += P[s][S1][j];
-          F[j] = A[s][S0][j] + dtG * lap;
+          for (int j = 0; j < V; j += 2) {
+            const float2 pc = f2(Pc[j], Pc[j + 1]);
+            float2 lap = add2(f2(P[s][S2][j], P[s][S2][j + 1]), f2(j == 0 ? l0 : Pc[j - 1], Pc[j]));
+            lap = fma2(m4, pc, lap);
+            lap = add2(lap, f2(Pc[j + 1], j + 1 == V - 1 ? rV : Pc[j + 2]));
+            lap = add2(lap, f2(P[s][S1][j], P[s][S1][j + 1]));
+            const float2 r = fma2(g2, lap, f2(A[s][S0][j], A[s][S0][j + 1]));
+            F[j] = r.x;
+            F[j + 1] = r.y;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            C lap = P[s][S2][j];
+            lap += j == 0 ? l0 : Pc[j - 1];
+            lap += C(-4) * Pc[j];
+            lap += j == V - 1 ? rV : Pc[j + 1];
+            lap += P[s][S1][j];
+            F[j] = A[s][S0][j] + dtG * lap;
+          }
         }
         if (s + 1 < SUB) {
 #pragma unroll
