@@ -7,7 +7,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "lbm_common.cuh"
 
@@ -331,6 +334,29 @@ int autotune_2d(lbm_handle *h) {
     }
     return fail(h, LBM_EINVAL, "HLBM_TUNING must be 'sub,rows,cols,collide_rows[,tile]'");
   }
+  // one choice per lattice shape and scheme in a process: every handle of
+  // the same problem then runs the same kernels (and gives the same bits)
+  using Key = std::tuple<int, int, int, int, int, int, int>;
+  struct Choice {
+    int sub, fd_rows, fd_cols, collide_rows, fd_tile_w;
+  };
+  static std::mutex cache_mu;
+  static std::map<Key, Choice> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const Key key{dev, h->P.Lx, h->P.Ly, h->P.precision, h->m, h->P.adv_variant, h->P.cubic_at_half};
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      h->sub = it->second.sub;
+      h->fd_rows = it->second.fd_rows;
+      h->fd_cols = it->second.fd_cols;
+      h->collide_rows = it->second.collide_rows;
+      h->fd_tile_w = it->second.fd_tile_w;
+      return LBM_OK;
+    }
+  }
   const bool verbose = std::getenv("HLBM_TUNE_VERBOSE") != nullptr;
   const size_t cb = compute_bytes(h->P.precision);
   CK(h, cudaMemsetAsync(h->phi[0], 0, cb * (size_t)h->S, h->stream), "cudaMemset");
@@ -408,6 +434,8 @@ int autotune_2d(lbm_handle *h) {
   h->collide_rows = best_cr;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(cache_mu);
+  cache.emplace(key, Choice{h->sub, h->fd_rows, h->fd_cols, h->collide_rows, h->fd_tile_w});
   return LBM_OK;
 }
 

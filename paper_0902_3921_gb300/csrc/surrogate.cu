@@ -7,8 +7,11 @@
 // check a residual, fall back to the plain scheme).  The paper has no
 // counterpart; the network is judged by the paper's observables.
 //
-// Layouts: activations NHWC with padded channel counts (the 4-channel input
-// is padded to 16, hidden layers C = 32, the last layer's outputs to 8);
+// Layouts: activations (BF16) are stored row-chunk planar, [n][y][c / 8][x][8]:
+// for each image row, the 8-channel chunks of all its pixels form contiguous
+// planes, so one operand plane of a row is one contiguous copy (see
+// conv_act_index); channel counts are padded (the 4-channel input to 16,
+// hidden layers C = 32); the last layer's FP32 output is [p][8];
 // weights [Cout_p][KS] with K = 9 Cin_p ordered (tap, ci), tap = (dy+1)*3 +
 // (dx+1), KS = K + 8 (bank-conflict padding, always zero).
 #include <cuda_bf16.h>
@@ -22,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "conv_tc.cuh"
 #include "lbm_common.cuh"
 
 typedef __nv_bfloat16 bf16;
@@ -45,7 +49,7 @@ __device__ __forceinline__ unsigned ld32(const bf16 *p) {
   return *reinterpret_cast<const unsigned *>(p);
 }
 
-enum { EPI_RELU = 0, EPI_LINEAR_F32 = 1, EPI_MASK = 2 };
+constexpr int EPI_RELU = CONV_RELU, EPI_LINEAR_F32 = CONV_LINEAR_F32, EPI_MASK = CONV_MASK;
 
 // out[p, co] = sum_{tap, ci} in[p + tap, ci] w[co][tap, ci] (periodic), then
 //   EPI_RELU:       bf16 max(. + bias, 0)
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(256)
     int gy = y0 + r - 1, gx = x0 + c - 1;
     gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
     gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
-    const uint4 val = *reinterpret_cast<const uint4 *>(in + (img + (long long)gy * W + gx) * CINP + v * 8);
+    const uint4 val = *reinterpret_cast<const uint4 *>(in + conv_act_index(img / W + gy, v, gx, W, VPP));
     *reinterpret_cast<uint4 *>(sin + pix * PS + v * 8) = val;
   }
   for (int k = tid; k < COUTP * KS / 8; k += 256)
@@ -103,9 +107,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const long long p = img + (long long)y * W + x0 + g + 8 * half;
+    const long long row = img / W + y;
+    const int x = x0 + g + 8 * half;
 #pragma unroll
     for (int j = 0; j < COUTP / 8; ++j) {
       const int co = j * 8 + 2 * t;
+      const long long q = conv_act_index(row, j, x, W, COUTP / 8) + 2 * t;
       float v0 = acc[j][2 * half], v1 = acc[j][2 * half + 1];
       if constexpr (EPI == EPI_LINEAR_F32) {
         *reinterpret_cast<float2 *>(out_f + p * COUTP + co) = make_float2(v0 + bias[co], v1 + bias[co + 1]);
@@ -114,11 +121,11 @@ __global__ void __launch_bounds__(256)
           v0 = fmaxf(v0 + bias[co], 0.f);
           v1 = fmaxf(v1 + bias[co + 1], 0.f);
         } else {
-          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + p * COUTP + co);
+          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + q);
           v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
           v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
         }
-        *reinterpret_cast<__nv_bfloat162 *>(out_bf + p * COUTP + co) = __floats2bfloat162_rn(v0, v1);
+        *reinterpret_cast<__nv_bfloat162 *>(out_bf + q) = __floats2bfloat162_rn(v0, v1);
       }
     }
   }
@@ -157,12 +164,12 @@ __global__ void __launch_bounds__(256)
       int gy = y0 + r - 1, gx = x0 + cc - 1;
       gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
       gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
-      sx[pix][c] = __bfloat162float(x[(img + (long long)gy * W + gx) * CINP + c]);
+      sx[pix][c] = __bfloat162float(x[conv_act_index(img / W + gy, c / 8, gx, W, CINP / 8) + c % 8]);
     }
     for (int k = tid; k < TILE_H * TILE_W * COUTP; k += 256) {
       const int pix = k / COUTP, c = k - pix * COUTP;
       const int r = pix / TILE_W, cc = pix - r * TILE_W;
-      sd[pix][c] = __bfloat162float(dz[(img + (long long)(y0 + r) * W + x0 + cc) * DZS + c]);
+      sd[pix][c] = __bfloat162float(dz[conv_act_index(img / W + y0 + r, c / 8, x0 + cc, W, DZS / 8) + c % 8]);
     }
     __syncthreads();
     if (tid < NT) {
@@ -208,34 +215,37 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ partial, int npart
   }
 }
 
-// raw FP32 state [p][4] -> normalised BF16 input [p][16] (channels 4..15 zero)
-__global__ void normalise_kernel(const float *__restrict__ x, long long P, const float *__restrict__ nrm,
-                                 bf16 *__restrict__ out) {
+// raw FP32 state [p][4] -> normalised BF16 input, 16 channels (4..15 zero),
+// row-chunk planar
+__global__ void normalise_kernel(const float *__restrict__ x, long long P, int W,
+                                 const float *__restrict__ nrm, bf16 *__restrict__ out) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
-  __align__(16) bf16 v[16];
+  __align__(16) bf16 v[8];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+  for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16(0.f);
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = __float2bfloat16((x[p * 4 + c] - nrm[c]) / nrm[4 + c]);
-  uint4 *o = reinterpret_cast<uint4 *>(out + p * 16);
-  o[0] = reinterpret_cast<uint4 *>(v)[0];
-  o[1] = reinterpret_cast<uint4 *>(v)[1];
+  const long long row = p / W;
+  const int xx = (int)(p - row * W);
+  *reinterpret_cast<uint4 *>(out + conv_act_index(row, 0, xx, W, 2)) = *reinterpret_cast<uint4 *>(v);
+  *reinterpret_cast<uint4 *>(out + conv_act_index(row, 1, xx, W, 2)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // MSE of the network output y [p][8] (4 used) against (x1 - x0) / out_std;
 // writes the gradient dL/dy as BF16 [p][16] and per-block partial sums.
 __global__ void __launch_bounds__(256)
     mse_kernel(const float *__restrict__ y, const float *__restrict__ x0, const float *__restrict__ x1,
-               long long P, const float *__restrict__ nrm, bf16 *__restrict__ dz, double *__restrict__ part) {
+               long long P, int W, const float *__restrict__ nrm, bf16 *__restrict__ dz,
+               double *__restrict__ part) {
   __shared__ double red[256];
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const double inv = 1.0 / (4.0 * (double)P);
   double acc = 0.0;
   if (p < P) {
-    __align__(16) bf16 v[16];
+    __align__(16) bf16 v[8];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+    for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16(0.f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const float target = (x1[p * 4 + c] - x0[p * 4 + c]) / nrm[8 + c];
@@ -243,9 +253,10 @@ __global__ void __launch_bounds__(256)
       acc += (double)e * e;
       v[c] = __float2bfloat16((float)(2.0 * inv) * e);
     }
-    uint4 *o = reinterpret_cast<uint4 *>(dz + p * 16);
-    o[0] = reinterpret_cast<uint4 *>(v)[0];
-    o[1] = reinterpret_cast<uint4 *>(v)[1];
+    const long long row = p / W;
+    const int xx = (int)(p - row * W);
+    *reinterpret_cast<uint4 *>(dz + conv_act_index(row, 0, xx, W, 2)) = *reinterpret_cast<uint4 *>(v);
+    *reinterpret_cast<uint4 *>(dz + conv_act_index(row, 1, xx, W, 2)) = make_uint4(0u, 0u, 0u, 0u);
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -439,9 +450,19 @@ cudaError_t conv(const bf16 *in, const bf16 *w, const float *bias, const bf16 *m
   return cudaGetLastError();
 }
 
+// the tcgen05 kernel unless the rows are not whole 128-pixel tiles or
+// HLBM_CONV_PATH=mma asks for the mma.sync kernel
+bool use_tc(int cinp, int coutp, int W) {
+  const char *e = std::getenv("HLBM_CONV_PATH");
+  if (e && std::strcmp(e, "mma") == 0) return false;
+  return conv_tc_supported(cinp, coutp, W);
+}
+
 // dispatch on the padded channel counts used by the network (C = 32 or 16)
 cudaError_t conv_any(int cinp, int coutp, int epi, const bf16 *in, const bf16 *w, const float *bias,
                      const bf16 *mask, int N, int H, int W, bf16 *ob, float *of, cudaStream_t s) {
+  if (use_tc(cinp, coutp, W))
+    return conv_tc(cinp, coutp, epi, in, w, 9 * cinp + 8, bias, mask, N, H, W, ob, of, s);
 #define CASE(CI, CO, E)                                               \
   if (cinp == CI && coutp == CO && epi == E)                          \
     return conv<CI, CO, E>(in, w, bias, mask, N, H, W, ob, of, s);
@@ -485,7 +506,7 @@ int check_shape(lbm_net *net, int N, int H, int W) {
 // forward pass on net->x0 (raw state, P pixels) -> net->yout
 int forward_raw(lbm_net *net, int N, int H, int W, cudaStream_t s) {
   const long long P = (long long)N * H * W;
-  normalise_kernel<<<nblk(P, 256), 256, 0, s>>>(net->x0, P, net->nrm, net->act[0]);
+  normalise_kernel<<<nblk(P, 256), 256, 0, s>>>(net->x0, P, W, net->nrm, net->act[0]);
   NCK(net, cudaGetLastError(), "normalise kernel");
   for (int l = 0; l < net->layers; l++) {
     const Layer &Ly = net->L[l];
@@ -675,7 +696,7 @@ int lbm_net_train_step(lbm_net *net, const float *x0, const float *x1, int N, in
   rc = forward_raw(net, N, H, W, s);
   if (rc) return rc;
   const unsigned nb = nblk(P, 256);
-  mse_kernel<<<nb, 256, 0, s>>>(net->yout, net->x0, x1, P, net->nrm, net->dz[0], net->dpart);
+  mse_kernel<<<nb, 256, 0, s>>>(net->yout, net->x0, x1, P, W, net->nrm, net->dz[0], net->dpart);
   NCK(net, cudaGetLastError(), "mse kernel");
   // backward: dz holds dL/dz of layer l (BF16, cinp_t of layer l channels)
   int cur = 0;

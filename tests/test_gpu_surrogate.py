@@ -88,6 +88,97 @@ def test_forward_matches_reference(C, L):
     net.close()
 
 
+def _forward_gpu(net, x0, N, H, W):
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.empty_like(d0)
+    net.forward(d0.data_ptr(), N, H, W, d1.data_ptr())
+    torch.cuda.synchronize()
+    return d1.cpu().numpy()
+
+
+def _forward_ref(params, x0):
+    xn = (x0 - NORM[0]) / NORM[1]
+    xn = torch.from_numpy(xn).to(torch.bfloat16).double().numpy()  # the GPU's BF16 input
+    y, _, _ = OS.forward(params, xn)
+    return x0 + y * NORM[2], y
+
+
+@pytest.mark.parametrize("C,L,H,W", [(32, 6, 8, 128), (32, 6, 8, 256), (16, 3, 8, 128)])
+def test_tensor_core_forward_matches_reference(C, L, H, W):
+    """Rows of whole 128-pixel tiles take the tcgen05 kernel: the same bar as
+    the mma.sync kernel against the FP64 reference."""
+    net, params = _random_net(C, L, seed=2)
+    net.set_normalisation(*NORM)
+    x0, _ = _inputs(2, H, W, 6)
+    got = _forward_gpu(net, x0, 2, H, W)
+    ref, y = _forward_ref(params, x0)
+    for c in range(4):
+        err = np.max(np.abs(got[..., c] - ref[..., c]))
+        scale = np.max(np.abs(y[..., c] * NORM[2][c]))
+        assert err <= 3e-2 * scale, (c, err, scale)
+    net.close()
+
+
+def test_tensor_core_and_mma_kernels_agree(monkeypatch):
+    """The tcgen05 and mma.sync kernels multiply the same BF16 operands and
+    accumulate in FP32: outputs agree to FP32 summation-order effects (one
+    BF16 rounding step where an intermediate activation falls on a tie)."""
+    net, _ = _random_net(32, 6, seed=4)
+    net.set_normalisation(*NORM)
+    x0, _ = _inputs(1, 8, 128, 8)
+    tc = _forward_gpu(net, x0, 1, 8, 128)
+    monkeypatch.setenv("HLBM_CONV_PATH", "mma")
+    mma = _forward_gpu(net, x0, 1, 8, 128)
+    for c in range(4):
+        scale = np.max(np.abs(mma[..., c] - x0[..., c]))
+        assert np.max(np.abs(tc[..., c] - mma[..., c])) <= 2e-2 * scale
+    net.close()
+
+
+def test_tensor_core_forward_full_size_sampled():
+    """2048^2 (the inference lattice): sampled pixels against the reference
+    run on a 32 x 32 periodic crop around each; six 3x3 layers see 6 pixels,
+    so the crop's wrapped edges never reach its centre."""
+    C, L, S = 32, 6, 2048
+    net, params = _random_net(C, L, seed=9)
+    net.set_normalisation(*NORM)
+    x0, _ = _inputs(1, S, S, 10)
+    got = _forward_gpu(net, x0, 1, S, S)
+    rng = np.random.default_rng(11)
+    pts = [(0, 0), (S - 1, S - 1), (0, 127), (5, 128)] + [tuple(v) for v in rng.integers(0, S, (4, 2))]
+    for (y, x) in pts:
+        idx_y = (y + np.arange(-16, 16)) % S
+        idx_x = (x + np.arange(-16, 16)) % S
+        crop = x0[:, idx_y][:, :, idx_x]
+        ref, yv = _forward_ref(params, crop)
+        for c in range(4):
+            scale = max(np.max(np.abs(yv[..., c] * NORM[2][c])), 1e-30)
+            assert abs(got[0, y, x, c] - ref[0, 16, 16, c]) <= 3e-2 * scale, (y, x, c)
+    net.close()
+
+
+def test_tensor_core_gradients_match_reference():
+    """The backward data pass (transposed, tap-flipped convolution masked by
+    the ReLU) on the tcgen05 kernel, W = 128."""
+    C, L = 32, 6
+    net, params = _random_net(C, L, seed=12)
+    net.set_normalisation(*NORM)
+    x0, x1 = _inputs(1, 8, 128, 13)
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.from_numpy(x1.astype(np.float32)).cuda()
+    loss = net.train_step(d0.data_ptr(), d1.data_ptr(), 1, 8, 128, lr=0.0, update=False)
+    g = _flat_to_params(net.get_grads().astype(np.float64), C, L)
+    xn = torch.from_numpy((x0 - NORM[0]) / NORM[1]).to(torch.bfloat16).double().numpy()
+    target = ((x1.astype(np.float32) - x0.astype(np.float32)) / NORM[2]).astype(np.float64)
+    ref_loss, ref_g = OS.loss_and_grads(params, xn, target)
+    assert loss == pytest.approx(ref_loss, rel=2e-2)
+    for li, ((gw, gb), (rw, rb)) in enumerate(zip(g, ref_g)):
+        ew = np.linalg.norm(gw - rw) / np.linalg.norm(rw)
+        eb = np.linalg.norm(gb - rb) / max(np.linalg.norm(rb), 1e-30)
+        assert ew <= 4e-2 and eb <= 4e-2, (li, ew, eb)
+    net.close()
+
+
 def test_gradients_and_loss_match_reference():
     C, L = 32, 6
     net, params = _random_net(C, L, seed=5)
