@@ -869,6 +869,191 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---- FD convection-diffusion: block kernel, one 128-column region per CTA ----
+// FP32 only.  A CTA of FDB_NW warps owns a region 128 columns wide and RY =
+// K FDB_NW rows high, whose inner (128 - 2H) x (RY - 2H) sites are written
+// (H = 3 SUB).  Warp w owns rows w, w + FDB_NW, ...; lane l owns the four
+// columns 4l .. 4l + 3 of each, so every shared-memory access is one float4
+// per lane (row pitch 128 floats: a warp reads 512 contiguous bytes) and the
+// x neighbours come from the adjacent lanes by shuffles.  Columns 0 and 127
+// are never valid, so lanes 0 and 31 need no neighbour outside the warp.
+// The advection coefficients of Eqs. 32-35 depend only on u*(t): they are
+// computed once per launch and kept in registers for all SUB substeps.
+// Shared memory: phi, phih and psi planes of RY x 128 floats; each substep
+// is three phases over a region that shrinks by one site per phase.
+constexpr int FDB_NW = 16;
+constexpr int FDB_RX = 128;
+
+template <int SUB, int K>
+struct FDBlock {
+  static constexpr int H = 3 * SUB, RY = K * FDB_NW, TX = FDB_RX - 2 * H, TY = RY - 2 * H;
+  static constexpr size_t smem = sizeof(float) * 3 * (size_t)RY * FDB_RX;
+};
+
+__device__ __forceinline__ float4 ld4(const float *a, int r, int c) {
+  return *reinterpret_cast<const float4 *>(a + r * FDB_RX + c);
+}
+__device__ __forceinline__ void st4(float *a, int r, int c, float4 v) {
+  *reinterpret_cast<float4 *>(a + r * FDB_RX + c) = v;
+}
+__device__ __forceinline__ float comp(const float4 &v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float4 mk4(const float (&e)[4]) { return make_float4(e[0], e[1], e[2], e[3]); }
+
+template <bool FLUX, int SUB, int K>
+__global__ void __launch_bounds__(FDB_NW * 32, 1)
+    fd2d_block_kernel(const float *__restrict__ phi_in, const float *__restrict__ u,
+                      float *__restrict__ phi_out, KParams<float> p) {
+  using G = FDBlock<SUB, K>;
+  constexpr int H = G::H, RY = G::RY, TX = G::TX, TY = G::TY, NC = FLUX ? 4 : 3;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) float fdb_smem[];
+  float *sp = fdb_smem, *sa = sp + RY * FDB_RX, *sq = sa + RY * FDB_RX;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = 4 * lane;
+  const int Lx = p.Lx, Ly = p.Ly;
+  const long long Sz = (long long)Lx * Ly;
+  const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H;
+  int gx[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) gx[j] = wrapi(x0 + c + j, Lx);
+  // 1. phi -> sp, u -> sa, v -> sq (the latter two only until the
+  //    coefficients are in registers)
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int r = warp + FDB_NW * k;
+    const long long row = (long long)wrapi(y0 + r, Ly) * Lx;
+    float e[4], f[4], g[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      e[j] = __ldg(phi_in + row + gx[j]);
+      f[j] = __ldg(u + row + gx[j]);
+      g[j] = __ldg(u + Sz + row + gx[j]);
+    }
+    st4(sp, r, c, mk4(e));
+    st4(sa, r, c, mk4(f));
+    st4(sq, r, c, mk4(g));
+  }
+  __syncthreads();
+  // 2. advection coefficients (printed form: c0, dt u, dt v; flux form: the
+  //    four face velocities) of this thread's sites
+  const float dt = p.dt, dtG = p.dtG, a = p.a, b = p.b, kappa = p.kappa;
+  const bool cubic_half = p.cubic_at_half != 0;
+  float T[K][NC][4];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int r = warp + FDB_NW * k;
+    const int rm = r > 0 ? r - 1 : r, rp = r < RY - 1 ? r + 1 : r;  // row 0 / RY-1: never valid
+    const float4 uc = ld4(sa, r, c), vc = ld4(sq, r, c), vm = ld4(sq, rm, c), vp = ld4(sq, rp, c);
+    const float uL0 = __shfl_up_sync(FULL, uc.w, 1), uR3 = __shfl_down_sync(FULL, uc.x, 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float ucj = comp(uc, j), uL = j == 0 ? uL0 : comp(uc, j - 1), uR = j == 3 ? uR3 : comp(uc, j + 1);
+      const float vcj = comp(vc, j), vmj = comp(vm, j), vpj = comp(vp, j);
+      if constexpr (!FLUX) {
+        const float div = (uR - uL) / 2.f + (vpj - vmj) / 2.f;
+        T[k][0][j] = 1.f - dt * (div + (fabsf(ucj) + fabsf(vcj)));
+        T[k][1][j] = dt * ucj;
+        T[k][2][j] = dt * vcj;
+      } else {
+        T[k][0][j] = 0.5f * (ucj + uR);
+        T[k][1][j] = 0.5f * (uL + ucj);
+        T[k][2][j] = 0.5f * (vcj + vpj);
+        T[k][3][j] = 0.5f * (vmj + vcj);
+      }
+    }
+  }
+  __syncthreads();
+  // 3. SUB substeps of Eqs. 32-36
+#pragma unroll 1
+  for (int s = 0; s < SUB; ++s) {
+    int lo = 3 * s + 1;  // phih = advected phi
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = warp + FDB_NW * k;
+      if (r < lo || r >= RY - lo) continue;  // warp-uniform
+      const float4 pc = ld4(sp, r, c), pu = ld4(sp, r - 1, c), pd = ld4(sp, r + 1, c);
+      const float l0 = __shfl_up_sync(FULL, pc.w, 1), r3 = __shfl_down_sync(FULL, pc.x, 1);
+      float e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float pcj = comp(pc, j), pl = j == 0 ? l0 : comp(pc, j - 1), pr = j == 3 ? r3 : comp(pc, j + 1);
+        if constexpr (!FLUX) {
+          const float t1 = T[k][1][j], t2 = T[k][2][j];
+          const float upx = t1 > 0.f ? pl : pr;  // u = 0 contributes nothing
+          const float upy = t2 > 0.f ? comp(pu, j) : comp(pd, j);
+          e[j] = T[k][0][j] * pcj + fabsf(t1) * upx + fabsf(t2) * upy;
+        } else {
+          const float t0 = T[k][0][j], t1 = T[k][1][j], t2 = T[k][2][j], t3 = T[k][3][j];
+          const float Jpx = t0 > 0.f ? t0 * pcj : t0 * pr;
+          const float Jmx = t1 > 0.f ? t1 * pl : t1 * pcj;
+          const float Jpy = t2 > 0.f ? t2 * pcj : t2 * comp(pd, j);
+          const float Jmy = t3 > 0.f ? t3 * comp(pu, j) : t3 * pcj;
+          float tend = Jpx - Jmx;
+          tend += Jpy - Jmy;
+          e[j] = pcj - dt * tend;
+        }
+      }
+      st4(sa, r, c, mk4(e));
+    }
+    __syncthreads();
+    lo = 3 * s + 2;  // psi = a phih + b phi^3 - kappa lap phih (Eq. 36)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = warp + FDB_NW * k;
+      if (r < lo || r >= RY - lo) continue;
+      const float4 ac = ld4(sa, r, c), au = ld4(sa, r - 1, c), ad = ld4(sa, r + 1, c);
+      const float4 pc = ld4(sp, r, c);
+      const float l0 = __shfl_up_sync(FULL, ac.w, 1), r3 = __shfl_down_sync(FULL, ac.x, 1);
+      float e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float hk = comp(ac, j);
+        float lap = comp(au, j);
+        lap += j == 0 ? l0 : comp(ac, j - 1);
+        lap += -4.f * hk;
+        lap += j == 3 ? r3 : comp(ac, j + 1);
+        lap += comp(ad, j);
+        const float cb = cubic_half ? hk : comp(pc, j);
+        e[j] = a * hk + b * (cb * cb * cb) - kappa * lap;
+      }
+      st4(sq, r, c, mk4(e));
+    }
+    __syncthreads();
+    lo = 3 * s + 3;  // phi^{n+1} = phih + dt Gamma lap psi
+    const bool last = s == SUB - 1;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = warp + FDB_NW * k;
+      if (r < lo || r >= RY - lo) continue;
+      const float4 qc = ld4(sq, r, c), qu = ld4(sq, r - 1, c), qd = ld4(sq, r + 1, c);
+      const float4 ac = ld4(sa, r, c);
+      const float l0 = __shfl_up_sync(FULL, qc.w, 1), r3 = __shfl_down_sync(FULL, qc.x, 1);
+      float e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float lap = comp(qu, j);
+        lap += j == 0 ? l0 : comp(qc, j - 1);
+        lap += -4.f * comp(qc, j);
+        lap += j == 3 ? r3 : comp(qc, j + 1);
+        lap += comp(qd, j);
+        e[j] = comp(ac, j) + dtG * lap;
+      }
+      if (!last) {
+        st4(sp, r, c, mk4(e));
+      } else if (r >= H && r < H + TY && y0 + r < Ly) {
+        const long long row = (long long)(y0 + r) * Lx;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int cc = c + j, xg = x0 + cc;
+          if (cc >= H && cc < H + TX && xg < Lx) phi_out[row + xg] = e[j];
+        }
+      }
+    }
+    if (!last) __syncthreads();
+  }
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     density2d_kernel(const S *__restrict__ hin, C *__restrict__ dn, KParams<C> p) {
@@ -1006,10 +1191,54 @@ cudaError_t fd2d_tile_one(lbm_handle *h, const KParams<C> &p, const C *src, C *d
   return cudaGetLastError();
 }
 
+template <bool FLUX, int SUB, int K>
+cudaError_t fd2d_block_one(lbm_handle *h, const KParams<float> &p, const float *src, float *dst) {
+  using G = FDBlock<SUB, K>;
+  dim3 grid((p.Lx + G::TX - 1) / G::TX, (p.Ly + G::TY - 1) / G::TY);
+  fd2d_block_kernel<FLUX, SUB, K><<<grid, FDB_NW * 32, G::smem, h->stream>>>(
+      src, static_cast<const float *>(h->u), dst, p);
+  return cudaGetLastError();
+}
+
+// block kernel shapes (substeps per launch, rows per warp)
+#define FDB_SHAPES(X) X(1, 4) X(2, 4) X(2, 5) X(4, 5) X(4, 6)
+
+template <typename C>
+cudaError_t fd2d_block(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub) {
+  if constexpr (std::is_same<C, float>::value) {
+    const bool flux = p.adv_variant == LBM_ADV_FLUX;
+#define FDB_CASE(SB, KK)                                                            \
+  if (sub == SB && h->fd_rows == KK)                                               \
+    return flux ? fd2d_block_one<true, SB, KK>(h, p, src, dst)                     \
+                : fd2d_block_one<false, SB, KK>(h, p, src, dst);
+    FDB_SHAPES(FDB_CASE)
+#undef FDB_CASE
+    // a remainder launch with fewer substeps than the shape
+    if (sub == 1) return flux ? fd2d_block_one<true, 1, 4>(h, p, src, dst) : fd2d_block_one<false, 1, 4>(h, p, src, dst);
+    if (sub == 2) return flux ? fd2d_block_one<true, 2, 4>(h, p, src, dst) : fd2d_block_one<false, 2, 4>(h, p, src, dst);
+    return flux ? fd2d_block_one<true, 4, 5>(h, p, src, dst) : fd2d_block_one<false, 4, 5>(h, p, src, dst);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename C>
 cudaError_t fd2d_tile(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub) {
   if (h->fd_tile_w == 32) return fd2d_tile_one<C, 32, 1>(h, p, src, dst);  // one substep
   return sub >= 2 ? fd2d_tile_one<C, 64, 2>(h, p, src, dst) : fd2d_tile_one<C, 64, 1>(h, p, src, dst);
+}
+
+cudaError_t fd2d_block_configure() {
+  cudaError_t e = cudaSuccess;
+#define FDB_CFG(SB, KK)                                                                         \
+  if (e == cudaSuccess)                                                                         \
+    e = cudaFuncSetAttribute(fd2d_block_kernel<false, SB, KK>,                                  \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FDBlock<SB, KK>::smem); \
+  if (e == cudaSuccess)                                                                         \
+    e = cudaFuncSetAttribute(fd2d_block_kernel<true, SB, KK>,                                   \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FDBlock<SB, KK>::smem);
+  FDB_SHAPES(FDB_CFG)
+#undef FDB_CFG
+  return e;
 }
 
 template <typename C>
@@ -1030,6 +1259,7 @@ cudaError_t fd2d_tile_configure() {
 
 template <typename C, int V>
 cudaError_t fd2d_sub(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub, int TY) {
+  if (h->fd_tile_w == 128) return fd2d_block<C>(h, p, src, dst, sub);
   if (h->fd_tile_w > 0) return fd2d_tile<C>(h, p, src, dst, sub);
   switch (sub) {
     case 1: return fd2d_launch_one<C, V, 1>(h, p, src, dst, TY);
@@ -1067,6 +1297,7 @@ cudaError_t collide2d_launch(lbm_handle *h, int in, int force_on, int mode) {
 
 cudaError_t collide2d_configure(int precision) {
   cudaError_t e = precision == LBM_F64 ? fd2d_tile_configure<double>() : fd2d_tile_configure<float>();
+  if (e == cudaSuccess && precision != LBM_F64) e = fd2d_block_configure();
   if (e != cudaSuccess) return e;
   if (precision == LBM_F64) return collide2d_async_configure<double>();
   if (precision == LBM_F32DEV) return collide2d_async_configure<float>();

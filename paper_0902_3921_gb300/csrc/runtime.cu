@@ -320,7 +320,10 @@ int autotune_2d(lbm_handle *h) {
   if (const char *fixed = std::getenv("HLBM_TUNING")) {
     int v[5] = {h->sub, h->fd_rows, h->fd_cols, h->collide_rows, 0};
     const int nv = std::sscanf(fixed, "%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4]);
-    if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64))) && v[0] >= 1 &&
+    const bool block_ok = v[4] == 128 && h->P.precision != LBM_F64 &&
+                          ((v[0] == 1 && v[1] == 4) || (v[0] == 2 && (v[1] == 4 || v[1] == 5)) ||
+                           (v[0] == 4 && (v[1] == 5 || v[1] == 6)));
+    if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
         (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV))) {
       h->sub = std::min(v[0], h->m);
@@ -331,6 +334,10 @@ int autotune_2d(lbm_handle *h) {
       if (h->fd_tile_w == 32) h->sub = 1;
       if (h->fd_tile_w == 64) h->sub = std::min(h->sub, 2);
       return LBM_OK;
+    }
+    if (nv == 5 && v[4] == 128 && !block_ok) {
+      return fail(h, LBM_EINVAL,
+                  "HLBM_TUNING block kernel shapes (sub,rows): (1,4) (2,4) (2,5) (4,5) (4,6), FP32 only");
     }
     return fail(h, LBM_EINVAL, "HLBM_TUNING must be 'sub,rows,cols,collide_rows[,tile]'");
   }
@@ -366,6 +373,18 @@ int autotune_2d(lbm_handle *h) {
     int tile_w, cols, sub, rows;
   };
   std::vector<FdShape> cands;
+  // block kernel (FP32): 128-column regions, (substeps, rows per warp)
+  if (h->P.precision != LBM_F64) {
+    if (h->m >= 4) {
+      cands.push_back({128, 4, 4, 5});
+      cands.push_back({128, 4, 4, 6});
+    }
+    if (h->m >= 2) {
+      cands.push_back({128, 4, 2, 4});
+      cands.push_back({128, 4, 2, 5});
+    }
+    cands.push_back({128, 4, 1, 4});
+  }
   // shared-memory tile kernel: 64 wide with 1 or 2 substeps, 32 wide with 1
   cands.push_back({32, 4, 1, 32});
   cands.push_back({64, 4, 1, 32});

@@ -373,6 +373,51 @@ def test_every_launch_shape(shape, precision, monkeypatch):
     assert t["fd_tile_width"] == int(shape.split(",")[4])
 
 
+# FP32 block kernel shapes (substeps, rows per warp; tile 128)
+BLOCK_SHAPES = ["4,5,2,1,128", "4,6,2,1,128", "2,4,2,1,128", "2,5,2,1,128", "1,4,2,1,128"]
+
+
+def _fp32_bar(ref, lat, tag):
+    dphi, du, dn = _errors(ref, lat)
+    _, ru = ref.moments()
+    umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+    assert dphi <= 1e-5 and du <= 1e-3 * umax, (tag, dphi, du, umax)
+
+
+@pytest.mark.parametrize("shape", BLOCK_SHAPES)
+@pytest.mark.parametrize("size", [(70, 45), (300, 217)])
+def test_block_kernel_shapes(shape, size, monkeypatch):
+    """The FP32 block FD kernel: a lattice smaller than one 128-column region
+    (the region wraps around it) and one of several regions with ragged
+    edges; m = 5 adds a remainder launch."""
+    monkeypatch.setenv("HLBM_TUNING", shape)
+    Lx, Ly = size
+    op, lp = _pair(Lx, Ly, m=5, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.drop(2, Lx, Ly, R=min(Lx, Ly) // 4, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, Lx, Ly)
+    u = u + 0.003 * np.sin(np.arange(Lx) / 4.0)[None, None, :]
+    ref, lat = _run_both(op, lp, n, phi, u, 12)
+    _fp32_bar(ref, lat, shape)
+    assert lbm.lbm_tuning(lat.handle)["fd_tile_width"] == 128
+
+
+@pytest.mark.parametrize("shape", ["4,5,2,1,128", "2,4,2,1,128"])
+def test_block_kernel_flux_variant(shape, monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", shape)
+    op, lp = _pair(150, 90, m=4, adv_variant=1, cubic_at_half=1, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.drop(2, 150, 90, R=20, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 150, 90)
+    u = u + 0.003 * np.cos(np.arange(90) / 3.0)[None, :, None]
+    ref, lat = _run_both(op, lp, n, phi, u, 15)
+    _fp32_bar(ref, lat, shape)
+
+
+def test_block_kernel_refused_in_fp64(monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", "4,5,2,1,128")
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(lbm.LbmParams(Lx=64, Ly=64, precision=lbm.LBM_F64, **CFG1))
+
+
 @pytest.mark.parametrize("shape", ["4,16,4,2,0", "1,32,4,0,32", "2,32,4,0,64"])
 def test_launch_shapes_flux_variant(shape, monkeypatch):
     monkeypatch.setenv("HLBM_TUNING", shape)
