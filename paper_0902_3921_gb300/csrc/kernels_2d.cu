@@ -870,9 +870,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---- FD convection-diffusion: block kernel, one 128-column region per CTA ----
-// FP32 only.  A CTA of FDB_NW warps owns a region 128 columns wide and RY =
-// K FDB_NW rows high, whose inner (128 - 2H) x (RY - 2H) sites are written
-// (H = 3 SUB).  Warp w owns rows w, w + FDB_NW, ...; lane l owns the four
+// FP32 only.  A CTA of NW warps owns a region 128 columns wide and RY =
+// K NW rows high, whose inner (128 - 2H) x (RY - 2H) sites are written
+// (H = 3 SUB).  Warp w owns rows w, w + NW, ...; lane l owns the four
 // columns 4l .. 4l + 3 of each, so every shared-memory access is one float4
 // per lane (row pitch 128 floats: a warp reads 512 contiguous bytes) and the
 // x neighbours come from the adjacent lanes by shuffles.  Columns 0 and 127
@@ -881,12 +881,11 @@ __global__ void __launch_bounds__(256)
 // computed once per launch and kept in registers for all SUB substeps.
 // Shared memory: phi, phih and psi planes of RY x 128 floats; each substep
 // is three phases over a region that shrinks by one site per phase.
-constexpr int FDB_NW = 16;
 constexpr int FDB_RX = 128;
 
-template <int SUB, int K>
+template <int SUB, int K, int NW>
 struct FDBlock {
-  static constexpr int H = 3 * SUB, RY = K * FDB_NW, TX = FDB_RX - 2 * H, TY = RY - 2 * H;
+  static constexpr int H = 3 * SUB, RY = K * NW, TX = FDB_RX - 2 * H, TY = RY - 2 * H;
   static constexpr size_t smem = sizeof(float) * 3 * (size_t)RY * FDB_RX;
 };
 
@@ -901,11 +900,11 @@ __device__ __forceinline__ float comp(const float4 &v, int j) {
 }
 __device__ __forceinline__ float4 mk4(const float (&e)[4]) { return make_float4(e[0], e[1], e[2], e[3]); }
 
-template <bool FLUX, int SUB, int K>
-__global__ void __launch_bounds__(FDB_NW * 32, 1)
+template <bool FLUX, int SUB, int K, int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
     fd2d_block_kernel(const float *__restrict__ phi_in, const float *__restrict__ u,
                       float *__restrict__ phi_out, KParams<float> p) {
-  using G = FDBlock<SUB, K>;
+  using G = FDBlock<SUB, K, NW>;
   constexpr int H = G::H, RY = G::RY, TX = G::TX, TY = G::TY, NC = FLUX ? 4 : 3;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) float fdb_smem[];
@@ -921,7 +920,7 @@ __global__ void __launch_bounds__(FDB_NW * 32, 1)
   //    coefficients are in registers)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int r = warp + FDB_NW * k;
+    const int r = warp + NW * k;
     const long long row = (long long)wrapi(y0 + r, Ly) * Lx;
     float e[4], f[4], g[4];
 #pragma unroll
@@ -942,7 +941,7 @@ __global__ void __launch_bounds__(FDB_NW * 32, 1)
   float T[K][NC][4];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int r = warp + FDB_NW * k;
+    const int r = warp + NW * k;
     const int rm = r > 0 ? r - 1 : r, rp = r < RY - 1 ? r + 1 : r;  // row 0 / RY-1: never valid
     const float4 uc = ld4(sa, r, c), vc = ld4(sq, r, c), vm = ld4(sq, rm, c), vp = ld4(sq, rp, c);
     const float uL0 = __shfl_up_sync(FULL, uc.w, 1), uR3 = __shfl_down_sync(FULL, uc.x, 1);
@@ -970,7 +969,7 @@ __global__ void __launch_bounds__(FDB_NW * 32, 1)
     int lo = 3 * s + 1;  // phih = advected phi
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = warp + FDB_NW * k;
+      const int r = warp + NW * k;
       if (r < lo || r >= RY - lo) continue;  // warp-uniform
       const float4 pc = ld4(sp, r, c), pu = ld4(sp, r - 1, c), pd = ld4(sp, r + 1, c);
       const float l0 = __shfl_up_sync(FULL, pc.w, 1), r3 = __shfl_down_sync(FULL, pc.x, 1);
@@ -1000,7 +999,7 @@ __global__ void __launch_bounds__(FDB_NW * 32, 1)
     lo = 3 * s + 2;  // psi = a phih + b phi^3 - kappa lap phih (Eq. 36)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = warp + FDB_NW * k;
+      const int r = warp + NW * k;
       if (r < lo || r >= RY - lo) continue;
       const float4 ac = ld4(sa, r, c), au = ld4(sa, r - 1, c), ad = ld4(sa, r + 1, c);
       const float4 pc = ld4(sp, r, c);
@@ -1024,7 +1023,7 @@ __global__ void __launch_bounds__(FDB_NW * 32, 1)
     const bool last = s == SUB - 1;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = warp + FDB_NW * k;
+      const int r = warp + NW * k;
       if (r < lo || r >= RY - lo) continue;
       const float4 qc = ld4(sq, r, c), qu = ld4(sq, r - 1, c), qd = ld4(sq, r + 1, c);
       const float4 ac = ld4(sa, r, c);
@@ -1191,32 +1190,33 @@ cudaError_t fd2d_tile_one(lbm_handle *h, const KParams<C> &p, const C *src, C *d
   return cudaGetLastError();
 }
 
-template <bool FLUX, int SUB, int K>
+template <bool FLUX, int SUB, int K, int NW>
 cudaError_t fd2d_block_one(lbm_handle *h, const KParams<float> &p, const float *src, float *dst) {
-  using G = FDBlock<SUB, K>;
+  using G = FDBlock<SUB, K, NW>;
   dim3 grid((p.Lx + G::TX - 1) / G::TX, (p.Ly + G::TY - 1) / G::TY);
-  fd2d_block_kernel<FLUX, SUB, K><<<grid, FDB_NW * 32, G::smem, h->stream>>>(
+  fd2d_block_kernel<FLUX, SUB, K, NW><<<grid, NW * 32, G::smem, h->stream>>>(
       src, static_cast<const float *>(h->u), dst, p);
   return cudaGetLastError();
 }
 
-// block kernel shapes (substeps per launch, rows per warp)
-#define FDB_SHAPES(X) X(1, 4) X(2, 4) X(2, 5) X(4, 5) X(4, 6)
+// block kernel shapes (substeps per launch, region rows RY, warps); the
+// tuning fields carry them as sub, rows = RY, cols = warps / 8
+#define FDB_SHAPES(X) X(1, 64, 16) X(2, 64, 16) X(2, 80, 16) X(4, 80, 16) X(4, 96, 16) X(4, 96, 32) X(2, 96, 32)
 
 template <typename C>
 cudaError_t fd2d_block(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub) {
   if constexpr (std::is_same<C, float>::value) {
     const bool flux = p.adv_variant == LBM_ADV_FLUX;
-#define FDB_CASE(SB, KK)                                                            \
-  if (sub == SB && h->fd_rows == KK)                                               \
-    return flux ? fd2d_block_one<true, SB, KK>(h, p, src, dst)                     \
-                : fd2d_block_one<false, SB, KK>(h, p, src, dst);
+#define FDB_CASE(SB, RYY, NWW)                                                      \
+  if (sub == SB && h->fd_rows == RYY && h->fd_cols * 8 == NWW)                     \
+    return flux ? fd2d_block_one<true, SB, RYY / NWW, NWW>(h, p, src, dst)         \
+                : fd2d_block_one<false, SB, RYY / NWW, NWW>(h, p, src, dst);
     FDB_SHAPES(FDB_CASE)
 #undef FDB_CASE
     // a remainder launch with fewer substeps than the shape
-    if (sub == 1) return flux ? fd2d_block_one<true, 1, 4>(h, p, src, dst) : fd2d_block_one<false, 1, 4>(h, p, src, dst);
-    if (sub == 2) return flux ? fd2d_block_one<true, 2, 4>(h, p, src, dst) : fd2d_block_one<false, 2, 4>(h, p, src, dst);
-    return flux ? fd2d_block_one<true, 4, 5>(h, p, src, dst) : fd2d_block_one<false, 4, 5>(h, p, src, dst);
+    if (sub == 1) return flux ? fd2d_block_one<true, 1, 4, 16>(h, p, src, dst) : fd2d_block_one<false, 1, 4, 16>(h, p, src, dst);
+    if (sub == 2) return flux ? fd2d_block_one<true, 2, 4, 16>(h, p, src, dst) : fd2d_block_one<false, 2, 4, 16>(h, p, src, dst);
+    return flux ? fd2d_block_one<true, 4, 5, 16>(h, p, src, dst) : fd2d_block_one<false, 4, 5, 16>(h, p, src, dst);
   }
   return cudaErrorInvalidValue;
 }
@@ -1229,13 +1229,15 @@ cudaError_t fd2d_tile(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, 
 
 cudaError_t fd2d_block_configure() {
   cudaError_t e = cudaSuccess;
-#define FDB_CFG(SB, KK)                                                                         \
+#define FDB_CFG(SB, RYY, NWW)                                                                   \
   if (e == cudaSuccess)                                                                         \
-    e = cudaFuncSetAttribute(fd2d_block_kernel<false, SB, KK>,                                  \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FDBlock<SB, KK>::smem); \
+    e = cudaFuncSetAttribute(fd2d_block_kernel<false, SB, RYY / NWW, NWW>,                      \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,                        \
+                             (int)FDBlock<SB, RYY / NWW, NWW>::smem);                            \
   if (e == cudaSuccess)                                                                         \
-    e = cudaFuncSetAttribute(fd2d_block_kernel<true, SB, KK>,                                   \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FDBlock<SB, KK>::smem);
+    e = cudaFuncSetAttribute(fd2d_block_kernel<true, SB, RYY / NWW, NWW>,                       \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,                        \
+                             (int)FDBlock<SB, RYY / NWW, NWW>::smem);
   FDB_SHAPES(FDB_CFG)
 #undef FDB_CFG
   return e;

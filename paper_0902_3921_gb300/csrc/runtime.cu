@@ -320,9 +320,11 @@ int autotune_2d(lbm_handle *h) {
   if (const char *fixed = std::getenv("HLBM_TUNING")) {
     int v[5] = {h->sub, h->fd_rows, h->fd_cols, h->collide_rows, 0};
     const int nv = std::sscanf(fixed, "%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4]);
-    const bool block_ok = v[4] == 128 && h->P.precision != LBM_F64 &&
-                          ((v[0] == 1 && v[1] == 4) || (v[0] == 2 && (v[1] == 4 || v[1] == 5)) ||
-                           (v[0] == 4 && (v[1] == 5 || v[1] == 6)));
+    // block kernel shapes: sub, region rows, warps / 8
+    const int shapes[7][3] = {{1, 64, 2}, {2, 64, 2}, {2, 80, 2}, {4, 80, 2}, {4, 96, 2}, {4, 96, 4}, {2, 96, 4}};
+    bool block_ok = false;
+    for (const auto &sh : shapes)
+      block_ok |= v[4] == 128 && h->P.precision != LBM_F64 && v[0] == sh[0] && v[1] == sh[1] && v[2] == sh[2];
     if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
         (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV))) {
@@ -337,7 +339,8 @@ int autotune_2d(lbm_handle *h) {
     }
     if (nv == 5 && v[4] == 128 && !block_ok) {
       return fail(h, LBM_EINVAL,
-                  "HLBM_TUNING block kernel shapes (sub,rows): (1,4) (2,4) (2,5) (4,5) (4,6), FP32 only");
+                  "HLBM_TUNING block kernel shapes (sub,rows,cols): (1,64,2) (2,64,2) (2,80,2) (4,80,2) "
+                  "(4,96,2) (4,96,4) (2,96,4), FP32 only");
     }
     return fail(h, LBM_EINVAL, "HLBM_TUNING must be 'sub,rows,cols,collide_rows[,tile]'");
   }
@@ -376,14 +379,16 @@ int autotune_2d(lbm_handle *h) {
   // block kernel (FP32): 128-column regions, (substeps, rows per warp)
   if (h->P.precision != LBM_F64) {
     if (h->m >= 4) {
-      cands.push_back({128, 4, 4, 5});
-      cands.push_back({128, 4, 4, 6});
+      cands.push_back({128, 2, 4, 80});
+      cands.push_back({128, 2, 4, 96});
+      cands.push_back({128, 4, 4, 96});
     }
     if (h->m >= 2) {
-      cands.push_back({128, 4, 2, 4});
-      cands.push_back({128, 4, 2, 5});
+      cands.push_back({128, 2, 2, 64});
+      cands.push_back({128, 2, 2, 80});
+      cands.push_back({128, 4, 2, 96});
     }
-    cands.push_back({128, 4, 1, 4});
+    cands.push_back({128, 2, 1, 64});
   }
   // shared-memory tile kernel: 64 wide with 1 or 2 substeps, 32 wide with 1
   cands.push_back({32, 4, 1, 32});

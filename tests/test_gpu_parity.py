@@ -373,8 +373,9 @@ def test_every_launch_shape(shape, precision, monkeypatch):
     assert t["fd_tile_width"] == int(shape.split(",")[4])
 
 
-# FP32 block kernel shapes (substeps, rows per warp; tile 128)
-BLOCK_SHAPES = ["4,5,2,1,128", "4,6,2,1,128", "2,4,2,1,128", "2,5,2,1,128", "1,4,2,1,128"]
+# FP32 block kernel shapes (substeps, region rows, warps / 8; tile 128)
+BLOCK_SHAPES = ["4,80,2,1,128", "4,96,2,1,128", "4,96,4,1,128", "2,64,2,1,128", "2,80,2,1,128",
+                "2,96,4,1,128", "1,64,2,1,128"]
 
 
 def _fp32_bar(ref, lat, tag):
@@ -401,7 +402,7 @@ def test_block_kernel_shapes(shape, size, monkeypatch):
     assert lbm.lbm_tuning(lat.handle)["fd_tile_width"] == 128
 
 
-@pytest.mark.parametrize("shape", ["4,5,2,1,128", "2,4,2,1,128"])
+@pytest.mark.parametrize("shape", ["4,80,2,1,128", "2,64,2,1,128", "4,96,4,1,128"])
 def test_block_kernel_flux_variant(shape, monkeypatch):
     monkeypatch.setenv("HLBM_TUNING", shape)
     op, lp = _pair(150, 90, m=4, adv_variant=1, cubic_at_half=1, precision=lbm.LBM_F32DEV, **CFG1)
@@ -413,7 +414,7 @@ def test_block_kernel_flux_variant(shape, monkeypatch):
 
 
 def test_block_kernel_refused_in_fp64(monkeypatch):
-    monkeypatch.setenv("HLBM_TUNING", "4,5,2,1,128")
+    monkeypatch.setenv("HLBM_TUNING", "4,80,2,1,128")
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(lbm.LbmParams(Lx=64, Ly=64, precision=lbm.LBM_F64, **CFG1))
 
