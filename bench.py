@@ -408,6 +408,146 @@ def run_batched(args, rank, world, local):
             "speedup_vs_plain": value / plain, "clocks": clocks.summary()}), flush=True)
 
 
+SURR_SIDE = 2048
+SURR_WINDOW = 50  # LB steps one forward pass replaces
+# algorithmic bytes per pixel of one 32 -> 32 convolution layer: BF16 input
+# and output activations, 32 channels each; FLOPs per pixel 2 x 9 x 32 x 32
+CONV_BYTES_PER_PX = 128
+CONV_FLOPS_PER_PX = 2 * 9 * 32 * 32
+
+
+def cpu_surrogate_forward(side=64, reps=1):
+    """The FP64 reference network (oracle/surrogate.py) on a side^2 lattice:
+    pixels per second of one forward pass (single thread)."""
+    from oracle import surrogate as OS
+    rng = np.random.default_rng(0)
+    chans = [4] + [32] * 5 + [4]
+    params = [(rng.standard_normal((co, 3, 3, ci)) * 0.1, np.zeros(co)) for ci, co in zip(chans[:-1], chans[1:])]
+    x = rng.standard_normal((1, side, side, 4))
+    t = time.perf_counter()
+    for _ in range(reps):
+        OS.forward(params, x)
+    dt = time.perf_counter() - t
+    return side * side * reps / dt, dt
+
+
+def run_surrogate(args, rank, world, local):
+    """The learned surrogate's step, x_{t+50} = x_t + Net(x_t), on the 2048^2
+    inference lattice: six periodic 3x3 convolutions (4 -> 32 -> ... -> 32 ->
+    4), BF16 weights and activations, FP32 accumulation on the tcgen05 tensor
+    cores.  Weights are random (throughput does not depend on their values).
+    value = lattice updates per second the forward pass stands in for
+    (2048^2 sites x 50 LB steps per pass); the plain scheme is timed on the
+    same lattice beside it."""
+    import torch
+    from paper_0902_3921_gb300 import build as B
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    B.build()
+    lbm.load_library()
+    S = SURR_SIDE
+    P = S * S
+    stream = torch.cuda.Stream()
+    net = lbm.Net(32, 6, seed=1)
+    net.set_normalisation([0.0, 0.0, 0.0, 0.0], [0.6, 2e-3, 2e-3, 3e-3], [0.05, 1e-3, 1e-3, 1e-3])
+    g = torch.Generator(device="cuda").manual_seed(rank)
+    x0 = (0.5 * torch.randn(P * 4, device="cuda", generator=g)).contiguous()
+    x1 = torch.empty_like(x0)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            net.forward(x0.data_ptr(), 1, S, S, x1.data_ptr(), stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 400)  # about 0.3 s, long enough for the clock samples
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+            for _ in range(steps):
+                net.forward(x0.data_ptr(), 1, S, S, x1.data_ptr(), stream=stream.cuda_stream)
+            t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    value = P * SURR_WINDOW / (ms / 1000.0) / 1e6
+    layer_ms = net.layer_times(x0.data_ptr(), 1, S, S, reps=max(3, args.steps // 2),
+                               stream=stream.cuda_stream)
+    dom = max(range(1, 5), key=lambda l: layer_ms[l])  # a 32 -> 32 layer
+    conv_s = layer_ms[dom] / 1000.0
+    achieved = CONV_BYTES_PER_PX * P / conv_s / 1e9
+    hbm_peak, hbm_kind = measured_peak()
+    tensor_tflops = CONV_FLOPS_PER_PX * P / conv_s / 1e12
+    bf16_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = json.load(f).get("bf16_tflops")
+    except OSError:
+        pass
+    # e2e: pinned host state in, prediction out, every step
+    hx0 = torch.empty(P * 4, dtype=torch.float32, pin_memory=True)
+    hx0.copy_(x0.cpu())
+    hx1 = torch.empty_like(hx0, pin_memory=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            x0.copy_(hx0, non_blocking=True)
+            net.forward(x0.data_ptr(), 1, S, S, x1.data_ptr(), stream=stream.cuda_stream)
+            hx1.copy_(x1, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    net.close()
+    # the plain scheme on the same lattice: 50 LB steps per window
+    lat = lbm.Lattice(lbm.LbmParams(Lx=S, Ly=S, fd_substeps=M_SUB, precision=lbm.LBM_F32DEV, **CFG),
+                      stream=stream.cuda_stream)
+    phi = I.spinodal(2, S, S, seed=rank, amp=0.01)
+    n, u = I.rest(2, S, S)
+    lat.init_fields(n, phi, u)
+    with torch.cuda.stream(stream):
+        lat.step(SURR_WINDOW)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        lat.step(SURR_WINDOW * 4)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = t0.elapsed_time(t1) / 4
+    plain = P * SURR_WINDOW / (ms_plain / 1000.0) / 1e6
+    lat.close()
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        pxs, secs = cpu_surrogate_forward(side=256, reps=3)
+        cpu = {"value": pxs * SURR_WINDOW / 1e6, "unit": "MLUPS-equivalent", "cores": 1, "kind": "oracle",
+               "sample": f"three FP64 forward passes of the same network on a 256x256 lattice ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "MLUPS-equivalent of the surrogate step (2048^2, 50 LB steps per pass)",
+            "value": value, "unit": "MLUPS", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "surrogate-2048x2048-6x3x3conv-32ch", "pixels": P,
+                       "window_lb_steps": SURR_WINDOW, "layers": 6, "channels": 32,
+                       "l2": "activations (256 MiB per 32-channel layer) exceed L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": f"conv_tc layer {dom} (32 -> 32, tcgen05)",
+                         "bytes_per_px": CONV_BYTES_PER_PX, "avg_launch_us": layer_ms[dom] * 1000.0,
+                         "peak_kind": hbm_kind,
+                         "tensor": {"achieved": tensor_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                    "frac": (tensor_tflops / bf16_peak) if bf16_peak else None}},
+            "layer_us": [v * 1000.0 for v in layer_ms],
+            "plain_scheme": {"value": plain, "unit": "MLUPS", "lattice": [S, S]},
+            "speedup_vs_plain_per_window": value / plain,
+            "cpu_baseline": cpu,
+            "e2e": {"value": P * SURR_WINDOW / (ms_e2e / 1000.0) / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": P * 16, "d2h_bytes_per_step": P * 16},
+            "gpu_launches": 8 * steps,
+            "clocks": clocks.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,7 +561,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no kernel timing, e2e or CPU baseline)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one")
-    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched"])
+    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "surrogate"])
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--plain-steps", type=int, default=10)
     args = ap.parse_args()
@@ -430,6 +570,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched":
         run_batched(args, rank, world, local)
+    elif args.workload == "surrogate":
+        run_surrogate(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

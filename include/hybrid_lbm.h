@@ -240,6 +240,13 @@ int lbm_net_normalisation(const lbm_net *net, float *out12);
 /* x1 = prediction of the state one window after x0 (device arrays). */
 int lbm_net_forward(lbm_net *net, const float *x0, int N, int H, int W, float *x1,
                     void *cuda_stream);
+/* Timing of the forward pass: runs it reps + 1 times on x0 (device array,
+ * first run a warm-up) with CUDA events recorded on the stream around each
+ * convolution launch, and writes the mean milliseconds of each layer's launch
+ * into the host array ms[layers]; synchronises the stream.  The paper has no
+ * counterpart (a measurement entry point). */
+int lbm_net_layer_times(lbm_net *net, const float *x0, int N, int H, int W, int reps, float *ms,
+                        void *cuda_stream);
 /* One training step on pairs (x0, x1): MSE between Net(x0) and the normalised
  * change, backward pass, and (update != 0) one Adam step with rate lr.  *loss
  * (may be NULL) receives the loss before the update; waits for the stream. */

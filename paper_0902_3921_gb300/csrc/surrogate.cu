@@ -503,11 +503,21 @@ int check_shape(lbm_net *net, int N, int H, int W) {
   return LBM_OK;
 }
 
-// forward pass on net->x0 (raw state, P pixels) -> net->yout
-int forward_raw(lbm_net *net, int N, int H, int W, cudaStream_t s) {
+// a failed (timed-out) completion wait inside a tensor-core convolution
+// since the last check, seen after the stream has been synchronised
+int check_conv(lbm_net *net) {
+  if (conv_tc_error(true) != 0)
+    return nfail(net, LBM_ETIMEOUT, "tensor-core convolution: an MMA completion wait timed out");
+  return LBM_OK;
+}
+
+// forward pass on net->x0 (raw state, P pixels) -> net->yout; ev (optional)
+// holds layers + 1 events recorded around the convolution launches
+int forward_raw(lbm_net *net, int N, int H, int W, cudaStream_t s, cudaEvent_t *ev = nullptr) {
   const long long P = (long long)N * H * W;
   normalise_kernel<<<nblk(P, 256), 256, 0, s>>>(net->x0, P, W, net->nrm, net->act[0]);
   NCK(net, cudaGetLastError(), "normalise kernel");
+  if (ev) NCK(net, cudaEventRecord(ev[0], s), "cudaEventRecord");
   for (int l = 0; l < net->layers; l++) {
     const Layer &Ly = net->L[l];
     const bool last = l == net->layers - 1;
@@ -515,6 +525,7 @@ int forward_raw(lbm_net *net, int N, int H, int W, cudaStream_t s) {
                       net->wbf + Ly.woff, net->b32 + Ly.boff, nullptr, N, H, W,
                       last ? nullptr : net->act[l + 1], last ? net->yout : nullptr, s),
         "conv forward");
+    if (ev) NCK(net, cudaEventRecord(ev[l + 1], s), "cudaEventRecord");
   }
   return LBM_OK;
 }
@@ -683,6 +694,35 @@ int lbm_net_forward(lbm_net *net, const float *x0, int N, int H, int W, float *x
   return LBM_OK;
 }
 
+int lbm_net_layer_times(lbm_net *net, const float *x0, int N, int H, int W, int reps, float *ms,
+                        void *cuda_stream) {
+  if (!net || !x0 || !ms || reps < 1) return LBM_EINVAL;
+  int rc = check_shape(net, N, H, W);
+  if (rc) return rc;
+  const long long P = (long long)N * H * W;
+  rc = ensure_workspace(net, P);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  NCK(net, cudaMemcpyAsync(net->x0, x0, sizeof(float) * 4 * P, cudaMemcpyDeviceToDevice, s), "copy");
+  std::vector<cudaEvent_t> ev(net->layers + 1);
+  for (auto &e : ev) NCK(net, cudaEventCreate(&e), "cudaEventCreate");
+  std::vector<double> acc(net->layers, 0.0);
+  for (int r = 0; r <= reps && rc == LBM_OK; r++) {  // r = 0: warm-up
+    rc = forward_raw(net, N, H, W, s, ev.data());
+    if (rc == LBM_OK && cudaStreamSynchronize(s) != cudaSuccess)
+      rc = nfail(net, LBM_ECUDA, "synchronize");
+    for (int l = 0; l < net->layers && rc == LBM_OK && r > 0; l++) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[l], ev[l + 1]);
+      acc[l] += t;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (int l = 0; l < net->layers; l++) ms[l] = (float)(acc[l] / reps);
+  return check_conv(net);
+}
+
 int lbm_net_train_step(lbm_net *net, const float *x0, const float *x1, int N, int H, int W, float lr,
                        int update, double *loss, void *cuda_stream) {
   if (!net || !x0 || !x1) return LBM_EINVAL;
@@ -737,6 +777,7 @@ int lbm_net_train_step(lbm_net *net, const float *x0, const float *x1, int N, in
     double acc = 0.0;
     for (double v : part) acc += v;
     *loss = acc;
+    return check_conv(net);
   }
   return LBM_OK;
 }
@@ -823,7 +864,7 @@ int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_s
   }
   if (fallbacks) *fallbacks = nfb;
   NCK(net, cudaStreamSynchronize(s), "synchronize");
-  return LBM_OK;
+  return check_conv(net);
 }
 
 void lbm_net_free(lbm_net *net) {

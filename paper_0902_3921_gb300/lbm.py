@@ -34,7 +34,8 @@ EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_popu
            "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_graphs", "lbm_batch_shape",
            "lbm_batch_synchronize", "lbm_batch_free", "lbm_batch_last_error", "lbm_net_create",
            "lbm_net_param_count", "lbm_net_params", "lbm_net_grads", "lbm_net_set_normalisation",
-           "lbm_net_normalisation", "lbm_net_forward", "lbm_net_train_step", "lbm_surrogate_state",
+           "lbm_net_normalisation", "lbm_net_forward", "lbm_net_layer_times", "lbm_net_train_step",
+           "lbm_surrogate_state",
            "lbm_surrogate_advance", "lbm_net_free", "lbm_net_last_error")
 
 
@@ -134,6 +135,7 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_net_set_normalisation.argtypes = [Nt, fp, fp, fp]
     lib.lbm_net_normalisation.argtypes = [Nt, fp]
     lib.lbm_net_forward.argtypes = [Nt, vp, ip, ip, ip, vp, vp]
+    lib.lbm_net_layer_times.argtypes = [Nt, vp, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_float), vp]
     lib.lbm_net_train_step.argtypes = [Nt, vp, vp, ip, ip, ip, ctypes.c_float, ip,
                                        ctypes.POINTER(ctypes.c_double), vp]
     lib.lbm_surrogate_state.argtypes = [H, vp]
@@ -144,7 +146,7 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_net_last_error.argtypes = [Nt]
     lib.lbm_net_last_error.restype = ctypes.c_char_p
     for name in ("lbm_net_create", "lbm_net_params", "lbm_net_grads", "lbm_net_set_normalisation",
-                 "lbm_net_normalisation", "lbm_net_forward", "lbm_net_train_step",
+                 "lbm_net_normalisation", "lbm_net_forward", "lbm_net_layer_times", "lbm_net_train_step",
                  "lbm_surrogate_state", "lbm_surrogate_advance"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_moments",
@@ -534,6 +536,14 @@ class Net:
         self._check(load_library().lbm_net_forward(self.handle, ctypes.c_void_p(x0_ptr), N, H, W,
                                                    ctypes.c_void_p(x1_ptr),
                                                    ctypes.c_void_p(stream or 0)), "lbm_net_forward")
+
+    def layer_times(self, x0_ptr, N, H, W, reps=10, stream=None):
+        """Mean milliseconds of each convolution layer's launch (CUDA events)."""
+        ms = (ctypes.c_float * self.layers)()
+        self._check(load_library().lbm_net_layer_times(self.handle, ctypes.c_void_p(x0_ptr), N, H, W,
+                                                       int(reps), ms, ctypes.c_void_p(stream or 0)),
+                    "lbm_net_layer_times")
+        return [float(v) for v in ms]
 
     def train_step(self, x0_ptr, x1_ptr, N, H, W, lr, update=True, stream=None):
         loss = ctypes.c_double()

@@ -285,3 +285,13 @@ def test_train_and_evaluate_end_to_end():
     assert abs(last["sum_phi_surrogate"] - last["sum_phi_plain"]) <= 0.02 * 128 * 128
     assert 0.5 < last["L_surrogate"] / last["L_plain"] < 2.0
     net.close()
+
+
+def test_layer_times_report_every_layer():
+    net, _ = _random_net(32, 6, seed=3)
+    net.set_normalisation(*NORM)
+    x0, _ = _inputs(1, 8, 256, 2)
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    ms = net.layer_times(d0.data_ptr(), 1, 8, 256, reps=3)
+    assert len(ms) == 6 and all(t > 0 for t in ms)
+    net.close()
