@@ -46,6 +46,11 @@ COLLIDE_BYTES_PER_SITE = 76
 FD_FLOPS_PER_SITE_SUBSTEP = 41
 # FP32 pipe peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the 1024^2 workload (profiles/collide2d_fd2d_spinodal1024.md),
+# valid for the kernel shapes captured there: the FD block kernel with 4
+# substeps, 96-row regions and 16 warps, and the collide kernel's 3-CTA variant
+NCU_TRAFFIC_1024 = {"fd": ((128, 96, 4, 2), 12.627456e6), "collide": (1, 41.967872e6 + 2.707712e6)}
 METRIC = "MLUPS (D2Q9 hybrid LB + FD step)"
 WORKLOAD = "spinodal-1024x1024-d2q9-f32dev"
 
@@ -246,18 +251,28 @@ def run_ours(args, rank, world, local):
     fd_ms, fd_n = kt["fd"]
     coll_avg_s = coll_ms / coll_n / 1000.0
     fd_avg_s = fd_ms / max(fd_n, 1) / 1000.0
+    fd_launches_per_step = max(fd_n, 1) / 2000.0
     achieved = COLLIDE_BYTES_PER_SITE * S / coll_avg_s / 1e9
     peak, peak_kind = measured_peak()
+    shape_fd = (tuning["fd_tile_width"], tuning["fd_rows_per_warp"], tuning["fd_substeps_per_launch"],
+                tuning["fd_cols_per_lane"])
+    traffic_fd = NCU_TRAFFIC_1024["fd"][1] if side == 1024 and shape_fd == NCU_TRAFFIC_1024["fd"][0] else None
+    traffic_coll = (NCU_TRAFFIC_1024["collide"][1]
+                    if side == 1024 and tuning["collide_sites_per_thread"] == NCU_TRAFFIC_1024["collide"][0]
+                    else None)
     roof_collide = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic_coll,
                     "kernel": "collide2d (stencil force + collide + stream)",
                     "bytes_per_site": COLLIDE_BYTES_PER_SITE, "avg_launch_us": coll_avg_s * 1e6,
                     "peak_kind": peak_kind, "share_of_step": coll_ms / (coll_ms + fd_ms)}
-    fd_tflops = FD_FLOPS_PER_SITE_SUBSTEP * M_SUB * S / fd_avg_s / 1e12
+    # FLOPs of one launch: the m substeps of an LB step spread over its launches
+    fd_flops_launch = FD_FLOPS_PER_SITE_SUBSTEP * M_SUB * S / fd_launches_per_step
+    fd_tflops = fd_flops_launch / fd_avg_s / 1e12
     roof_fd = {"bound": "alu", "achieved": fd_tflops, "peak": FP32_PEAK_TFLOPS,
-               "unit": "TFLOP/s", "frac": fd_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+               "unit": "TFLOP/s", "frac": fd_tflops / FP32_PEAK_TFLOPS, "traffic": traffic_fd,
                "kernel": "fd2d (m = 4 FD substeps of Eqs. 32-36)",
                "flops_per_site": FD_FLOPS_PER_SITE_SUBSTEP * M_SUB,
+               "launches_per_lb_step": fd_launches_per_step,
                "avg_launch_us": fd_avg_s * 1e6, "peak_kind": "derived (unit counts x clock)",
                "share_of_step": fd_ms / (coll_ms + fd_ms)}
     dominant, other = (roof_fd, roof_collide) if fd_ms > coll_ms else (roof_collide, roof_fd)
@@ -414,6 +429,9 @@ SURR_WINDOW = 50  # LB steps one forward pass replaces
 # and output activations, 32 channels each; FLOPs per pixel 2 x 9 x 32 x 32
 CONV_BYTES_PER_PX = 128
 CONV_FLOPS_PER_PX = 2 * 9 * 32 * 32
+# DRAM bytes of one 32 -> 32 layer launch at 2048^2 from one ncu capture
+# (profiles/conv_tc_surrogate2048.md)
+NCU_TRAFFIC_CONV_2048 = 278.498816e6 + 222.286080e6
 
 
 def cpu_surrogate_forward(side=64, reps=1):
@@ -532,7 +550,8 @@ def run_surrogate(args, rank, world, local):
                        "window_lb_steps": SURR_WINDOW, "layers": 6, "channels": 32,
                        "l2": "activations (256 MiB per 32-channel layer) exceed L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak,
+                         "traffic": NCU_TRAFFIC_CONV_2048 if S == 2048 else None,
                          "kernel": f"conv_tc layer {dom} (32 -> 32, tcgen05)",
                          "bytes_per_px": CONV_BYTES_PER_PX, "avg_launch_us": layer_ms[dom] * 1000.0,
                          "peak_kind": hbm_kind,
