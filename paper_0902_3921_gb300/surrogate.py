@@ -29,14 +29,37 @@ def _params(side):
 
 
 def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=2000, lr=1e-3,
-          channels=32, layers=6, seed0=0, log=None):
+          channels=32, layers=6, seed0=0, log=None, reservoir=0, batch=0, updates=1, lr_final=None):
+    """Trains a network on pairs (x_t, x_{t+window}) that the plain scheme
+    produces.  reservoir = 0: every window's pairs of the current lattices are
+    one training batch.  reservoir > 0: the pairs stream into a device
+    reservoir of that many pairs (uniform reservoir sampling over every pair
+    seen), and each window is followed by `updates` steps on `batch` pairs
+    drawn from it without replacement, so a batch mixes times and trajectories.
+    lr decays from lr to lr_final (cosine) over the run when lr_final is set."""
     import torch
     stream = torch.cuda.Stream()
     net = lbm.Net(channels, layers, seed=seed0 + 12345)
     x0 = torch.empty((lattices, side, side, 4), dtype=torch.float32, device="cuda")
     x1 = torch.empty_like(x0)
+    if reservoir:
+        batch = batch or lattices
+        buf0 = torch.empty((reservoir, side, side, 4), dtype=torch.float32, device="cuda")
+        buf1 = torch.empty_like(buf0)
+        xb0 = torch.empty((batch, side, side, 4), dtype=torch.float32, device="cuda")
+        xb1 = torch.empty_like(xb0)
+    rng = np.random.default_rng(seed0)
+    seen = 0
+    total = generations * iters * (updates if reservoir else 1)
+    step = 0
     history = []
     t0 = time.time()
+
+    def rate():
+        if lr_final is None:
+            return lr
+        return lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * step / max(total - 1, 1)))
+
     for gen in range(generations):
         lats = []
         for k in range(lattices):
@@ -55,16 +78,36 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
                 a = x0.cpu().numpy().reshape(-1, 4)
                 d = (x1 - x0).cpu().numpy().reshape(-1, 4)
                 net.set_normalisation(a.mean(0), a.std(0) + 1e-12, d.std(0) + 1e-12)
-            loss = net.train_step(x0.data_ptr(), x1.data_ptr(), lattices, side, side, lr,
-                                  stream=stream.cuda_stream)
+            if not reservoir:
+                loss = net.train_step(x0.data_ptr(), x1.data_ptr(), lattices, side, side, rate(),
+                                      stream=stream.cuda_stream)
+                step += 1
+            else:
+                with torch.cuda.stream(stream):
+                    for k in range(lattices):
+                        slot = seen if seen < reservoir else int(rng.integers(0, seen + 1))
+                        if slot < reservoir:
+                            buf0[slot].copy_(x0[k])
+                            buf1[slot].copy_(x1[k])
+                        seen += 1
+                    for _ in range(updates):
+                        fill = min(seen, reservoir)
+                        idx = rng.choice(fill, size=min(batch, fill), replace=False)
+                        for b, j in enumerate(idx):
+                            xb0[b].copy_(buf0[int(j)])
+                            xb1[b].copy_(buf1[int(j)])
+                        loss = net.train_step(xb0.data_ptr(), xb1.data_ptr(), len(idx), side, side,
+                                              rate(), stream=stream.cuda_stream)
+                        step += 1
             history.append(loss)
             if log and (it % 20 == 0 or it == iters - 1):
-                log(f"gen {gen} iter {it} t={lats[0].t} loss {loss:.4e}")
+                log(f"gen {gen} iter {it} t={lats[0].t} loss {loss:.4e} lr {rate():.2e}")
         for lat in lats:
             lat.close()
     return net, {"loss_first": history[0], "loss_last": history[-1],
                  "loss_last10": float(np.mean(history[-10:])), "pairs": lattices * iters * generations,
-                 "trajectories": lattices * generations, "seconds": time.time() - t0}
+                 "trajectories": lattices * generations, "updates": step,
+                 "reservoir": reservoir, "seconds": time.time() - t0}
 
 
 def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 16000),
@@ -130,9 +173,26 @@ def main():
     ap.add_argument("--window", type=int, default=50)
     ap.add_argument("--mass-tol", type=float, default=2e-3)
     ap.add_argument("--phi-clamp", type=float, default=0.0)
+    ap.add_argument("--reservoir", type=int, default=0, help="pairs kept for sampling (0: none)")
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--updates", type=int, default=1, help="training steps per window")
+    ap.add_argument("--lr-final", type=float, default=None)
+    ap.add_argument("--save", default=None, help="write the trained parameters (.npz)")
+    ap.add_argument("--load", default=None, help="evaluate parameters written by --save")
     args = ap.parse_args()
-    net, hist = train(args.side, args.lattices, args.generations, args.iters, window=args.window,
-                      lr=args.lr, log=lambda m: print(m, flush=True))
+    if args.load:
+        z = np.load(args.load)
+        net = lbm.Net(32, 6, seed=0)
+        net.set_params(z["params"])
+        nrm = z["normalisation"]
+        net.set_normalisation(nrm[0], nrm[1], nrm[2])
+        hist = {"loaded": args.load}
+    else:
+        net, hist = train(args.side, args.lattices, args.generations, args.iters, window=args.window,
+                          lr=args.lr, log=lambda m: print(m, flush=True), reservoir=args.reservoir,
+                          batch=args.batch, updates=args.updates, lr_final=args.lr_final)
+    if args.save:
+        np.savez(args.save, params=net.get_params(), normalisation=np.asarray(net.normalisation()))
     res = evaluate(net, args.eval_side, checkpoints=tuple(int(c) for c in args.checkpoints.split(",")),
                    window=args.window, mass_tol=args.mass_tol, phi_clamp=args.phi_clamp,
                    log=lambda m: print(m, flush=True))
