@@ -423,6 +423,111 @@ def run_batched(args, rank, world, local):
             "speedup_vs_plain": value / plain, "clocks": clocks.summary()}), flush=True)
 
 
+D3_SIDE = 256
+D3_CFG = dict(CFG, N=1 / 6, Q=1 / 3)  # the 3D stencil weights of the 3D drop tests
+D3_LB_PER_STEP = 10
+# algorithmic bytes per site: D3Q19 populations read + written, phi read
+D3_COLLIDE_BYTES = {"f32": 2 * 19 * 4 + 4, "f16": 2 * 19 * 2 + 4}
+# FD3d per substep: phi read + written, u* (3 components) read (the fused
+# minimum; the three-pass kernels also write and re-read phih and psi)
+D3_FD_BYTES = 4 + 4 + 12
+D3_M = 8
+
+
+def run_drop3d(args, rank, world, local):
+    """D3Q19 drop on a 256^3 periodic lattice (R = 48, centred), FP32 and FP16
+    deviations, m = 8 FD substeps; one timed step = lbm_step(10)."""
+    import torch
+    from paper_0902_3921_gb300 import build as B
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    B.build()
+    lbm.load_library()
+    S3 = D3_SIDE
+    S = S3 ** 3
+    xi = (2 * D3_CFG["kappa"] / -D3_CFG["a"]) ** 0.5
+    phi0 = (-D3_CFG["a"] / D3_CFG["b"]) ** 0.5
+    phi = I.drop(3, S3, S3, S3, R=48, phi0=phi0, xi=xi)
+    n, u = I.rest(3, S3, S3, S3)
+    stream = torch.cuda.Stream()
+    out = {}
+    peak, peak_kind = measured_peak()
+    for name, prec in (("f32", lbm.LBM_F32DEV), ("f16", lbm.LBM_F16DEV)):
+        lat = lbm.Lattice(lbm.LbmParams(dims=3, Lx=S3, Ly=S3, Lz=S3, precision=prec, **D3_CFG),
+                          stream=stream.cuda_stream)
+        lat.init_fields(n, phi, u)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                lat.step(D3_LB_PER_STEP)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clocks:
+            with torch.cuda.stream(stream):
+                t0.record(stream)
+                for _ in range(args.steps):
+                    lat.step(D3_LB_PER_STEP)
+                t1.record(stream)
+            torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / args.steps
+        value = S * D3_LB_PER_STEP / (ms / 1000.0) / 1e6
+        lbm.lbm_set_kernel_timing(lat.handle, True)
+        lbm.lbm_kernel_times(lat.handle, reset=True)
+        with torch.cuda.stream(stream):
+            lat.step(D3_LB_PER_STEP)
+        kt = lbm.lbm_kernel_times(lat.handle, reset=True)
+        lbm.lbm_set_kernel_timing(lat.handle, False)
+        (cms, cn), (fms, fn) = kt["collide"], kt["fd"]
+        c_s, f_s = cms / cn / 1000.0, fms / fn / 1000.0  # f_s: all FD launches of one LB step
+        ac = D3_COLLIDE_BYTES[name] * S / c_s / 1e9
+        af = D3_M * D3_FD_BYTES * S / f_s / 1e9
+        roof_c = {"bound": "hbm", "achieved": ac, "peak": peak, "unit": "GB/s", "frac": ac / peak,
+                  "traffic": None, "kernel": "collide3d", "bytes_per_site": D3_COLLIDE_BYTES[name],
+                  "avg_launch_us": c_s * 1e6, "peak_kind": peak_kind, "share_of_step": cms / (cms + fms)}
+        roof_f = {"bound": "hbm", "achieved": af, "peak": peak, "unit": "GB/s", "frac": af / peak,
+                  "traffic": None,
+                  "kernel": "fd3d (m = 8 substeps, three passes each: phih, psi, phi)",
+                  "bytes_per_site": D3_M * D3_FD_BYTES, "avg_launch_us": f_s * 1e6,
+                  "note": "avg_launch_us covers the 24 launches of one LB step",
+                  "peak_kind": peak_kind, "share_of_step": fms / (cms + fms)}
+        dom, oth = (roof_c, roof_f) if cms >= fms else (roof_f, roof_c)
+        out[name] = {"value": value, "ms_per_step": ms, "roofline": dom, "roofline_other_kernel": oth,
+                     "clocks": clocks.summary(), "launches_per_step": (cn + fn)}
+        lat.close()
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        import oracle as O
+        O.build()
+        op = O.Params(dims=3, Lx=64, Ly=64, Lz=64, m=8, **D3_CFG)
+        p64 = I.drop(3, 64, 64, 64, R=12, phi0=phi0, xi=xi)
+        n64, u64 = I.rest(3, 64, 64, 64)
+        st = O.State.create(op, n64, p64, u64)
+        tc = time.perf_counter()
+        st.run(2)
+        dt = time.perf_counter() - tc
+        cpu = {"value": 64 ** 3 * 2 / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"2 LB steps of a 64^3 drop ({dt:.1f} s, single thread)"}
+    if rank == 0:
+        f32 = out["f32"]
+        print(json.dumps({
+            "metric": "MLUPS (D3Q19 hybrid LB + FD step)", "value": f32["value"], "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": f32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "drop3d-256^3-d3q19", "lattice": [S3, S3, S3], "R": 48,
+                       "lb_steps_per_timed_step": D3_LB_PER_STEP, "fd_substeps": 8,
+                       "precision": "f32 deviations",
+                       "l2": "working set (5.4 GB FP32 populations) exceeds L2"},
+            "roofline": f32["roofline"], "roofline_other_kernel": f32["roofline_other_kernel"],
+            "fp16_deviations": {"value": out["f16"]["value"], "unit": "MLUPS",
+                                "roofline": out["f16"]["roofline"],
+                                "roofline_other_kernel": out["f16"]["roofline_other_kernel"]},
+            "cpu_baseline": cpu, "gpu_launches": f32["launches_per_step"] * args.steps,
+            "clocks": f32["clocks"]}), flush=True)
+
+
 SURR_SIDE = 2048
 SURR_WINDOW = 50  # LB steps one forward pass replaces
 # algorithmic bytes per pixel of one 32 -> 32 convolution layer: BF16 input
@@ -580,7 +685,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no kernel timing, e2e or CPU baseline)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one")
-    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "surrogate"])
+    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "surrogate", "drop3d"])
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--plain-steps", type=int, default=10)
     args = ap.parse_args()
@@ -591,6 +696,8 @@ def main():
         run_batched(args, rank, world, local)
     elif args.workload == "surrogate":
         run_surrogate(args, rank, world, local)
+    elif args.workload == "drop3d":
+        run_drop3d(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -10,6 +10,8 @@
 // along the axis and M on the eight edge neighbours with a non-zero component
 // along it (2N + 8M = 1); lap_D has Q on the six faces, R on the twelve edges
 // and -(6Q + 12R) at the centre (Q + 4R = 1).
+#include <cstdlib>
+
 #include "lbm_common.cuh"
 
 namespace hlbm {
@@ -289,6 +291,100 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---- FD 3D, FP32: three passes per substep --------------------------------------
+// One site per thread over the whole lattice, periodic neighbours by index
+// arithmetic; no halo is recomputed.  Pass 1: phih (Eqs. 32-35) from the
+// 7-point neighbourhood of phi and u*; pass 2: psi = a phih + b phi^3 -
+// kappa lap phih (Eq. 36); pass 3: phi^{n+1} = phih + dt Gamma lap psi.  The
+// expressions are those of fd3d_kernel, in the same order.
+struct Nbr3 {
+  long long s, xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ bool nbr3(const KParams<float> &p, Nbr3 &n) {
+  const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  if (x >= Lx || y >= Ly) return false;
+  const long long PL = (long long)Lx * Ly;
+  n.s = z * PL + (long long)y * Lx + x;
+  n.xm = n.s + (x == 0 ? Lx - 1 : -1);
+  n.xp = n.s + (x == Lx - 1 ? 1 - Lx : 1);
+  n.ym = n.s + (y == 0 ? (long long)(Ly - 1) * Lx : -(long long)Lx);
+  n.yp = n.s + (y == Ly - 1 ? -(long long)(Ly - 1) * Lx : (long long)Lx);
+  n.zm = n.s + (z == 0 ? (Lz - 1) * PL : -PL);
+  n.zp = n.s + (z == Lz - 1 ? -(Lz - 1) * PL : PL);
+  return true;
+}
+
+template <bool FLUX>
+__global__ void __launch_bounds__(256)
+    fd3_adv_kernel(const float *__restrict__ phi, const float *__restrict__ u,
+                   float *__restrict__ A, KParams<float> p) {
+  Nbr3 n;
+  if (!nbr3(p, n)) return;
+  const long long Sz = (long long)p.Lx * p.Ly * p.Lz;
+  const float *v = u + Sz, *w = u + 2 * Sz;
+  const float ph = __ldg(phi + n.s);
+  float tend;
+  if constexpr (!FLUX) {
+    const float ua = __ldg(u + n.s), va = __ldg(v + n.s), wa = __ldg(w + n.s);
+    const float dux = (__ldg(u + n.xp) - __ldg(u + n.xm)) / 2.f;
+    const float dpx = ua < 0.f ? __ldg(phi + n.xp) - ph : ph - __ldg(phi + n.xm);
+    const float duy = (__ldg(v + n.yp) - __ldg(v + n.ym)) / 2.f;
+    const float dpy = va < 0.f ? __ldg(phi + n.yp) - ph : ph - __ldg(phi + n.ym);
+    const float duz = (__ldg(w + n.zp) - __ldg(w + n.zm)) / 2.f;
+    const float dpz = wa < 0.f ? __ldg(phi + n.zp) - ph : ph - __ldg(phi + n.zm);
+    tend = (ph * dux + ua * dpx);
+    tend += (ph * duy + va * dpy);
+    tend += (ph * duz + wa * dpz);
+  } else {
+    auto flux = [&](const float *uu, long long m, long long q) {
+      const float uc = __ldg(uu + n.s);
+      const float Up = 0.5f * (uc + __ldg(uu + q));
+      const float Um = 0.5f * (__ldg(uu + m) + uc);
+      const float Jp = Up > 0.f ? Up * ph : Up * __ldg(phi + q);
+      const float Jm = Um > 0.f ? Um * __ldg(phi + m) : Um * ph;
+      return Jp - Jm;
+    };
+    tend = flux(u, n.xm, n.xp);
+    tend += flux(v, n.ym, n.yp);
+    tend += flux(w, n.zm, n.zp);
+  }
+  A[n.s] = ph - p.dt * tend;
+}
+
+__global__ void __launch_bounds__(256)
+    fd3_psi_kernel(const float *__restrict__ A, const float *__restrict__ phi,
+                   float *__restrict__ P, KParams<float> p) {
+  Nbr3 n;
+  if (!nbr3(p, n)) return;
+  const float hk = __ldg(A + n.s);
+  const float c = p.cubic_at_half ? hk : __ldg(phi + n.s);
+  float lap = __ldg(A + n.zm);
+  lap += __ldg(A + n.ym);
+  lap += __ldg(A + n.xm);
+  lap += -6.f * hk;
+  lap += __ldg(A + n.xp);
+  lap += __ldg(A + n.yp);
+  lap += __ldg(A + n.zp);
+  P[n.s] = p.a * hk + p.b * (c * c * c) - p.kappa * lap;
+}
+
+__global__ void __launch_bounds__(256)
+    fd3_phi_kernel(const float *__restrict__ P, const float *__restrict__ A,
+                   float *__restrict__ phi_out, KParams<float> p) {
+  Nbr3 n;
+  if (!nbr3(p, n)) return;
+  float lap = __ldg(P + n.zm);
+  lap += __ldg(P + n.ym);
+  lap += __ldg(P + n.xm);
+  lap += -6.f * __ldg(P + n.s);
+  lap += __ldg(P + n.xp);
+  lap += __ldg(P + n.yp);
+  lap += __ldg(P + n.zp);
+  phi_out[n.s] = __ldg(A + n.s) + p.dtG * lap;
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     density3d_kernel(const S *__restrict__ hin, C *__restrict__ dn, KParams<C> p) {
@@ -333,6 +429,27 @@ cudaError_t collide3d(lbm_handle *h, int in, int force_on, int mode) {
           <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   }
   return cudaGetLastError();
+}
+
+// the m substeps of an LB step as three passes each (FP32)
+cudaError_t fd3d_passes(lbm_handle *h, int in) {
+  KParams<float> p = make_params<float>(h, 0);
+  dim3 grid((p.Lx + 31) / 32, (p.Ly + 7) / 8, p.Lz), block(32, 8);
+  const float *u = static_cast<const float *>(h->u);
+  float *A = static_cast<float *>(h->fd_a), *P = static_cast<float *>(h->fd_p);
+  const float *src = static_cast<const float *>(h->phi[in]);
+  const bool flux = p.adv_variant == LBM_ADV_FLUX;
+  for (int j = 0; j < h->m; ++j) {
+    float *dst = static_cast<float *>(((h->m - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
+    if (flux) fd3_adv_kernel<true><<<grid, block, 0, h->stream>>>(src, u, A, p);
+    else fd3_adv_kernel<false><<<grid, block, 0, h->stream>>>(src, u, A, p);
+    fd3_psi_kernel<<<grid, block, 0, h->stream>>>(A, src, P, p);
+    fd3_phi_kernel<<<grid, block, 0, h->stream>>>(P, A, dst, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = dst;
+  }
+  return cudaSuccess;
 }
 
 template <typename C, int TX, int TY, int TZ>
@@ -385,6 +502,7 @@ cudaError_t collide3d_launch(lbm_handle *h, int in, int force_on, int mode) {
 
 cudaError_t fd3d_launch(lbm_handle *h, int in) {
   if (h->P.precision == LBM_F64) return fd3d<double, FD3_TX_D, FD3_TY, FD3_TZ>(h, in);
+  if (h->fd_a != nullptr && std::getenv("HLBM_FD3_TILE") == nullptr) return fd3d_passes(h, in);
   return fd3d<float, FD3_TX_F, FD3_TY, FD3_TZ>(h, in);
 }
 

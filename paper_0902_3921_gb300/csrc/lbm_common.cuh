@@ -127,6 +127,7 @@ struct lbm_handle {
   int cur = 0;  // which of the two population/phi buffers holds time t
   void *h[2] = {nullptr, nullptr};
   void *phi[3] = {nullptr, nullptr, nullptr};  // [2] = FD scratch between launches
+  void *fd_a = nullptr, *fd_p = nullptr;        // 3D FP32 FD: phih and psi planes
   void *u = nullptr;
   void *dn = nullptr;
   double *staging = nullptr;   // (dims + 3) * S doubles

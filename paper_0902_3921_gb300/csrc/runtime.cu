@@ -551,7 +551,9 @@ int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out) {
                 {(void **)&h->staging, sizeof(double) * (h->dims + 3) * (size_t)h->S},
                 {(void **)&h->partials, sizeof(double) * DIAG_BLOCKS * DIAG_NPART},
                 {(void **)&h->dres, sizeof(double) * DIAG_COUNT},
-                {&h->dn, P.T != 1.0 / 3.0 ? cb * (size_t)h->S : 0}};
+                {&h->dn, P.T != 1.0 / 3.0 ? cb * (size_t)h->S : 0},
+                {&h->fd_a, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0},
+                {&h->fd_p, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0}};
   for (auto &a : allocs) {
     if (a.n == 0) continue;
     cudaError_t e = cudaMalloc(a.p, a.n);
@@ -778,7 +780,7 @@ void lbm_free(lbm_handle *h) {
   }
   for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
   void *ptrs[] = {h->h[0], h->h[1], h->phi[0], h->phi[1], h->phi[2], h->u, h->dn,
-                  h->staging, h->partials, h->dres};
+                  h->staging, h->partials, h->dres, h->fd_a, h->fd_p};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
