@@ -241,6 +241,8 @@ __global__ void __launch_bounds__(256, MINB)
   const int ly0 = 4 * ty;
   const int x = x0 + tx;
   const int xm = x == 0 ? Lx - 1 : x - 1, xp = x >= Lx - 1 ? 0 : x + 1;
+  pdl_wait();  // phi(t) comes from the previous kernel
+  pdl_trigger();
   // 1. every pulled population f_i(r, t) = buf_i(r - e_i) of the tile
 #pragma unroll
   for (int r = 0; r < CA_RY; ++r) {
@@ -916,6 +918,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
   int gx[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) gx[j] = wrapi(x0 + c + j, Lx);
+  pdl_wait();  // u*(t) comes from the previous kernel
+  pdl_trigger();
   // 1. phi -> sp, u -> sa, v -> sq (the latter two only until the
   //    coefficients are in registers)
 #pragma unroll
@@ -1121,11 +1125,10 @@ cudaError_t collide2d_async(lbm_handle *h, int in, int force_on, int mode) {
   const bool tgen = p.cs2mT != C(0);
   if (mode == COLLIDE_STEP) {
     if (tgen)
-      collide2d_async_kernel<C, true, COLLIDE_STEP, MINB>
-          <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
-    else
-      collide2d_async_kernel<C, false, COLLIDE_STEP, MINB>
-          <<<grid, block, smem, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+      return launch_pdl(collide2d_async_kernel<C, true, COLLIDE_STEP, MINB>, grid, block, smem,
+                        h->stream, hin, hout, phi, dn, u, h->staging, p);
+    return launch_pdl(collide2d_async_kernel<C, false, COLLIDE_STEP, MINB>, grid, block, smem,
+                      h->stream, hin, hout, phi, dn, u, h->staging, p);
   } else {
     if (tgen)
       collide2d_async_kernel<C, true, COLLIDE_MOMENTS, MINB>
@@ -1194,9 +1197,8 @@ template <bool FLUX, int SUB, int K, int NW>
 cudaError_t fd2d_block_one(lbm_handle *h, const KParams<float> &p, const float *src, float *dst) {
   using G = FDBlock<SUB, K, NW>;
   dim3 grid((p.Lx + G::TX - 1) / G::TX, (p.Ly + G::TY - 1) / G::TY);
-  fd2d_block_kernel<FLUX, SUB, K, NW><<<grid, NW * 32, G::smem, h->stream>>>(
-      src, static_cast<const float *>(h->u), dst, p);
-  return cudaGetLastError();
+  return launch_pdl(fd2d_block_kernel<FLUX, SUB, K, NW>, grid, dim3(NW * 32), G::smem, h->stream,
+                    src, static_cast<const float *>(h->u), dst, p);
 }
 
 // block kernel shapes (substeps per launch, region rows RY, warps); the

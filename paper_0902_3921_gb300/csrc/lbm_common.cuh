@@ -14,6 +14,34 @@
 
 namespace hlbm {
 
+// Programmatic dependent launch: a kernel launched with launch_pdl() may be
+// scheduled while the previous kernel of the stream is still finishing; it
+// calls pdl_wait() before touching anything that kernel wrote (the wait
+// returns once that grid has completed and its writes are visible; without
+// the launch attribute it returns at once), and pdl_trigger() to let the
+// next kernel be scheduled early in turn.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+bool pdl_enabled();  // HLBM_PDL=0 turns it off (read once)
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+
 // ---- lattices (Sec. II A, Fig. 1; D3Q19 for 3D) --------------------------------
 // D2Q9 order: 0 rest; 1..4 = (1,0),(0,1),(-1,0),(0,-1); 5..8 = (1,1),(-1,1),(-1,-1),(1,-1).
 __host__ __device__ constexpr int q9_ex(int i) {

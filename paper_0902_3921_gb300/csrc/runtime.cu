@@ -466,6 +466,14 @@ int autotune_2d(lbm_handle *h) {
 }  // namespace
 
 namespace hlbm {
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("HLBM_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 // n(t), phi(t), u*(t) as FP64 in the handle's staging buffer (surrogate coupling)
 int queue_moments_for(lbm_handle *h) { return queue_moments(h); }
 }  // namespace hlbm
