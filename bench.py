@@ -445,11 +445,11 @@ def run_drop3d(args, rank, world, local):
     torch.cuda.set_device(local)
     B.build()
     lbm.load_library()
-    S3 = D3_SIDE
+    S3 = args.side3d
     S = S3 ** 3
     xi = (2 * D3_CFG["kappa"] / -D3_CFG["a"]) ** 0.5
     phi0 = (-D3_CFG["a"] / D3_CFG["b"]) ** 0.5
-    phi = I.drop(3, S3, S3, S3, R=48, phi0=phi0, xi=xi)
+    phi = I.drop(3, S3, S3, S3, R=48 * S3 / 256, phi0=phi0, xi=xi)
     n, u = I.rest(3, S3, S3, S3)
     stream = torch.cuda.Stream()
     out = {}
@@ -516,7 +516,7 @@ def run_drop3d(args, rank, world, local):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": f32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "drop3d-256^3-d3q19", "lattice": [S3, S3, S3], "R": 48,
+            "config": {"workload": f"drop3d-{S3}^3-d3q19", "lattice": [S3, S3, S3], "R": 48 * S3 // 256,
                        "lb_steps_per_timed_step": D3_LB_PER_STEP, "fd_substeps": 8,
                        "precision": "f32 deviations",
                        "l2": "working set (5.4 GB FP32 populations) exceeds L2"},
@@ -687,6 +687,8 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one")
     ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "surrogate", "drop3d"])
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--side3d", type=int, default=D3_SIDE,
+                    help="3D lattice side (the workload is 256; smaller sides are for profiling)")
     ap.add_argument("--plain-steps", type=int, default=10)
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -385,6 +385,164 @@ __global__ void __launch_bounds__(256)
   phi_out[n.s] = __ldg(A + n.s) + p.dtG * lap;
 }
 
+// ---- the same three passes, four x-sites per thread, marching in z ------------
+// (Lx a multiple of 4.)  A warp covers 128 consecutive x (float4 per lane, the
+// x neighbours by shuffles; lanes at a warp or lattice edge load their wrapped
+// neighbour), a block 8 rows of y, and each thread marches F3V_NZ planes in z
+// keeping the z-1, z, z+1 values of the marched field in registers.
+constexpr int F3V_NZ = 16;
+
+struct Vq {
+  int x4, xc, y, z0, z1, lane;
+  bool ok;
+};
+
+__device__ __forceinline__ Vq vq_of(const KParams<float> &p) {
+  Vq q;
+  q.lane = threadIdx.x;
+  q.x4 = 4 * (blockIdx.x * 32 + threadIdx.x);
+  q.xc = min(q.x4, p.Lx - 4);  // loads of lanes past the lattice edge stay in bounds
+  q.ok = q.x4 < p.Lx;
+  q.y = blockIdx.y * 8 + threadIdx.y;
+  q.z0 = blockIdx.z * F3V_NZ;
+  q.z1 = min(q.z0 + F3V_NZ, p.Lz);
+  return q;
+}
+
+__device__ __forceinline__ const float *row_of(const float *a, int y, int z, const KParams<float> &p) {
+  return a + ((long long)z * p.Ly + y) * p.Lx;
+}
+
+__device__ __forceinline__ float4 ld4g(const float *row, int x) {
+  return __ldg(reinterpret_cast<const float4 *>(row + x));
+}
+
+// values at x4 - 1 and x4 + 4 of `row`, whose quad at x4 is c
+__device__ __forceinline__ void xnbr4(const float *row, float4 c, const Vq &q, int Lx, float &l,
+                                      float &r) {
+  l = __shfl_up_sync(0xffffffffu, c.w, 1);
+  r = __shfl_down_sync(0xffffffffu, c.x, 1);
+  if (q.lane == 0 || q.x4 == 0) l = __ldg(row + (q.x4 == 0 ? Lx - 1 : q.xc - 1));
+  if (q.lane == 31 || q.x4 + 4 >= Lx) r = __ldg(row + (q.x4 + 4 >= Lx ? 0 : q.x4 + 4));
+}
+
+__device__ __forceinline__ float cmp4(const float4 &v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+template <bool FLUX>
+__global__ void __launch_bounds__(256)
+    fd3v_adv_kernel(const float *__restrict__ phi, const float *__restrict__ u,
+                    float *__restrict__ A, KParams<float> p) {
+  const Vq q = vq_of(p);
+  if (q.y >= p.Ly) return;  // warp-uniform (a warp is one row)
+  const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
+  const long long Sz = (long long)Lx * Ly * Lz;
+  const float *v = u + Sz, *w = u + 2 * Sz;
+  const int ym = q.y == 0 ? Ly - 1 : q.y - 1, yp = q.y == Ly - 1 ? 0 : q.y + 1;
+  const int zb = q.z0 == 0 ? Lz - 1 : q.z0 - 1;
+  float4 pm = ld4g(row_of(phi, q.y, zb, p), q.xc), pc = ld4g(row_of(phi, q.y, q.z0, p), q.xc);
+  float4 wm = ld4g(row_of(w, q.y, zb, p), q.xc), wc = ld4g(row_of(w, q.y, q.z0, p), q.xc);
+  for (int z = q.z0; z < q.z1; ++z) {
+    const int zn = z == Lz - 1 ? 0 : z + 1;
+    const float *prow = row_of(phi, q.y, z, p), *urow = row_of(u, q.y, z, p);
+    const float4 pp = ld4g(row_of(phi, q.y, zn, p), q.xc), wp = ld4g(row_of(w, q.y, zn, p), q.xc);
+    const float4 pym = ld4g(row_of(phi, ym, z, p), q.xc), pyp = ld4g(row_of(phi, yp, z, p), q.xc);
+    const float4 uc = ld4g(urow, q.xc), vc = ld4g(row_of(v, q.y, z, p), q.xc);
+    const float4 vym = ld4g(row_of(v, ym, z, p), q.xc), vyp = ld4g(row_of(v, yp, z, p), q.xc);
+    float pl, pr, ul, ur;
+    xnbr4(prow, pc, q, Lx, pl, pr);
+    xnbr4(urow, uc, q, Lx, ul, ur);
+    float e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float ph = cmp4(pc, j);
+      const float pxm = j == 0 ? pl : cmp4(pc, j - 1), pxp = j == 3 ? pr : cmp4(pc, j + 1);
+      const float uxm = j == 0 ? ul : cmp4(uc, j - 1), uxp = j == 3 ? ur : cmp4(uc, j + 1);
+      float tend;
+      if constexpr (!FLUX) {
+        const float ua = cmp4(uc, j), va = cmp4(vc, j), wa = cmp4(wc, j);
+        const float dux = (uxp - uxm) / 2.f;
+        const float dpx = ua < 0.f ? pxp - ph : ph - pxm;
+        const float duy = (cmp4(vyp, j) - cmp4(vym, j)) / 2.f;
+        const float dpy = va < 0.f ? cmp4(pyp, j) - ph : ph - cmp4(pym, j);
+        const float duz = (cmp4(wp, j) - cmp4(wm, j)) / 2.f;
+        const float dpz = wa < 0.f ? cmp4(pp, j) - ph : ph - cmp4(pm, j);
+        tend = (ph * dux + ua * dpx);
+        tend += (ph * duy + va * dpy);
+        tend += (ph * duz + wa * dpz);
+      } else {
+        auto flux = [&](float cm, float cc, float cp, float fm, float fp) {
+          const float Up = 0.5f * (cc + cp);
+          const float Um = 0.5f * (cm + cc);
+          const float Jp = Up > 0.f ? Up * ph : Up * fp;
+          const float Jm = Um > 0.f ? Um * fm : Um * ph;
+          return Jp - Jm;
+        };
+        tend = flux(uxm, cmp4(uc, j), uxp, pxm, pxp);
+        tend += flux(cmp4(vym, j), cmp4(vc, j), cmp4(vyp, j), cmp4(pym, j), cmp4(pyp, j));
+        tend += flux(cmp4(wm, j), cmp4(wc, j), cmp4(wp, j), cmp4(pm, j), cmp4(pp, j));
+      }
+      e[j] = ph - p.dt * tend;
+    }
+    if (q.ok)
+      *reinterpret_cast<float4 *>(A + ((long long)z * Ly + q.y) * Lx + q.x4) =
+          make_float4(e[0], e[1], e[2], e[3]);
+    pm = pc;
+    pc = pp;
+    wm = wc;
+    wc = wp;
+  }
+}
+
+// LAP7 of a field with the quad c at (y, z) and its neighbours, in the order
+// z-1, y-1, x-1, centre, x+1, y+1, z+1 of the scalar kernels
+template <bool PSI>
+__global__ void __launch_bounds__(256)
+    fd3v_lap_kernel(const float *__restrict__ F, const float *__restrict__ G,
+                    float *__restrict__ out, KParams<float> p) {
+  // PSI:  out = a F + b c^3 - kappa lap F, c = (cubic_at_half ? F : G)
+  // else: out = G + dtG lap F
+  const Vq q = vq_of(p);
+  if (q.y >= p.Ly) return;
+  const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
+  const int ym = q.y == 0 ? Ly - 1 : q.y - 1, yp = q.y == Ly - 1 ? 0 : q.y + 1;
+  const int zb = q.z0 == 0 ? Lz - 1 : q.z0 - 1;
+  float4 fm = ld4g(row_of(F, q.y, zb, p), q.xc), fc = ld4g(row_of(F, q.y, q.z0, p), q.xc);
+  for (int z = q.z0; z < q.z1; ++z) {
+    const int zn = z == Lz - 1 ? 0 : z + 1;
+    const float *frow = row_of(F, q.y, z, p);
+    const float4 fp = ld4g(row_of(F, q.y, zn, p), q.xc);
+    const float4 fym = ld4g(row_of(F, ym, z, p), q.xc), fyp = ld4g(row_of(F, yp, z, p), q.xc);
+    const float4 gc = ld4g(row_of(G, q.y, z, p), q.xc);
+    float fl, fr;
+    xnbr4(frow, fc, q, Lx, fl, fr);
+    float e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float hk = cmp4(fc, j);
+      float lap = cmp4(fm, j);
+      lap += cmp4(fym, j);
+      lap += j == 0 ? fl : cmp4(fc, j - 1);
+      lap += -6.f * hk;
+      lap += j == 3 ? fr : cmp4(fc, j + 1);
+      lap += cmp4(fyp, j);
+      lap += cmp4(fp, j);
+      if constexpr (PSI) {
+        const float c = p.cubic_at_half ? hk : cmp4(gc, j);
+        e[j] = p.a * hk + p.b * (c * c * c) - p.kappa * lap;
+      } else {
+        e[j] = cmp4(gc, j) + p.dtG * lap;
+      }
+    }
+    if (q.ok)
+      *reinterpret_cast<float4 *>(out + ((long long)z * Ly + q.y) * Lx + q.x4) =
+          make_float4(e[0], e[1], e[2], e[3]);
+    fm = fc;
+    fc = fp;
+  }
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     density3d_kernel(const S *__restrict__ hin, C *__restrict__ dn, KParams<C> p) {
@@ -439,12 +597,21 @@ cudaError_t fd3d_passes(lbm_handle *h, int in) {
   float *A = static_cast<float *>(h->fd_a), *P = static_cast<float *>(h->fd_p);
   const float *src = static_cast<const float *>(h->phi[in]);
   const bool flux = p.adv_variant == LBM_ADV_FLUX;
+  const bool vec = p.Lx % 4 == 0 && p.Lx >= 4 && std::getenv("HLBM_FD3_SCALAR") == nullptr;
+  dim3 gridv((p.Lx / 4 + 31) / 32, (p.Ly + 7) / 8, (p.Lz + F3V_NZ - 1) / F3V_NZ);
   for (int j = 0; j < h->m; ++j) {
     float *dst = static_cast<float *>(((h->m - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
-    if (flux) fd3_adv_kernel<true><<<grid, block, 0, h->stream>>>(src, u, A, p);
-    else fd3_adv_kernel<false><<<grid, block, 0, h->stream>>>(src, u, A, p);
-    fd3_psi_kernel<<<grid, block, 0, h->stream>>>(A, src, P, p);
-    fd3_phi_kernel<<<grid, block, 0, h->stream>>>(P, A, dst, p);
+    if (vec) {
+      if (flux) fd3v_adv_kernel<true><<<gridv, block, 0, h->stream>>>(src, u, A, p);
+      else fd3v_adv_kernel<false><<<gridv, block, 0, h->stream>>>(src, u, A, p);
+      fd3v_lap_kernel<true><<<gridv, block, 0, h->stream>>>(A, src, P, p);
+      fd3v_lap_kernel<false><<<gridv, block, 0, h->stream>>>(P, A, dst, p);
+    } else {
+      if (flux) fd3_adv_kernel<true><<<grid, block, 0, h->stream>>>(src, u, A, p);
+      else fd3_adv_kernel<false><<<grid, block, 0, h->stream>>>(src, u, A, p);
+      fd3_psi_kernel<<<grid, block, 0, h->stream>>>(A, src, P, p);
+      fd3_phi_kernel<<<grid, block, 0, h->stream>>>(P, A, dst, p);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     src = dst;

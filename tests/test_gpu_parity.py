@@ -278,17 +278,23 @@ def test_3d_variants_fp64(variant):
 
 
 @pytest.mark.parametrize("variant", ["paper", "flux"])
-@pytest.mark.parametrize("fd_path", ["passes", "tile"])
-def test_3d_fp32_fd_paths(variant, fd_path, monkeypatch):
-    """FP32 3D: the three-pass FD (default) and the shared-memory tile kernel
-    against the oracle, both advection forms, on a ragged grid."""
+@pytest.mark.parametrize("fd_path,shape", [("vec", (36, 19, 21)), ("vec", (132, 10, 17)),
+                                           ("scalar", (37, 18, 21)), ("tile", (37, 18, 21))])
+def test_3d_fp32_fd_paths(variant, fd_path, shape, monkeypatch):
+    """FP32 3D against the oracle, both advection forms: the three FD passes
+    with four x-sites per thread marching in z (Lx a multiple of 4; ragged in
+    x against the 128-site warp, in y against 8 rows, in z against 16
+    planes), the one-site-per-thread passes (any Lx) and the shared-memory
+    tile kernel."""
     if fd_path == "tile":
         monkeypatch.setenv("HLBM_FD3_TILE", "1")
+    Lx, Ly, Lz = shape
     kw = dict(CFG1, N=1 / 6, Q=1 / 3, adv_variant=1 if variant == "flux" else 0)
-    op, lp = _pair(37, 18, 21, dims=3, m=8, precision=lbm.LBM_F32DEV, **kw)
-    phi = I.drop(3, 37, 18, 21, R=6, phi0=O.phi0_of(op), xi=O.xi_of(op))
-    n, u = I.rest(3, 37, 18, 21)
-    u = u + 0.002 * np.sin(np.arange(37) / 5.0)[None, None, None, :]
+    op, lp = _pair(Lx, Ly, Lz, dims=3, m=8, precision=lbm.LBM_F32DEV, **kw)
+    phi = I.drop(3, Lx, Ly, Lz, R=6, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(3, Lx, Ly, Lz)
+    u = u + 0.002 * np.sin(np.arange(Lx) / 5.0)[None, None, None, :]
+    u[1] += 0.001 * np.cos(np.arange(Lz) / 3.0)[:, None, None]
     ref, lat = _run_both(op, lp, n, phi, u, 10)
     dphi, du, dn = _errors(ref, lat)
     _, ru = ref.moments()
