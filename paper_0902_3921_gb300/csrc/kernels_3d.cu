@@ -150,9 +150,10 @@ __global__ void __launch_bounds__(256)
     Fx += n * p.gx;
     Fy += n * p.gy;
     Fz += n * p.gz;
-    const C ux = (jx + C(0.5) * Fx) / n;
-    const C uy = (jy + C(0.5) * Fy) / n;
-    const C uz = (jz + C(0.5) * Fz) / n;
+    const C inv_n = C(1) / n;
+    const C ux = (jx + C(0.5) * Fx) * inv_n;
+    const C uy = (jy + C(0.5) * Fy) * inv_n;
+    const C uz = (jz + C(0.5) * Fz) * inv_n;
     const long long s = zc + yc + x;
     if constexpr (MODE == COLLIDE_MOMENTS) {
       stg[s] = (double)n;
@@ -164,16 +165,28 @@ __global__ void __launch_bounds__(256)
     }
     const C usq = ux * ux + uy * uy + uz * uz;
     const C uF = ux * Fx + uy * Fy + uz * Fz;
+    // BGK + Guo source (Eqs. 15, 17, 29) per opposite pair (i, i + 1): the
+    // parts even and odd in e_i are formed once and added / subtracted
+    const C om = p.tau_inv, keep = C(1) - p.tau_inv;
+    const C base = dens - n * (C(1.5) * usq);  // the u-independent and |u|^2 parts
+    const C n3 = C(3) * n, n45 = C(4.5) * n;
+    const C pF3 = C(3) * p.pref, pF9 = C(9) * p.pref, puF = C(3) * p.pref * uF;
+    {
+      const C w = C(q19_w(0));
+      Store<S, C>::st(hout + s, keep * hv[0] + om * (w * base) + w * (-puF), p.scale);
+    }
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-      const int ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
+    for (int k = 0; k < 9; ++k) {
+      const int i = 2 * k + 1, ib = i + 1;  // e_ib = -e_i
       const C w = C(q19_w(i));
-      const C eu = C(ex) * ux + C(ey) * uy + C(ez) * uz;
-      const C eF = C(ex) * Fx + C(ey) * Fy + C(ez) * Fz;
-      const C heq = w * (dens + n * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq));
-      const C Fi = p.pref * w * (C(3) * (eF - uF) + C(9) * eu * eF);
-      const C post = hv[i] - (hv[i] - heq) * p.tau_inv + Fi;
-      Store<S, C>::st(hout + i * Sz + s, post, p.scale);
+      const C eu = C(q19_ex(i)) * ux + C(q19_ey(i)) * uy + C(q19_ez(i)) * uz;
+      const C eF = C(q19_ex(i)) * Fx + C(q19_ey(i)) * Fy + C(q19_ez(i)) * Fz;
+      const C even = w * (base + n45 * eu * eu);
+      const C odd = w * (n3 * eu);
+      const C Feven = w * (pF9 * eu * eF - puF);
+      const C Fodd = w * (pF3 * eF);
+      Store<S, C>::st(hout + i * Sz + s, keep * hv[i] + om * (even + odd) + (Feven + Fodd), p.scale);
+      Store<S, C>::st(hout + ib * Sz + s, keep * hv[ib] + om * (even - odd) + (Feven - Fodd), p.scale);
     }
     uout[s] = ux;
     uout[Sz + s] = uy;
