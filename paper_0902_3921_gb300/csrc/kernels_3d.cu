@@ -10,6 +10,7 @@
 // along the axis and M on the eight edge neighbours with a non-zero component
 // along it (2N + 8M = 1); lap_D has Q on the six faces, R on the twelve edges
 // and -(6Q + 12R) at the centre (Q + 4R = 1).
+#include <algorithm>
 #include <cstdlib>
 
 #include "lbm_common.cuh"
@@ -401,7 +402,8 @@ __global__ void __launch_bounds__(256)
 // ---- the same three passes, four x-sites per thread, marching in z ------------
 // (Lx a multiple of 4.)  A warp covers 128 consecutive x (float4 per lane, the
 // x neighbours by shuffles; lanes at a warp or lattice edge load their wrapped
-// neighbour), a block 8 rows of y, and each thread marches F3V_NZ planes in z
+// neighbour), a block 8 rows of y, and each thread marches nz planes in z
+// (at most F3V_NZ, fewer when the lattice is too small to fill the GPU)
 // keeping the z-1, z, z+1 values of the marched field in registers.
 constexpr int F3V_NZ = 16;
 
@@ -410,15 +412,15 @@ struct Vq {
   bool ok;
 };
 
-__device__ __forceinline__ Vq vq_of(const KParams<float> &p) {
+__device__ __forceinline__ Vq vq_of(const KParams<float> &p, int nz) {
   Vq q;
   q.lane = threadIdx.x;
   q.x4 = 4 * (blockIdx.x * 32 + threadIdx.x);
   q.xc = min(q.x4, p.Lx - 4);  // loads of lanes past the lattice edge stay in bounds
   q.ok = q.x4 < p.Lx;
   q.y = blockIdx.y * 8 + threadIdx.y;
-  q.z0 = blockIdx.z * F3V_NZ;
-  q.z1 = min(q.z0 + F3V_NZ, p.Lz);
+  q.z0 = blockIdx.z * nz;
+  q.z1 = min(q.z0 + nz, p.Lz);
   return q;
 }
 
@@ -446,8 +448,8 @@ __device__ __forceinline__ float cmp4(const float4 &v, int j) {
 template <bool FLUX>
 __global__ void __launch_bounds__(256)
     fd3v_adv_kernel(const float *__restrict__ phi, const float *__restrict__ u,
-                    float *__restrict__ A, KParams<float> p) {
-  const Vq q = vq_of(p);
+                    float *__restrict__ A, KParams<float> p, int nz) {
+  const Vq q = vq_of(p, nz);
   if (q.y >= p.Ly) return;  // warp-uniform (a warp is one row)
   const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
   const long long Sz = (long long)Lx * Ly * Lz;
@@ -513,10 +515,10 @@ __global__ void __launch_bounds__(256)
 template <bool PSI>
 __global__ void __launch_bounds__(256)
     fd3v_lap_kernel(const float *__restrict__ F, const float *__restrict__ G,
-                    float *__restrict__ out, KParams<float> p) {
+                    float *__restrict__ out, KParams<float> p, int nz) {
   // PSI:  out = a F + b c^3 - kappa lap F, c = (cubic_at_half ? F : G)
   // else: out = G + dtG lap F
-  const Vq q = vq_of(p);
+  const Vq q = vq_of(p, nz);
   if (q.y >= p.Ly) return;
   const int Lx = p.Lx, Ly = p.Ly, Lz = p.Lz;
   const int ym = q.y == 0 ? Ly - 1 : q.y - 1, yp = q.y == Ly - 1 ? 0 : q.y + 1;
@@ -611,14 +613,17 @@ cudaError_t fd3d_passes(lbm_handle *h, int in) {
   const float *src = static_cast<const float *>(h->phi[in]);
   const bool flux = p.adv_variant == LBM_ADV_FLUX;
   const bool vec = p.Lx % 4 == 0 && p.Lx >= 4 && std::getenv("HLBM_FD3_SCALAR") == nullptr;
-  dim3 gridv((p.Lx / 4 + 31) / 32, (p.Ly + 7) / 8, (p.Lz + F3V_NZ - 1) / F3V_NZ);
+  // planes per thread: about 1216 blocks (8 per SM of 152) or 16 planes
+  const long long bxy = (long long)((p.Lx / 4 + 31) / 32) * ((p.Ly + 7) / 8);
+  const int nz = (int)std::max<long long>(1, std::min<long long>(F3V_NZ, p.Lz * bxy / 1216));
+  dim3 gridv((p.Lx / 4 + 31) / 32, (p.Ly + 7) / 8, (p.Lz + nz - 1) / nz);
   for (int j = 0; j < h->m; ++j) {
     float *dst = static_cast<float *>(((h->m - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
     if (vec) {
-      if (flux) fd3v_adv_kernel<true><<<gridv, block, 0, h->stream>>>(src, u, A, p);
-      else fd3v_adv_kernel<false><<<gridv, block, 0, h->stream>>>(src, u, A, p);
-      fd3v_lap_kernel<true><<<gridv, block, 0, h->stream>>>(A, src, P, p);
-      fd3v_lap_kernel<false><<<gridv, block, 0, h->stream>>>(P, A, dst, p);
+      if (flux) fd3v_adv_kernel<true><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
+      else fd3v_adv_kernel<false><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
+      fd3v_lap_kernel<true><<<gridv, block, 0, h->stream>>>(A, src, P, p, nz);
+      fd3v_lap_kernel<false><<<gridv, block, 0, h->stream>>>(P, A, dst, p, nz);
     } else {
       if (flux) fd3_adv_kernel<true><<<grid, block, 0, h->stream>>>(src, u, A, p);
       else fd3_adv_kernel<false><<<grid, block, 0, h->stream>>>(src, u, A, p);
