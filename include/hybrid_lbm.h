@@ -258,8 +258,9 @@ int lbm_surrogate_state(lbm_handle *h, float *out);
 /* Advances h by `windows` windows of `window_steps` LB steps each with the
  * network: state -> prediction -> residual check (mean change of phi per site
  * |d sum phi| / sites <= mass_tol; max |phi| <= max(1.1 phi0, 1.05 max|phi_t|);
- * max |u*| <= max(1.5 max|u*_t|, 0.01 c_s), with _t the state the window starts
- * from; HLBM_SURROGATE_VERBOSE=1 prints the values per window); a passing
+ * max |u*| <= max(1.5 max|u*_t|, 0.01 c_s); max |n - 1| <= max(2 max|n_t - 1|,
+ * 1e-3); every value finite; with _t the state the window starts from;
+ * HLBM_SURROGATE_VERBOSE=1 prints the values per window); a passing
  * prediction becomes the new state (populations rebuilt as f_eq(n, u* - F/2n)
  * with phi shifted to keep sum phi if conserve_mass), a failing one is
  * replaced by window_steps plain LB steps.  phi_clamp > 0 first clips the

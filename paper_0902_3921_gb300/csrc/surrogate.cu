@@ -339,34 +339,37 @@ __global__ void clamp_phi_kernel(float *__restrict__ x, long long S, float cap) 
   if (s < S) x[s * 4] = fminf(fmaxf(x[s * 4], -cap), cap);
 }
 
-// per-block partials of sum phi, sum |phi|, max |phi|, max |u| over a state
+// per-block partials of sum phi, sum |phi|, max |phi|, max |u|, max |n - 1|
+// over a state; a non-finite phi, u or n makes the maxima infinite
+constexpr int NSTAT = 5;
 __global__ void __launch_bounds__(256)
     state_stats_kernel(const float *__restrict__ x, long long S, double *__restrict__ part) {
-  __shared__ double r[4][256];
-  double sp = 0, sa = 0, mp = 0, mu = 0;
+  __shared__ double r[NSTAT][256];
+  double sp = 0, sa = 0, mp = 0, mu = 0, mn = 0;
   for (long long s = blockIdx.x * 256LL + threadIdx.x; s < S; s += (long long)gridDim.x * 256) {
-    const double ph = x[s * 4], ux = x[s * 4 + 1], uy = x[s * 4 + 2];
+    const double ph = x[s * 4], ux = x[s * 4 + 1], uy = x[s * 4 + 2], dn = x[s * 4 + 3];
     sp += ph;
     sa += fabs(ph);
     mp = fmax(mp, fabs(ph));
     mu = fmax(mu, sqrt(ux * ux + uy * uy));
-    if (!isfinite(ph) || !isfinite(ux) || !isfinite(uy)) mp = INFINITY;
+    mn = fmax(mn, fabs(dn));
+    if (!isfinite(ph) || !isfinite(ux) || !isfinite(uy) || !isfinite(dn)) mp = mu = mn = INFINITY;
   }
   r[0][threadIdx.x] = sp;
   r[1][threadIdx.x] = sa;
   r[2][threadIdx.x] = mp;
   r[3][threadIdx.x] = mu;
+  r[4][threadIdx.x] = mn;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
     if (threadIdx.x < k) {
       r[0][threadIdx.x] += r[0][threadIdx.x + k];
       r[1][threadIdx.x] += r[1][threadIdx.x + k];
-      r[2][threadIdx.x] = fmax(r[2][threadIdx.x], r[2][threadIdx.x + k]);
-      r[3][threadIdx.x] = fmax(r[3][threadIdx.x], r[3][threadIdx.x + k]);
+      for (int q = 2; q < NSTAT; ++q) r[q][threadIdx.x] = fmax(r[q][threadIdx.x], r[q][threadIdx.x + k]);
     }
     __syncthreads();
   }
-  if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = r[threadIdx.x][0];
+  if (threadIdx.x < NSTAT) part[blockIdx.x * NSTAT + threadIdx.x] = r[threadIdx.x][0];
 }
 
 struct Layer {
@@ -816,40 +819,41 @@ int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_s
     if (rc) return rc;
     predict_kernel<<<nblk(S, 256), 256, 0, s>>>(net->yout, net->x0, S, net->nrm, net->x1);
     NCK(net, cudaGetLastError(), "surrogate kernels");
-    double st[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    std::vector<double> part(4 * sb);
+    double st[2][NSTAT] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+    std::vector<double> part(NSTAT * sb);
     for (int k = 0; k < 2; k++) {
       state_stats_kernel<<<sb, 256, 0, s>>>(k == 0 ? net->x0 : net->x1, S, net->dpart);
       NCK(net, cudaGetLastError(), "surrogate kernels");
-      NCK(net, cudaMemcpyAsync(part.data(), net->dpart, sizeof(double) * 4 * sb,
+      NCK(net, cudaMemcpyAsync(part.data(), net->dpart, sizeof(double) * NSTAT * sb,
                                cudaMemcpyDeviceToHost, s),
           "copy");
       NCK(net, cudaStreamSynchronize(s), "synchronize");
       for (int b = 0; b < sb; b++) {
-        const double *q = &part[b * 4];
+        const double *q = &part[b * NSTAT];
         st[k][0] += q[0];
         st[k][1] += q[1];
-        st[k][2] = std::max(st[k][2], q[2]);
-        st[k][3] = std::max(st[k][3], q[3]);
+        for (int j = 2; j < NSTAT; j++) st[k][j] = std::max(st[k][j], q[j]);
       }
       if (k == 0 && phi_clamp > 0.0) {
         clamp_phi_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, (float)(phi_clamp * st[0][2]));
         NCK(net, cudaGetLastError(), "clamp kernel");
       }
     }
-    // residual check: the mean change of phi per site, and bounds on |phi| and
-    // |u*| relative to the state the window starts from (an unbounded or
-    // runaway prediction fails them)
+    // residual check: the mean change of phi per site, and bounds on |phi|,
+    // |u*| and |n - 1| relative to the state the window starts from (an
+    // unbounded, non-finite or runaway prediction fails them)
     const double drift = std::fabs(st[1][0] - st[0][0]) / (double)S;
     const double phi_cap = std::max(1.1 * h->phi0, 1.05 * st[0][2]);
     const double u_cap = std::max(1.5 * st[0][3], 0.01 / std::sqrt(3.0));
-    const bool ok = std::isfinite(st[1][2]) && std::isfinite(st[1][3]) && drift <= mass_tol &&
-                    st[1][2] <= phi_cap && st[1][3] <= u_cap;
+    const double n_cap = std::max(2.0 * st[0][4], 1e-3);
+    const bool ok = std::isfinite(st[1][2]) && std::isfinite(st[1][3]) && std::isfinite(st[1][4]) &&
+                    drift <= mass_tol && st[1][2] <= phi_cap && st[1][3] <= u_cap && st[1][4] <= n_cap;
     if (std::getenv("HLBM_SURROGATE_VERBOSE"))
       std::fprintf(stderr,
                    "hlbm surrogate t=%lld mean dphi %.3e max|phi| %.4f (state %.4f) max|u| %.3e "
-                   "(state %.3e) -> %s\n",
-                   h->t, drift, st[1][2], st[0][2], st[1][3], st[0][3], ok ? "accepted" : "plain steps");
+                   "(state %.3e) max|n-1| %.3e (state %.3e) -> %s\n",
+                   h->t, drift, st[1][2], st[0][2], st[1][3], st[0][3], st[1][4], st[0][4],
+                   ok ? "accepted" : "plain steps");
     if (ok) {
       const double shift = conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0;
       staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift, h->staging);

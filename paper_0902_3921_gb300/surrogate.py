@@ -29,14 +29,19 @@ def _params(side):
 
 
 def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=2000, lr=1e-3,
-          channels=32, layers=6, seed0=0, log=None, reservoir=0, batch=0, updates=1, lr_final=None):
+          channels=32, layers=6, seed0=0, log=None, reservoir=0, batch=0, updates=1, lr_final=None,
+          pushforward=0.0, pushforward_from=1):
     """Trains a network on pairs (x_t, x_{t+window}) that the plain scheme
     produces.  reservoir = 0: every window's pairs of the current lattices are
     one training batch.  reservoir > 0: the pairs stream into a device
     reservoir of that many pairs (uniform reservoir sampling over every pair
     seen), and each window is followed by `updates` steps on `batch` pairs
     drawn from it without replacement, so a batch mixes times and trajectories.
-    lr decays from lr to lr_final (cosine) over the run when lr_final is set."""
+    lr decays from lr to lr_final (cosine) over the run when lr_final is set.
+    pushforward > 0 (reservoir only, from generation pushforward_from on):
+    that fraction of the windows also adds the pair (Net(x_{t-window}),
+    x_{t+window}), whose input is the network's own prediction of x_t, so the
+    network learns to correct the errors it makes when applied repeatedly."""
     import torch
     stream = torch.cuda.Stream()
     net = lbm.Net(channels, layers, seed=seed0 + 12345)
@@ -48,6 +53,8 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
         buf1 = torch.empty_like(buf0)
         xb0 = torch.empty((batch, side, side, 4), dtype=torch.float32, device="cuda")
         xb1 = torch.empty_like(xb0)
+        xprev = torch.empty_like(x0)
+        xhat = torch.empty_like(x0)
     rng = np.random.default_rng(seed0)
     seen = 0
     total = generations * iters * (updates if reservoir else 1)
@@ -84,12 +91,21 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
                 step += 1
             else:
                 with torch.cuda.stream(stream):
-                    for k in range(lattices):
+                    def offer(a, b):
+                        nonlocal seen
                         slot = seen if seen < reservoir else int(rng.integers(0, seen + 1))
                         if slot < reservoir:
-                            buf0[slot].copy_(x0[k])
-                            buf1[slot].copy_(x1[k])
+                            buf0[slot].copy_(a)
+                            buf1[slot].copy_(b)
                         seen += 1
+                    if pushforward > 0 and gen >= pushforward_from and it > 0 and rng.random() < pushforward:
+                        net.forward(xprev.data_ptr(), lattices, side, side, xhat.data_ptr(),
+                                    stream=stream.cuda_stream)
+                        for k in range(lattices):
+                            offer(xhat[k], x1[k])
+                    for k in range(lattices):
+                        offer(x0[k], x1[k])
+                    xprev.copy_(x0)
                     for _ in range(updates):
                         fill = min(seen, reservoir)
                         idx = rng.choice(fill, size=min(batch, fill), replace=False)
@@ -177,6 +193,9 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--updates", type=int, default=1, help="training steps per window")
     ap.add_argument("--lr-final", type=float, default=None)
+    ap.add_argument("--pushforward", type=float, default=0.0,
+                    help="fraction of windows that add (Net(x_{t-w}), x_{t+w}) pairs")
+    ap.add_argument("--pushforward-from", type=int, default=1, help="first generation with them")
     ap.add_argument("--save", default=None, help="write the trained parameters (.npz)")
     ap.add_argument("--load", default=None, help="evaluate parameters written by --save")
     args = ap.parse_args()
@@ -190,7 +209,8 @@ def main():
     else:
         net, hist = train(args.side, args.lattices, args.generations, args.iters, window=args.window,
                           lr=args.lr, log=lambda m: print(m, flush=True), reservoir=args.reservoir,
-                          batch=args.batch, updates=args.updates, lr_final=args.lr_final)
+                          batch=args.batch, updates=args.updates, lr_final=args.lr_final,
+                          pushforward=args.pushforward, pushforward_from=args.pushforward_from)
     if args.save:
         np.savez(args.save, params=net.get_params(), normalisation=np.asarray(net.normalisation()))
     res = evaluate(net, args.eval_side, checkpoints=tuple(int(c) for c in args.checkpoints.split(",")),

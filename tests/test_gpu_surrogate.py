@@ -271,6 +271,32 @@ def test_surrogate_state_and_fallback():
     net.close()
 
 
+def test_residual_check_rejects_nonfinite_and_runaway_density():
+    """A prediction with a non-finite value, or a density change far beyond
+    the state's, is never accepted: the windows fall back to the plain
+    scheme and the lattice stays equal to one stepped plainly."""
+    cfg = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    p = lbm.LbmParams(Lx=64, Ly=32, precision=lbm.LBM_F32DEV, fd_substeps=4, **cfg)
+    phi = I.spinodal(2, 64, 32, seed=5, amp=0.1)
+    n, u = I.rest(2, 64, 32)
+    for case in ("nan", "density"):
+        a = lbm.Lattice(p).init_fields(n, phi, u)
+        b = lbm.Lattice(p).init_fields(n, phi, u)
+        net = lbm.Net(16, 3, seed=2)
+        net.set_normalisation(*NORM)
+        w = np.zeros(net.nparams, dtype=np.float32)
+        # the last entry is the bias of the last layer's n - 1 channel (no
+        # ReLU after it, so a NaN there reaches the prediction)
+        w[-1] = np.nan if case == "nan" else 1e3
+        net.set_params(w)
+        fb = lbm.lbm_surrogate_advance(a.handle, net, windows=2, window_steps=10, mass_tol=1.0)
+        b.step(20)
+        assert fb == 2, case
+        for xa, xb in zip(a.moments(), b.moments()):
+            assert np.array_equal(xa, xb), case
+        net.close()
+
+
 def test_train_and_evaluate_end_to_end():
     """A short version of the training/evaluation pipeline: the loss falls
     and the surrogate-advanced lattice keeps its mass and domain size close
