@@ -888,7 +888,9 @@ constexpr int FDB_RX = 128;
 template <int SUB, int K, int NW>
 struct FDBlock {
   static constexpr int H = 3 * SUB, RY = K * NW, TX = FDB_RX - 2 * H, TY = RY - 2 * H;
-  static constexpr size_t smem = sizeof(float) * 3 * (size_t)RY * FDB_RX;
+  // phi, phih, psi planes, and (printed advection form) the c0 plane
+  static constexpr size_t smem_of(bool flux) { return sizeof(float) * (flux ? 3 : 4) * (size_t)RY * FDB_RX; }
+  static constexpr size_t smem = smem_of(false);
 };
 
 __device__ __forceinline__ float4 ld4(const float *a, int r, int c) {
@@ -907,10 +909,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
     fd2d_block_kernel(const float *__restrict__ phi_in, const float *__restrict__ u,
                       float *__restrict__ phi_out, KParams<float> p) {
   using G = FDBlock<SUB, K, NW>;
-  constexpr int H = G::H, RY = G::RY, TX = G::TX, TY = G::TY, NC = FLUX ? 4 : 3;
+  constexpr int H = G::H, RY = G::RY, TX = G::TX, TY = G::TY, NC = FLUX ? 4 : 2;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) float fdb_smem[];
-  float *sp = fdb_smem, *sa = sp + RY * FDB_RX, *sq = sa + RY * FDB_RX;
+  float *sp = fdb_smem, *sa = sp + RY * FDB_RX, *sq = sa + RY * FDB_RX, *st0 = sq + RY * FDB_RX;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = 4 * lane;
   const int Lx = p.Lx, Ly = p.Ly;
   const long long Sz = (long long)Lx * Ly;
@@ -949,15 +951,16 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int rm = r > 0 ? r - 1 : r, rp = r < RY - 1 ? r + 1 : r;  // row 0 / RY-1: never valid
     const float4 uc = ld4(sa, r, c), vc = ld4(sq, r, c), vm = ld4(sq, rm, c), vp = ld4(sq, rp, c);
     const float uL0 = __shfl_up_sync(FULL, uc.w, 1), uR3 = __shfl_down_sync(FULL, uc.x, 1);
+    float c0[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float ucj = comp(uc, j), uL = j == 0 ? uL0 : comp(uc, j - 1), uR = j == 3 ? uR3 : comp(uc, j + 1);
       const float vcj = comp(vc, j), vmj = comp(vm, j), vpj = comp(vp, j);
       if constexpr (!FLUX) {
         const float div = (uR - uL) / 2.f + (vpj - vmj) / 2.f;
-        T[k][0][j] = 1.f - dt * (div + (fabsf(ucj) + fabsf(vcj)));
-        T[k][1][j] = dt * ucj;
-        T[k][2][j] = dt * vcj;
+        c0[j] = 1.f - dt * (div + (fabsf(ucj) + fabsf(vcj)));  // kept in shared memory
+        T[k][0][j] = dt * ucj;
+        T[k][1][j] = dt * vcj;
       } else {
         T[k][0][j] = 0.5f * (ucj + uR);
         T[k][1][j] = 0.5f * (uL + ucj);
@@ -965,6 +968,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         T[k][3][j] = 0.5f * (vmj + vcj);
       }
     }
+    if constexpr (!FLUX) st4(st0, r, c, mk4(c0));
   }
   __syncthreads();
   // 3. SUB substeps of Eqs. 32-36
@@ -976,16 +980,18 @@ __global__ void __launch_bounds__(NW * 32, 1)
       const int r = warp + NW * k;
       if (r < lo || r >= RY - lo) continue;  // warp-uniform
       const float4 pc = ld4(sp, r, c), pu = ld4(sp, r - 1, c), pd = ld4(sp, r + 1, c);
+      float4 t0v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (!FLUX) t0v = ld4(st0, r, c);
       const float l0 = __shfl_up_sync(FULL, pc.w, 1), r3 = __shfl_down_sync(FULL, pc.x, 1);
       float e[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float pcj = comp(pc, j), pl = j == 0 ? l0 : comp(pc, j - 1), pr = j == 3 ? r3 : comp(pc, j + 1);
         if constexpr (!FLUX) {
-          const float t1 = T[k][1][j], t2 = T[k][2][j];
+          const float t1 = T[k][0][j], t2 = T[k][1][j];
           const float upx = t1 > 0.f ? pl : pr;  // u = 0 contributes nothing
           const float upy = t2 > 0.f ? comp(pu, j) : comp(pd, j);
-          e[j] = T[k][0][j] * pcj + fabsf(t1) * upx + fabsf(t2) * upy;
+          e[j] = comp(t0v, j) * pcj + fabsf(t1) * upx + fabsf(t2) * upy;
         } else {
           const float t0 = T[k][0][j], t1 = T[k][1][j], t2 = T[k][2][j], t3 = T[k][3][j];
           const float Jpx = t0 > 0.f ? t0 * pcj : t0 * pr;
@@ -1197,7 +1203,7 @@ template <bool FLUX, int SUB, int K, int NW>
 cudaError_t fd2d_block_one(lbm_handle *h, const KParams<float> &p, const float *src, float *dst) {
   using G = FDBlock<SUB, K, NW>;
   dim3 grid((p.Lx + G::TX - 1) / G::TX, (p.Ly + G::TY - 1) / G::TY);
-  return launch_pdl(fd2d_block_kernel<FLUX, SUB, K, NW>, grid, dim3(NW * 32), G::smem, h->stream,
+  return launch_pdl(fd2d_block_kernel<FLUX, SUB, K, NW>, grid, dim3(NW * 32), G::smem_of(FLUX), h->stream,
                     src, static_cast<const float *>(h->u), dst, p);
 }
 
@@ -1235,11 +1241,11 @@ cudaError_t fd2d_block_configure() {
   if (e == cudaSuccess)                                                                         \
     e = cudaFuncSetAttribute(fd2d_block_kernel<false, SB, RYY / NWW, NWW>,                      \
                              cudaFuncAttributeMaxDynamicSharedMemorySize,                        \
-                             (int)FDBlock<SB, RYY / NWW, NWW>::smem);                            \
+                             (int)FDBlock<SB, RYY / NWW, NWW>::smem_of(false));                  \
   if (e == cudaSuccess)                                                                         \
     e = cudaFuncSetAttribute(fd2d_block_kernel<true, SB, RYY / NWW, NWW>,                       \
                              cudaFuncAttributeMaxDynamicSharedMemorySize,                        \
-                             (int)FDBlock<SB, RYY / NWW, NWW>::smem);
+                             (int)FDBlock<SB, RYY / NWW, NWW>::smem_of(true));
   FDB_SHAPES(FDB_CFG)
 #undef FDB_CFG
   return e;
