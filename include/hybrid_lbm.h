@@ -108,6 +108,31 @@ typedef struct lbm_handle lbm_handle;
  * or NULL for a stream owned by the handle.  Does not initialise the fields. */
 int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out);
 
+/* Device buffers a caller (for example a PyTorch program) allocates and lends
+ * to a handle: the two population lattices (q planes of S sites each, q = 9
+ * or 19, element type FP64 / FP32 / FP16 as the precision stores deviations),
+ * the three phi planes (t, t+1, FD scratch) and the dims velocity planes u*
+ * (FP64 in LBM_F64, FP32 otherwise).  Each pointer must be 16-byte aligned
+ * and hold at least the byte count lbm_buffer_bytes reports. */
+typedef struct {
+  void *populations[2];
+  void *phi[3];
+  void *u;
+} lbm_buffers;
+
+/* Byte counts of the lbm_buffers members for *params: bytes[0] for each
+ * population lattice, bytes[1] for each phi plane, bytes[2] for u*.  Pure
+ * arithmetic (no CUDA call); EINVAL as lbm_create's validation. */
+int lbm_buffer_bytes(const lbm_params *params, unsigned long long bytes[3]);
+
+/* lbm_create on caller-owned buffers (the handle adopts them):
+ * the handle reads and writes them but never frees them; they must outlive
+ * the handle.  Everything else (FP64 staging, diagnostics scratch, the 3D FD
+ * planes) is still allocated by the handle.  EINVAL for a NULL or unaligned
+ * buffer, before any CUDA call. */
+int lbm_create_with_buffers(const lbm_params *params, void *cuda_stream, const lbm_buffers *buffers,
+                            lbm_handle **out);
+
 /* Sets t = 0, phi(0) = phi and populations f_i = feq_i(n, u - F/(2n)) (Eqs. 15,
  * 18), F from Eq. 28 at t = 0, so that the u* of Eq. 18 at t = 0 equals u.
  * n, phi, ux, uy (and uz in 3D; ignored and may be NULL in 2D) are host arrays

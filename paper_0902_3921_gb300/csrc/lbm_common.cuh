@@ -156,6 +156,7 @@ struct lbm_handle {
   void *h[2] = {nullptr, nullptr};
   void *phi[3] = {nullptr, nullptr, nullptr};  // [2] = FD scratch between launches
   void *fd_a = nullptr, *fd_p = nullptr;        // 3D FP32 FD: phih and psi planes
+  bool adopted = false;                        // h, phi, u belong to the caller
   void *u = nullptr;
   void *dn = nullptr;
   double *staging = nullptr;   // (dims + 3) * S doubles

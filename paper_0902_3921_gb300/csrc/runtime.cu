@@ -4,6 +4,7 @@
 // checkpoints.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -494,7 +495,41 @@ int lbm_lattice(int dims, int *e, double *w) {
   return q;
 }
 
+int lbm_buffer_bytes(const lbm_params *params, unsigned long long bytes[3]) {
+  if (bytes == nullptr) return fail(nullptr, LBM_EINVAL, "bytes is NULL");
+  std::string why;
+  int rc = validate(params, why);
+  if (rc) return fail(nullptr, rc, why);
+  const unsigned long long S =
+      (unsigned long long)params->Lx * params->Ly * (params->dims == 3 ? params->Lz : 1);
+  const int q = params->dims == 2 ? 9 : 19;
+  bytes[0] = storage_bytes(params->precision) * q * S;
+  bytes[1] = compute_bytes(params->precision) * S;
+  bytes[2] = compute_bytes(params->precision) * params->dims * S;
+  return LBM_OK;
+}
+
+static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_buffers *adopt,
+                       lbm_handle **out);
+
 int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out) {
+  return create_impl(params, cuda_stream, nullptr, out);
+}
+
+int lbm_create_with_buffers(const lbm_params *params, void *cuda_stream, const lbm_buffers *buffers,
+                            lbm_handle **out) {
+  if (out) *out = nullptr;
+  if (buffers == nullptr) return fail(nullptr, LBM_EINVAL, "buffers is NULL");
+  const void *ptrs[6] = {buffers->populations[0], buffers->populations[1], buffers->phi[0],
+                         buffers->phi[1], buffers->phi[2], buffers->u};
+  for (const void *q : ptrs)
+    if (q == nullptr || reinterpret_cast<uintptr_t>(q) % 16 != 0)
+      return fail(nullptr, LBM_EINVAL, "every lbm_buffers pointer must be non-NULL and 16-byte aligned");
+  return create_impl(params, cuda_stream, buffers, out);
+}
+
+static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_buffers *adopt,
+                       lbm_handle **out) {
   if (out == nullptr) return fail(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -562,8 +597,15 @@ int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out) {
                 {&h->dn, P.T != 1.0 / 3.0 ? cb * (size_t)h->S : 0},
                 {&h->fd_a, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0},
                 {&h->fd_p, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0}};
+  if (adopt) {
+    h->adopted = true;
+    h->h[0] = adopt->populations[0];
+    h->h[1] = adopt->populations[1];
+    for (int k = 0; k < 3; k++) h->phi[k] = adopt->phi[k];
+    h->u = adopt->u;
+  }
   for (auto &a : allocs) {
-    if (a.n == 0) continue;
+    if (a.n == 0 || *a.p != nullptr) continue;  // adopted
     cudaError_t e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc"));
   }
@@ -787,10 +829,13 @@ void lbm_free(lbm_handle *h) {
     cudaEventDestroy(ev.b);
   }
   for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
-  void *ptrs[] = {h->h[0], h->h[1], h->phi[0], h->phi[1], h->phi[2], h->u, h->dn,
-                  h->staging, h->partials, h->dres, h->fd_a, h->fd_p};
-  for (void *p : ptrs)
+  void *owned[] = {h->dn, h->staging, h->partials, h->dres, h->fd_a, h->fd_p};
+  void *lent[] = {h->h[0], h->h[1], h->phi[0], h->phi[1], h->phi[2], h->u};
+  for (void *p : owned)
     if (p) cudaFree(p);
+  if (!h->adopted)
+    for (void *p : lent)
+      if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

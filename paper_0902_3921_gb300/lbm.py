@@ -26,7 +26,7 @@ LBM_ADV_PAPER, LBM_ADV_FLUX = 0, 1
 PRECISIONS = {"f64": LBM_F64, "f32dev": LBM_F32DEV, "f16dev": LBM_F16DEV}
 
 # the exported symbols of include/hybrid_lbm.h
-EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_populations",
+EXPORTS = ("lbm_create", "lbm_buffer_bytes", "lbm_create_with_buffers", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_populations",
            "lbm_lattice", "lbm_diagnostics", "lbm_synchronize", "lbm_time", "lbm_fd_substeps",
            "lbm_set_graphs", "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_save",
            "lbm_load", "lbm_free", "lbm_last_error", "lbm_tuning", "lbm_diagnostics_noalloc",
@@ -37,6 +37,11 @@ EXPORTS = ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_popu
            "lbm_net_normalisation", "lbm_net_forward", "lbm_net_layer_times", "lbm_net_train_step",
            "lbm_surrogate_state",
            "lbm_surrogate_advance", "lbm_net_free", "lbm_net_last_error")
+
+
+class c_lbm_buffers(ctypes.Structure):
+    _fields_ = [("populations", ctypes.c_void_p * 2), ("phi", ctypes.c_void_p * 3),
+                ("u", ctypes.c_void_p)]
 
 
 class c_lbm_params(ctypes.Structure):
@@ -85,6 +90,9 @@ def load_library(path: str = LIB_PATH):
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
     H = ctypes.c_void_p
     lib.lbm_create.argtypes = [ctypes.POINTER(c_lbm_params), vp, ctypes.POINTER(H)]
+    lib.lbm_buffer_bytes.argtypes = [ctypes.POINTER(c_lbm_params), ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.lbm_create_with_buffers.argtypes = [ctypes.POINTER(c_lbm_params), vp,
+                                            ctypes.POINTER(c_lbm_buffers), ctypes.POINTER(H)]
     lib.lbm_init_fields.argtypes = [H, dp, dp, dp, dp, dp]
     lib.lbm_step.argtypes = [H, ctypes.c_longlong]
     lib.lbm_moments.argtypes = [H, dp, dp, dp, dp, dp]
@@ -235,6 +243,36 @@ def lbm_create(params: LbmParams, cuda_stream: int | None = None):
     return h
 
 
+def lbm_buffer_bytes(params: LbmParams):
+    """(population lattice, phi plane, u* planes) byte counts for lbm_create_with_buffers."""
+    lib = load_library()
+    b = (ctypes.c_ulonglong * 3)()
+    cp = params.to_c()
+    rc = lib.lbm_buffer_bytes(ctypes.byref(cp), b)
+    if rc != LBM_OK:
+        raise LbmError(rc, lib.lbm_last_error(None).decode())
+    return int(b[0]), int(b[1]), int(b[2])
+
+
+def lbm_create_with_buffers(params: LbmParams, populations, phi, u, cuda_stream: int | None = None):
+    """lbm_create on caller-owned device buffers, given as integer pointers:
+    populations (2), phi (3), u.  The caller keeps them alive."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    cp = params.to_c()
+    buf = c_lbm_buffers()
+    for k in range(2):
+        buf.populations[k] = populations[k]
+    for k in range(3):
+        buf.phi[k] = phi[k]
+    buf.u = u
+    rc = lib.lbm_create_with_buffers(ctypes.byref(cp), ctypes.c_void_p(cuda_stream or 0),
+                                     ctypes.byref(buf), ctypes.byref(h))
+    if rc != LBM_OK:
+        raise LbmError(rc, lib.lbm_last_error(None).decode())
+    return h
+
+
 def lbm_init_fields(h, params: LbmParams, n, phi, u):
     S = params.S
     n, phi = _f64(n, S), _f64(phi, S)
@@ -364,13 +402,23 @@ def lbm_last_error(h=None) -> str:
 
 @dataclass
 class Lattice:
-    """Owning wrapper around one lbm_handle."""
+    """Owning wrapper around one lbm_handle.  buffers (optional): caller-owned
+    device tensors {"populations": (a, b), "phi": (a, b, c), "u": a} with
+    .data_ptr() (e.g. torch tensors of the sizes lbm_buffer_bytes gives); the
+    lattice keeps references to them so that they outlive the handle."""
     params: LbmParams
     stream: int | None = None
+    buffers: dict | None = None
     handle: object = field(default=None, init=False)
 
     def __post_init__(self):
-        self.handle = lbm_create(self.params, self.stream)
+        if self.buffers is None:
+            self.handle = lbm_create(self.params, self.stream)
+        else:
+            b = self.buffers
+            self.handle = lbm_create_with_buffers(
+                self.params, [t.data_ptr() for t in b["populations"]], [t.data_ptr() for t in b["phi"]],
+                b["u"].data_ptr(), self.stream)
 
     def init_fields(self, n, phi, u):
         lbm_init_fields(self.handle, self.params, n, phi, u)

@@ -43,7 +43,8 @@ def test_struct_layouts_match_header():
     # the ctypes mirrors must match the C structs field for field
     src = open(os.path.join(ROOT, "include", "hybrid_lbm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    for name, mirror in (("lbm_params", lbm.c_lbm_params), ("lbm_diag", lbm.c_lbm_diag)):
+    for name, mirror in (("lbm_params", lbm.c_lbm_params), ("lbm_diag", lbm.c_lbm_diag),
+                         ("lbm_buffers", lbm.c_lbm_buffers)):
         seg = [s for s in src.split("typedef struct {") if ("} " + name + ";") in s][0]
         body = seg.split("} " + name + ";")[0]
         fields = re.findall(r"(\w+)(?:\[\d\])?\s*[;,]", body)
@@ -102,3 +103,24 @@ def test_fd_substep_rule():
         lbm.lbm_create(lbm.LbmParams(fd_substeps=2))
     with pytest.raises(lbm.LbmError, match="m >= 6"):
         lbm.lbm_create(lbm.LbmParams(dims=3, Lz=8, fd_substeps=5))
+
+
+def test_buffer_bytes_and_adoption_checks(lib):
+    """lbm_buffer_bytes is arithmetic on the parameters; lbm_create_with_buffers
+    refuses NULL or unaligned buffers before touching CUDA."""
+    kw = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5)
+    S2 = 64 * 48
+    assert lbm.lbm_buffer_bytes(lbm.LbmParams(Lx=64, Ly=48, precision=lbm.LBM_F32DEV, **kw)) == (
+        9 * 4 * S2, 4 * S2, 2 * 4 * S2)
+    assert lbm.lbm_buffer_bytes(lbm.LbmParams(Lx=64, Ly=48, precision=lbm.LBM_F64, **kw)) == (
+        9 * 8 * S2, 8 * S2, 2 * 8 * S2)
+    S3 = 10 * 12 * 14
+    assert lbm.lbm_buffer_bytes(lbm.LbmParams(dims=3, Lx=10, Ly=12, Lz=14, precision=lbm.LBM_F16DEV,
+                                              **kw)) == (19 * 2 * S3, 4 * S3, 3 * 4 * S3)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_buffer_bytes(lbm.LbmParams(Lx=64, Ly=48, **dict(kw, tau=0.4)))
+    p = lbm.LbmParams(Lx=64, Ly=48, precision=lbm.LBM_F32DEV, **kw)
+    for pops, phi, u in (([0, 4096], [4096] * 3, 4096), ([4096, 4096], [4096, 4100, 4096], 4096)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create_with_buffers(p, pops, phi, u)
+        assert e.value.code == lbm.LBM_EINVAL

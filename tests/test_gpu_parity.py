@@ -355,6 +355,36 @@ def test_3d_drop_64_precision_over_5000_steps():
         assert dphi <= bphi and du <= bu * umax, (prec, dphi, du, umax)
 
 
+@pytest.mark.parametrize("precision", [lbm.LBM_F32DEV, lbm.LBM_F64])
+def test_handle_on_torch_buffers(precision):
+    """A handle that adopts torch-allocated buffers gives the same bits as one
+    that owns its memory, and really works in them: after lbm_init_fields the
+    torch phi plane holds phi(0)."""
+    import torch
+    Lx, Ly = 70, 45
+    p = lbm.LbmParams(Lx=Lx, Ly=Ly, precision=precision, **CFG1)
+    bp, bphi, bu = lbm.lbm_buffer_bytes(p)
+    dt = torch.float64 if precision == lbm.LBM_F64 else torch.float32
+    es = torch.finfo(dt).bits // 8
+    bufs = {"populations": [torch.zeros(bp // es, dtype=dt, device="cuda") for _ in range(2)],
+            "phi": [torch.zeros(bphi // es, dtype=dt, device="cuda") for _ in range(3)],
+            "u": torch.zeros(bu // es, dtype=dt, device="cuda")}
+    phi = I.drop(2, Lx, Ly, R=10, phi0=1.0, xi=1.67)
+    n, u = I.rest(2, Lx, Ly)
+    a = lbm.Lattice(p, buffers=bufs).init_fields(n, phi, u)
+    a.synchronize()
+    np.testing.assert_array_equal(bufs["phi"][0].cpu().numpy().reshape(Ly, Lx), phi.astype(
+        np.float64 if precision == lbm.LBM_F64 else np.float32))
+    b = lbm.Lattice(p).init_fields(n, phi, u)
+    a.step(30)
+    b.step(30)
+    for xa, xb in zip(a.moments(), b.moments()):
+        assert np.array_equal(xa, xb)
+    a.close()
+    b.close()
+    assert torch.isfinite(bufs["populations"][0]).all()  # still usable after the handle is freed
+
+
 def test_checkpoint_roundtrip_bitwise(tmp_path):
     op, lp = _pair(48, 40, precision=lbm.LBM_F32DEV, **CFG1)
     phi = I.spinodal(2, 48, 40, seed=9)
