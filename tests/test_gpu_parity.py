@@ -8,6 +8,8 @@ Tolerances (written here, derived in the design notes):
     |d phi|_inf <= 1e-5 and |d u*|_inf <= 1e-3 max|u*_oracle|;
   * FP16-deviation mode: error reported, bounded loosely.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -383,6 +385,54 @@ def test_handle_on_torch_buffers(precision):
     a.close()
     b.close()
     assert torch.isfinite(bufs["populations"][0]).all()  # still usable after the handle is freed
+
+
+def _table1():
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table1_spurious_velocities.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append(tuple(float(v) for v in line.split()))
+    return rows
+
+
+def _drop128_umax(tau, N, Q, steps):
+    L = 128
+    p = lbm.LbmParams(Lx=L, Ly=L, a=-1e-3, b=1e-3, kappa=3e-3, tau=tau, Gamma=5.0, N=N, Q=Q,
+                      precision=lbm.LBM_F64)
+    phi = I.drop(2, L, L, R=32, phi0=1.0, xi=np.sqrt(2 * 3e-3 / 1e-3))
+    n, u = I.rest(2, L, L)
+    lat = lbm.Lattice(p).init_fields(n, phi, u)
+    lat.step(steps)
+    umax = lat.diagnostics()["u_max"] * np.sqrt(3.0)
+    lat.close()
+    return umax
+
+
+def test_table1_spurious_velocities():
+    """Sec. III, Table I (tests/golden/table1_spurious_velocities.txt): the
+    equilibrated drop's maximum spurious velocity for the paper's optimal
+    (N, Q) at each tau.  The paper states neither the run length nor the
+    initial profile; after 40 000 steps from a tanh profile the FP64 path
+    gives the printed values within a factor of 1.7 over two decades (within
+    6-37 % at 200 000 steps), decreasing with tau as printed.
+
+    With the SC stencils (N = 1/2, Q = 1) the force's Laplacian is the
+    5-point one that Eq. 36 uses (Sec. II C), so the discrete system has an
+    exact stationary drop with u* = 0: mu_D is uniform once the diffusion has
+    converged and -phi d_D mu_D vanishes.  The SC velocity therefore decays
+    far below the OC value instead of exceeding it ten-fold as Fig. 4 shows;
+    the test pins the property of the scheme as printed."""
+    rows = _table1()
+    got = []
+    for tau, N, Q, paper in rows:
+        umax = _drop128_umax(tau, N, Q, 40000)
+        print(f"Table I: tau {tau} N {N} Q {Q}: |u*_max|/c_s = {umax:.3e} (paper {paper:.3e})")
+        assert paper / 1.7 <= umax <= paper * 1.7, (tau, umax, paper)
+        got.append(umax)
+    assert all(a > b for a, b in zip(got[:5], got[1:5]))  # tau = 0.6 .. 5: decreasing
+    sc = _drop128_umax(1.0, 0.5, 1.0, 40000)
+    print(f"SC stencils at tau 1: |u*_max|/c_s = {sc:.3e}")
+    assert sc < 0.02 * got[2]
 
 
 def test_checkpoint_roundtrip_bitwise(tmp_path):
