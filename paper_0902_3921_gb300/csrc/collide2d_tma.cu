@@ -1,0 +1,542 @@
+// collide2d_tma.cu -- D2Q9 collide-and-stream with its inputs staged in shared
+// memory by the tensor memory accelerator (FP32 deviation storage).
+//
+// The arithmetic is that of the shared-memory collide kernels of
+// kernels_2d.cu: mu = a phi + b phi^3 - kappa lap_D phi (Eqs. 5, 31) on the
+// tile + 1, F = -phi d_D mu (Eqs. 28, 30) plus n g (and grad((c_s^2 - T) n)
+// when T != 1/3), n and u* (Eqs. 12, 18), BGK with the forcing term (Eqs. 15,
+// 17, 29).  What differs is how a 32 x 32 tile's inputs reach shared memory:
+// thread 0 issues ten tiled TMA copies that complete on one mbarrier,
+//   plane i with e_x =  0: columns x0 .. x0 + 31      (x sits at column tx)
+//   plane i with e_x = +1: columns x0 - 4 .. x0 + 31  (x - 1 sits at column tx + 3)
+//   plane i with e_x = -1: columns x0 .. x0 + 35      (x + 1 sits at column tx + 1)
+//   (rows y0 - e_y .. y0 - e_y + 31: the pull f_i(r, t) = buf_i(r - e_i))
+//   phi: columns x0 - 4 .. x0 + 35, rows y0 - 2 .. y0 + 33 (halo 2 for mu and d_D mu)
+// A copy's x origin must be a multiple of 16 bytes, hence the 36- and
+// 40-column boxes.  The copies do not wrap around the periodic lattice:
+// cells outside it arrive as zeros, and the CTAs on the lattice's edges
+// reload the cells they use from the periodic images before computing.
+//
+// PACK evaluates the collision of a thread's two rows at a time with packed
+// FP32 pair instructions (add/mul/fma .f32x2); MINB is the number of CTAs
+// per SM the registers are budgeted for.  Variants (the collide_rows value of
+// the handle's launch shapes): 3 scalar (3 CTAs/SM), 5 packed (4), 6 packed (3).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "lbm_common.cuh"
+
+namespace hlbm {
+
+namespace {
+
+constexpr int TT = 32;                // tile side in sites
+constexpr int TR = 4;                 // rows per thread (32 x 8 threads)
+constexpr int PHW = 40, PHH = 36;     // phi box
+constexpr int MUW = TT + 2;           // mu on the tile + 1
+constexpr int TMA_MIN_SIDE = 64;
+
+// number of planes j < i pulled along x (e_x != 0): 0 0 1 1 2 2 3 4 5 6
+__host__ __device__ constexpr int nshift(int i) { return i <= 5 ? i / 2 : i - 3; }
+__host__ __device__ constexpr int plane_w(int i) { return q9_ex(i) == 0 ? TT : TT + 4; }
+__host__ __device__ constexpr int plane_off(int i) { return TT * (TT * i + 4 * nshift(i)); }
+__host__ __device__ constexpr int col_off(int i) { return q9_ex(i) > 0 ? 3 : (q9_ex(i) < 0 ? 1 : 0); }
+__host__ __device__ constexpr int box_dx(int i) { return q9_ex(i) > 0 ? -4 : 0; }
+
+constexpr int POP_FLOATS = plane_off(9);
+constexpr int OFF_POP = 128;  // bytes [0, 128): the mbarrier
+constexpr int OFF_PHI = OFF_POP + 4 * POP_FLOATS;
+constexpr int OFF_MU = OFF_PHI + 4 * PHW * PHH;
+constexpr int OFF_PN = OFF_MU + 4 * MUW * MUW;
+constexpr uint32_t TX_BYTES = 4u * (POP_FLOATS + PHW * PHH);
+static_assert(OFF_PHI % 128 == 0 && (4 * plane_off(1)) % 128 == 0 && (4 * plane_off(2)) % 128 == 0,
+              "TMA destinations must be 128-byte aligned");
+
+// + 128: room to align the dynamic shared-memory base to 128 bytes
+template <bool TGEN>
+constexpr size_t tma_smem() {
+  return 128 + OFF_PN + (TGEN ? 4 * MUW * MUW : 0);
+}
+
+__device__ int g_collide_tma_err = 0;
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the mbarrier phase `parity` to complete; gives up after limit_ns.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = gtimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                       uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ float2 s2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, s2(-1.f), a); }
+
+// mu at the centre of a 3 x 3 window of phi (explicitly rounded: the same
+// site's mu is evaluated by the interior and the frame code)
+__device__ __forceinline__ float mu_at(const KParams<float> &p, const float (&w)[3][3]) {
+  float lap = rn_mul(p.R, w[0][0]);
+  lap = rn_fma(p.Q, w[0][1], lap);
+  lap = rn_fma(p.R, w[0][2], lap);
+  lap = rn_fma(p.Q, w[1][0], lap);
+  lap = rn_fma(p.C0, w[1][1], lap);
+  lap = rn_fma(p.Q, w[1][2], lap);
+  lap = rn_fma(p.R, w[2][0], lap);
+  lap = rn_fma(p.Q, w[2][1], lap);
+  lap = rn_fma(p.R, w[2][2], lap);
+  const float c = w[1][1];
+  const float c3 = rn_mul(rn_mul(c, c), c);
+  return rn_fma(p.a, c, rn_fma(p.b, c3, rn_mul(-p.kappa, lap)));
+}
+
+template <bool TGEN, int MODE, bool PACK, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    collide2d_tma_kernel(const __grid_constant__ CUtensorMap map_p32,
+                         const __grid_constant__ CUtensorMap map_p36,
+                         const __grid_constant__ CUtensorMap map_phi, const float *__restrict__ hin,
+                         float *__restrict__ hout, const float *__restrict__ phi,
+                         const float *__restrict__ dn, float *__restrict__ uout,
+                         double *__restrict__ stg, KParams<float> p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *base = smem_raw + ((128u - (su32(smem_raw) & 127u)) & 127u);
+  const uint32_t bar = su32(base);
+  float *pops = reinterpret_cast<float *>(base + OFF_POP);
+  float(*sphi)[PHW] = reinterpret_cast<float(*)[PHW]>(base + OFF_PHI);
+  float(*smu)[MUW] = reinterpret_cast<float(*)[MUW]>(base + OFF_MU);
+  float(*spn)[MUW] = reinterpret_cast<float(*)[MUW]>(base + OFF_PN);
+  const int Lx = p.Lx, Ly = p.Ly;
+  const long long Sz = (long long)Lx * Ly;
+  const int x0 = blockIdx.x * TT, y0 = blockIdx.y * TT;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ly0 = TR * ty, x = x0 + tx;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();  // phi(t) and the populations come from the previous kernels
+  pdl_trigger();
+  // 1. the ten copies (one thread), the T != 1/3 pressure by plain loads meanwhile
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TX_BYTES)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      tma_3d(su32(pops + plane_off(i)), plane_w(i) == TT ? &map_p32 : &map_p36, x0 + box_dx(i),
+             y0 - q9_ey(i), i, bar);
+    tma_2d(su32(&sphi[0][0]), &map_phi, x0 - 4, y0 - 2, bar);
+  }
+  if constexpr (TGEN) {
+    for (int k = tid; k < MUW * MUW; k += 256) {
+      const int ry = k / MUW, rx = k - ry * MUW;
+      const int gx = wrapi(x0 + rx - 1, Lx), gy = wrapi(y0 + ry - 1, Ly);
+      spn[ry][rx] = p.cs2mT * (1.f + dn[(long long)gy * Lx + gx]);
+    }
+  }
+  const bool arrived = bar_wait(bar, 0, 500000000ull);
+  if (!__syncthreads_and(arrived)) {
+    // the copies did not complete within 0.5 s: report, let them land, leave
+    if (tid == 0) {
+      atomicExch(&g_collide_tma_err, 1);
+      bar_wait(bar, 0, 500000000ull);
+    }
+    return;
+  }
+  // 2. periodic images of the cells the copies left as zeros (edge CTAs only)
+  if (x0 == 0 || y0 == 0 || x0 + TT + 2 > Lx || y0 + TT + 2 > Ly) {
+    for (int k = tid; k < (TT + 4) * (TT + 4); k += 256) {  // phi: rows y0-2 .., columns x0-2 ..
+      const int ry = k / (TT + 4), rx = k - ry * (TT + 4);
+      const int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+      if (gx < 0 || gx >= Lx || gy < 0 || gy >= Ly)
+        sphi[ry][rx + 2] = phi[(long long)wrapi(gy, Ly) * Lx + wrapi(gx, Lx)];
+    }
+    // populations: the pulls from outside the lattice start at the first or
+    // last column or row
+    for (int k = tid; k < 8 * 2 * TT; k += 256) {
+      const int i = 1 + k / (2 * TT), j = k % (2 * TT);
+      const int ex = q9_ex(i), ey = q9_ey(i);
+      int xs, ys;
+      if (j < TT) {
+        if (ex == 0) continue;
+        xs = ex > 0 ? 0 : Lx - 1;
+        ys = y0 + j;
+      } else {
+        if (ey == 0) continue;
+        ys = ey > 0 ? 0 : Ly - 1;
+        xs = x0 + j - TT;
+      }
+      if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + TT || ys >= Ly) continue;
+      const int sx = wrapi(xs - ex, Lx), sy = wrapi(ys - ey, Ly);
+      pops[plane_off(i) + (ys - y0) * plane_w(i) + (xs - x0) + col_off(i)] =
+          hin[i * Sz + (long long)sy * Lx + sx];
+    }
+  }
+  __syncthreads();
+  // 3. mu on the tile + 1: the interior four rows per thread with rows reused
+  //    from registers, then the one-site frame
+  {
+    float w[3][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) w[k + 1][j] = sphi[ly0 + 1 + k][tx + 3 + j];
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        w[0][j] = w[1][j];
+        w[1][j] = w[2][j];
+        w[2][j] = sphi[ly0 + 3 + r][tx + 3 + j];
+      }
+      smu[ly0 + 1 + r][tx + 1] = mu_at(p, w);
+    }
+    for (int k = tid; k < 2 * MUW + 2 * (MUW - 2); k += 256) {
+      int my, mx;
+      if (k < MUW) {
+        my = 0;
+        mx = k;
+      } else if (k < 2 * MUW) {
+        my = MUW - 1;
+        mx = k - MUW;
+      } else {
+        const int q = k - 2 * MUW;
+        my = 1 + (q >> 1);
+        mx = (q & 1) ? MUW - 1 : 0;
+      }
+      float v[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2) v[a][b2] = sphi[my + a][mx + b2 + 2];
+      smu[my][mx] = mu_at(p, v);
+    }
+  }
+  __syncthreads();
+
+  // 4. force, moments and collision; mu rows reused from registers
+  float m3[3][3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m3[k + 1][j] = smu[ly0 + k][tx + j];
+  // F = -phi d_D mu (+ d_D((c_s^2 - T) n)) at tile row ly, m3 = mu rows ly-1 .. ly+1
+  auto force_at = [&](int ly, float &Fx, float &Fy) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      m3[0][j] = m3[1][j];
+      m3[1][j] = m3[2][j];
+      m3[2][j] = smu[ly + 2][tx + j];
+    }
+    float gmx = -p.M * m3[0][0];
+    gmx += p.M * m3[0][2];
+    gmx += -p.N * m3[1][0];
+    gmx += p.N * m3[1][2];
+    gmx += -p.M * m3[2][0];
+    gmx += p.M * m3[2][2];
+    float gmy = -p.M * m3[0][0];
+    gmy += -p.N * m3[0][1];
+    gmy += -p.M * m3[0][2];
+    gmy += p.M * m3[2][0];
+    gmy += p.N * m3[2][1];
+    gmy += p.M * m3[2][2];
+    const float ph = sphi[ly + 2][tx + 4];
+    Fx = -ph * gmx;
+    Fy = -ph * gmy;
+    if constexpr (TGEN) {
+      const int mx = tx + 1, my = ly + 1;
+      float px = -p.M * spn[my - 1][mx - 1];
+      px += p.M * spn[my - 1][mx + 1];
+      px += -p.N * spn[my][mx - 1];
+      px += p.N * spn[my][mx + 1];
+      px += -p.M * spn[my + 1][mx - 1];
+      px += p.M * spn[my + 1][mx + 1];
+      float py = -p.M * spn[my - 1][mx - 1];
+      py += -p.N * spn[my - 1][mx];
+      py += -p.M * spn[my - 1][mx + 1];
+      py += p.M * spn[my + 1][mx - 1];
+      py += p.N * spn[my + 1][mx];
+      py += p.M * spn[my + 1][mx + 1];
+      Fx += px;
+      Fy += py;
+    }
+  };
+  auto pop = [&](int i, int ly) { return pops[plane_off(i) + ly * plane_w(i) + tx + col_off(i)]; };
+  const float om = p.tau_inv, keep = 1.f - p.tau_inv;
+
+  if constexpr (!PACK) {
+#pragma unroll 1
+    for (int r = 0; r < TR; ++r) {
+      const int ly = ly0 + r, y = y0 + ly;
+      float Fx, Fy;
+      force_at(ly, Fx, Fy);
+      if (x >= Lx || y >= Ly) continue;
+      float h[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = pop(i, ly);
+      float dens = h[0];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) dens += h[i];
+      const float jx = ((h[1] - h[3]) + (h[5] - h[7])) + (h[8] - h[6]);
+      const float jy = ((h[2] - h[4]) + (h[5] - h[7])) + (h[6] - h[8]);
+      const float n = 1.f + dens;
+      Fx += n * p.gx;
+      Fy += n * p.gy;
+      const float inv_n = 1.f / n;
+      const float ux = (jx + 0.5f * Fx) * inv_n;
+      const float uy = (jy + 0.5f * Fy) * inv_n;
+      const long long s = (long long)y * Lx + x;
+      if constexpr (MODE == COLLIDE_MOMENTS) {
+        stg[s] = (double)n;
+        stg[Sz + s] = (double)sphi[ly + 2][tx + 4];
+        stg[2 * Sz + s] = (double)ux;
+        stg[3 * Sz + s] = (double)uy;
+        continue;
+      }
+      const float usq = ux * ux + uy * uy;
+      const float uF = ux * Fx + uy * Fy;
+      {
+        const float w = float(q9_w(0));
+        const float heq = w * (dens - n * (1.5f * usq));
+        const float Fi = p.pref * w * (-3.f * uF);
+        hout[s] = keep * h[0] + om * heq + Fi;
+      }
+      const float base = dens - n * (1.5f * usq);
+      const float n3 = 3.f * n, n45 = 4.5f * n;
+      const float pF3 = 3.f * p.pref, pF9 = 9.f * p.pref, puF = 3.f * p.pref * uF;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = k < 2 ? k + 1 : k + 3, ib = i + 2;  // (1,3) (2,4) (5,7) (6,8)
+        const float w = float(q9_w(i));
+        const float eu = float(q9_ex(i)) * ux + float(q9_ey(i)) * uy;
+        const float eF = float(q9_ex(i)) * Fx + float(q9_ey(i)) * Fy;
+        const float even = w * (base + n45 * eu * eu);
+        const float odd = w * (n3 * eu);
+        const float Feven = w * (pF9 * eu * eF - puF);
+        const float Fodd = w * (pF3 * eF);
+        hout[i * Sz + s] = keep * h[i] + om * (even + odd) + (Feven + Fodd);
+        hout[ib * Sz + s] = keep * h[ib] + om * (even - odd) + (Feven - Fodd);
+      }
+      uout[s] = ux;
+      uout[Sz + s] = uy;
+    }
+  } else {
+    static_assert(MODE == COLLIDE_STEP, "the packed collision is a step kernel");
+    // per weight class w: A = w / tau, B = w (1 - 1/2tau) (Eqs. 17, 29)
+    const float A0 = om * float(q9_w(0)), B0 = p.pref * float(q9_w(0));
+    const float A1 = om * float(q9_w(1)), B1 = p.pref * float(q9_w(1));
+    const float A2 = om * float(q9_w(5)), B2 = p.pref * float(q9_w(5));
+#pragma unroll 1
+    for (int r = 0; r < TR; r += 2) {
+      const int lya = ly0 + r, ya = y0 + lya;
+      float2 Fx, Fy;
+      force_at(lya, Fx.x, Fy.x);
+      force_at(lya + 1, Fx.y, Fy.y);
+      if (x >= Lx || ya >= Ly) continue;
+      const bool row_b = ya + 1 < Ly;
+      float2 h[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = make_float2(pop(i, lya), pop(i, lya + 1));
+      float2 dens = h[0];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) dens = add2(dens, h[i]);
+      const float2 jx = add2(add2(sub2(h[1], h[3]), sub2(h[5], h[7])), sub2(h[8], h[6]));
+      const float2 jy = add2(add2(sub2(h[2], h[4]), sub2(h[5], h[7])), sub2(h[6], h[8]));
+      const float2 n = add2(s2(1.f), dens);
+      Fx = fma2(n, s2(p.gx), Fx);
+      Fy = fma2(n, s2(p.gy), Fy);
+      const float2 inv_n = make_float2(1.f / n.x, 1.f / n.y);
+      const float2 ux = mul2(fma2(s2(0.5f), Fx, jx), inv_n);
+      const float2 uy = mul2(fma2(s2(0.5f), Fy, jy), inv_n);
+      const float2 usq = fma2(ux, ux, mul2(uy, uy));
+      const float2 uF = fma2(ux, Fx, mul2(uy, Fy));
+      // w (base + 4.5 n eu^2) / tau + w pref (9 eu eF - 3 uF) = A se + B fe  (even part)
+      // w 3 n eu / tau + w pref 3 eF                         = An3 eu + 3B eF (odd part)
+      const float2 base = fma2(n, mul2(usq, s2(-1.5f)), dens);
+      const float2 n45 = mul2(n, s2(4.5f)), m3uF = mul2(uF, s2(-3.f));
+      const float2 An3_1 = mul2(n, s2(3.f * A1)), An3_2 = mul2(n, s2(3.f * A2));
+      float2 o[9];
+      o[0] = fma2(s2(keep), h[0], fma2(s2(A0), base, mul2(s2(-3.f * B0), uF)));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = k < 2 ? k + 1 : k + 3, ib = i + 2;
+        const float A = k < 2 ? A1 : A2, B = k < 2 ? B1 : B2;
+        const float2 An3 = k < 2 ? An3_1 : An3_2;
+        float2 eu, eF;
+        if (k == 0) { eu = ux; eF = Fx; }
+        else if (k == 1) { eu = uy; eF = Fy; }
+        else if (k == 2) { eu = add2(ux, uy); eF = add2(Fx, Fy); }
+        else { eu = sub2(uy, ux); eF = sub2(Fy, Fx); }
+        const float2 se = fma2(mul2(n45, eu), eu, base);
+        const float2 fe = fma2(mul2(eu, s2(9.f)), eF, m3uF);
+        const float2 E = fma2(s2(A), se, mul2(s2(B), fe));
+        const float2 O = fma2(eu, An3, mul2(s2(3.f * B), eF));
+        o[i] = add2(fma2(s2(keep), h[i], E), O);
+        o[ib] = sub2(fma2(s2(keep), h[ib], E), O);
+      }
+      const long long s = (long long)ya * Lx + x;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) hout[i * Sz + s] = o[i].x;
+      uout[s] = ux.x;
+      uout[Sz + s] = uy.x;
+      if (row_b) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hout[i * Sz + s + Lx] = o[i].y;
+        uout[s + Lx] = ux.y;
+        uout[Sz + s + Lx] = uy.y;
+      }
+    }
+  }
+}
+
+// ---- host side -------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+bool encode(CUtensorMap *map, void *ptr, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
+            const cuuint32_t *box) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint32_t ones[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, ptr, dims, strides, box, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// maps per buffer parity b: [b][0] populations 32 wide, [b][1] populations 36 wide, [b][2] phi
+CUtensorMap *maps_of(lbm_handle *h) { return reinterpret_cast<CUtensorMap *>(h->tma_maps); }
+
+bool prepare(lbm_handle *h) {
+  if (h->tma_ready) return true;
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  const cuuint64_t Lx = (cuuint64_t)h->P.Lx, Ly = (cuuint64_t)h->P.Ly;
+  const cuuint64_t pd[3] = {Lx, Ly, 9}, ps[2] = {4 * Lx, 4 * Lx * Ly};
+  const cuuint64_t fd[2] = {Lx, Ly}, fs[1] = {4 * Lx};
+  const cuuint32_t b32[3] = {TT, TT, 1}, b36[3] = {TT + 4, TT, 1}, bphi[2] = {PHW, PHH};
+  CUtensorMap *m = maps_of(h);
+  for (int b = 0; b < 2; ++b) {
+    if (!encode(&m[3 * b + 0], h->h[b], 3, pd, ps, b32) || !encode(&m[3 * b + 1], h->h[b], 3, pd, ps, b36) ||
+        !encode(&m[3 * b + 2], h->phi[b], 2, fd, fs, bphi))
+      return false;
+  }
+  h->tma_ready = true;
+  return true;
+}
+
+template <bool TGEN, int MODE, bool PACK, int MINB>
+cudaError_t launch_one(lbm_handle *h, int in, const KParams<float> &p) {
+  const CUtensorMap *m = maps_of(h) + 3 * in;
+  dim3 grid((p.Lx + TT - 1) / TT, (p.Ly + TT - 1) / TT), block(32, 256 / 32);
+  const float *hin = static_cast<const float *>(h->h[in]);
+  float *hout = static_cast<float *>(h->h[1 - in]);
+  const float *phi = static_cast<const float *>(h->phi[in]);
+  const float *dn = static_cast<const float *>(h->dn);
+  float *u = static_cast<float *>(h->u);
+  auto kern = collide2d_tma_kernel<TGEN, MODE, PACK, MINB>;
+  if (MODE == COLLIDE_STEP)
+    return launch_pdl(kern, grid, block, tma_smem<TGEN>(), h->stream, m[0], m[1], m[2], hin, hout, phi, dn, u,
+                      h->staging, p);
+  kern<<<grid, block, tma_smem<TGEN>(), h->stream>>>(m[0], m[1], m[2], hin, hout, phi, dn, u, h->staging, p);
+  return cudaGetLastError();
+}
+
+template <bool TGEN>
+cudaError_t launch_step(lbm_handle *h, int in, const KParams<float> &p, int variant) {
+  switch (variant) {
+    case 5: return launch_one<TGEN, COLLIDE_STEP, true, 4>(h, in, p);
+    case 6: return launch_one<TGEN, COLLIDE_STEP, true, 3>(h, in, p);
+    default: return launch_one<TGEN, COLLIDE_STEP, false, 3>(h, in, p);
+  }
+}
+
+}  // namespace
+
+bool collide2d_tma_eligible(const lbm_handle *h) {
+  return h->dims == 2 && h->P.precision == LBM_F32DEV && h->P.Lx % 4 == 0 && h->P.Lx >= TMA_MIN_SIDE &&
+         h->P.Ly >= TMA_MIN_SIDE && encode_fn() != nullptr;
+}
+
+cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant) {
+  if (!collide2d_tma_eligible(h)) return cudaErrorInvalidValue;
+  if (!prepare(h)) return cudaErrorInvalidValue;
+  const KParams<float> p = make_params<float>(h, force_on);
+  const bool tgen = p.cs2mT != 0.f;
+  if (mode == COLLIDE_STEP) return tgen ? launch_step<true>(h, in, p, variant) : launch_step<false>(h, in, p, variant);
+  return tgen ? launch_one<true, COLLIDE_MOMENTS, false, 3>(h, in, p)
+              : launch_one<false, COLLIDE_MOMENTS, false, 3>(h, in, p);
+}
+
+cudaError_t collide2d_tma_configure() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto fn, size_t smem) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  };
+  set(collide2d_tma_kernel<false, COLLIDE_STEP, false, 3>, tma_smem<false>());
+  set(collide2d_tma_kernel<false, COLLIDE_STEP, true, 4>, tma_smem<false>());
+  set(collide2d_tma_kernel<false, COLLIDE_STEP, true, 3>, tma_smem<false>());
+  set(collide2d_tma_kernel<true, COLLIDE_STEP, false, 3>, tma_smem<true>());
+  set(collide2d_tma_kernel<true, COLLIDE_STEP, true, 4>, tma_smem<true>());
+  set(collide2d_tma_kernel<true, COLLIDE_STEP, true, 3>, tma_smem<true>());
+  set(collide2d_tma_kernel<false, COLLIDE_MOMENTS, false, 3>, tma_smem<false>());
+  set(collide2d_tma_kernel<true, COLLIDE_MOMENTS, false, 3>, tma_smem<true>());
+  return e;
+}
+
+int collide2d_tma_error(bool reset) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_collide_tma_err, sizeof v) != cudaSuccess) return -1;
+  if (reset && v != 0) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_collide_tma_err, &zero, sizeof zero);
+  }
+  return v;
+}
+
+}  // namespace hlbm

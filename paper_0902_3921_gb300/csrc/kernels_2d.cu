@@ -1169,6 +1169,11 @@ cudaError_t collide2d_async_configure() {
 
 template <typename S, typename C>
 cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
+  if constexpr (std::is_same<S, C>::value && sizeof(C) == 4) {
+    // 3, 5, 6: TMA staging (scalar, packed-pair 4 CTAs/SM, packed-pair 3 CTAs/SM)
+    if (h->collide_rows == 3 || h->collide_rows == 5 || h->collide_rows == 6)
+      return collide2d_tma(h, in, force_on, mode, h->collide_rows);
+  }
   if constexpr (std::is_same<S, C>::value) {
     // 0: asynchronous staging sized for 4 CTAs per SM (FP64: 2), 1: for 3
     if (h->collide_rows == 0)
@@ -1310,7 +1315,10 @@ cudaError_t collide2d_configure(int precision) {
   if (e == cudaSuccess && precision != LBM_F64) e = fd2d_block_configure();
   if (e != cudaSuccess) return e;
   if (precision == LBM_F64) return collide2d_async_configure<double>();
-  if (precision == LBM_F32DEV) return collide2d_async_configure<float>();
+  if (precision == LBM_F32DEV) {
+    e = collide2d_async_configure<float>();
+    return e == cudaSuccess ? collide2d_tma_configure() : e;
+  }
   return cudaSuccess;
 }
 

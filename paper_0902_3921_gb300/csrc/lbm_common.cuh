@@ -157,6 +157,10 @@ struct lbm_handle {
   void *phi[3] = {nullptr, nullptr, nullptr};  // [2] = FD scratch between launches
   void *fd_a = nullptr, *fd_p = nullptr;        // 3D FP32 FD: phih and psi planes
   bool adopted = false;                        // h, phi, u belong to the caller
+  // TMA descriptors of the FP32 collide kernel (CUtensorMap, 128 bytes each):
+  // per buffer parity, populations in 32- and 36-column boxes and phi
+  alignas(64) unsigned char tma_maps[6 * 128] = {};
+  bool tma_ready = false;
   void *u = nullptr;
   void *dn = nullptr;
   double *staging = nullptr;   // (dims + 3) * S doubles
@@ -207,5 +211,13 @@ enum { COLLIDE_STEP = 0, COLLIDE_MOMENTS = 1 };
 
 template <typename C>
 KParams<C> make_params(const lbm_handle *h, int force_on);
+
+// collide with TMA staging (collide2d_tma.cu): FP32 deviations, Lx % 4 == 0,
+// Lx, Ly >= 64; variant 3: scalar collision, 5 / 6: packed pairs budgeted for
+// 4 / 3 CTAs per SM (step mode; the moments mode is always scalar)
+bool collide2d_tma_eligible(const lbm_handle *h);
+cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant);
+cudaError_t collide2d_tma_configure();
+int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
 
 }  // namespace hlbm

@@ -107,6 +107,14 @@ int cuda_fail(lbm_handle *h, cudaError_t e, const char *what) {
               std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// After a synchronisation: a bounded device wait of the TMA collide kernel
+// that gave up (its copies never completed) latches LBM_ETIMEOUT.
+int check_device_waits(lbm_handle *h) {
+  if (h->tma_ready && collide2d_tma_error(true) > 0)
+    return fail(h, LBM_ETIMEOUT, "collide kernel: a TMA copy did not complete within 0.5 s");
+  return LBM_OK;
+}
+
 #define CK(h, call, what)                              \
   do {                                                 \
     cudaError_t e_ = (call);                           \
@@ -328,7 +336,8 @@ int autotune_2d(lbm_handle *h) {
       block_ok |= v[4] == 128 && h->P.precision != LBM_F64 && v[0] == sh[0] && v[1] == sh[1] && v[2] == sh[2];
     if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
-        (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV))) {
+        (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV) ||
+         ((v[3] == 3 || v[3] == 5 || v[3] == 6) && collide2d_tma_eligible(h)))) {
       h->sub = std::min(v[0], h->m);
       h->fd_rows = v[1];
       h->fd_cols = h->P.precision == LBM_F64 ? 2 : v[2];
@@ -438,8 +447,11 @@ int autotune_2d(lbm_handle *h) {
   h->fd_rows = bestc.rows;
   best = 1e30f;
   int best_cr = 2;
-  for (int cr : {0, 1, 2, 4}) {
+  for (int cr : {0, 1, 2, 4, 3, 5, 6}) {
     if (cr < 2 && h->P.precision == LBM_F16DEV) continue;  // cp.async moves >= 4 bytes
+    if (cr >= 5 || cr == 3) {
+      if (!collide2d_tma_eligible(h)) continue;
+    }
     h->collide_rows = cr;
     const float ms =
         time_launches(h, e0, e1, [&] { return launch_collide(h, 0, 0, COLLIDE_STEP); });
@@ -673,6 +685,7 @@ int lbm_moments(lbm_handle *h, double *n, double *phi, double *ux, double *uy, d
       CK(h, cudaMemcpyAsync(dst[k], h->staging + k * h->S, bytes, cudaMemcpyDeviceToHost, h->stream),
          "device-to-host copy");
   CK(h, cudaStreamSynchronize(h->stream), "lbm_moments");
+  if (check_device_waits(h)) return h->err;
   return LBM_OK;
 }
 
@@ -701,6 +714,7 @@ int lbm_diagnostics(lbm_handle *h, lbm_diag *out) {
   CK(h, cudaMemcpyAsync(res, h->dres, sizeof res, cudaMemcpyDeviceToHost, h->stream),
      "device-to-host copy");
   CK(h, cudaStreamSynchronize(h->stream), "lbm_diagnostics");
+  if (check_device_waits(h)) return h->err;
   std::memset(out, 0, sizeof *out);
   out->t = h->t;
   out->sum_n = res[DIAG_SUM_N];
@@ -724,6 +738,7 @@ int lbm_synchronize(lbm_handle *h) {
   if (h == nullptr) return LBM_EINVAL;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) cuda_fail(h, e, "lbm_synchronize");
+  check_device_waits(h);
   return h->err;
 }
 

@@ -565,3 +565,71 @@ def test_launch_shapes_flux_variant(shape, monkeypatch):
     ref, lat = _run_both(op, lp, n, phi, u, 20)
     dphi, du, dn = _errors(ref, lat)
     assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (shape, dphi, du, dn)
+
+
+# TMA-staged collide kernel (FP32, Lx % 4 == 0, sides >= 64): 3 scalar
+# collision, 5 / 6 packed-pair collision budgeted for 4 / 3 CTAs per SM
+TMA_VARIANTS = [3, 5, 6]
+
+
+@pytest.mark.parametrize("variant", TMA_VARIANTS)
+@pytest.mark.parametrize("size", [(64, 64), (100, 68), (300, 217)])
+def test_tma_collide_against_oracle(variant, size, monkeypatch):
+    """Every tile of 64 x 64 is an edge tile (the copies' zero-filled cells are
+    all replaced by periodic images); 100 x 68 and 300 x 217 have ragged last
+    tiles in both directions."""
+    monkeypatch.setenv("HLBM_TUNING", f"4,80,2,{variant},128")
+    Lx, Ly = size
+    op, lp = _pair(Lx, Ly, m=4, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.drop(2, Lx, Ly, R=min(Lx, Ly) // 4, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, Lx, Ly)
+    u = u + 0.003 * np.sin(np.arange(Lx) / 4.0)[None, None, :] + 0.002 * np.cos(np.arange(Ly) / 3.0)[None, :, None]
+    ref, lat = _run_both(op, lp, n, phi, u, 12)
+    _fp32_bar(ref, lat, (variant, size))
+    assert lbm.lbm_tuning(lat.handle)["collide_sites_per_thread"] == variant
+
+
+@pytest.mark.parametrize("variant", TMA_VARIANTS)
+@pytest.mark.parametrize("extra", ["T", "force"])
+def test_tma_collide_T_and_body_force(variant, extra, monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", f"4,80,2,{variant},128")
+    kw = dict(CFG1)
+    if extra == "T":
+        kw["T"] = 0.28
+    else:
+        kw.update(g=(2e-5, -1e-5, 0.0), force_steps=6)
+    op, lp = _pair(96, 72, m=4, precision=lbm.LBM_F32DEV, **kw)
+    phi = I.drop(2, 96, 72, R=18, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 96, 72)
+    n = n + 0.001 * np.sin(np.arange(96) / 6.0)[None, :]
+    ref, lat = _run_both(op, lp, n, phi, u, 12)
+    _fp32_bar(ref, lat, (variant, extra))
+
+
+@pytest.mark.parametrize("variant", TMA_VARIANTS)
+def test_tma_collide_translation_equivariance_bitwise(variant, monkeypatch):
+    """Shifting the initial state by whole tiles (32 sites) moves interior
+    tiles onto the lattice's edges and back: the periodic images the edge
+    CTAs reload must reproduce exactly what the copies deliver inside."""
+    monkeypatch.setenv("HLBM_TUNING", f"4,80,2,{variant},128")
+    op, lp = _pair(128, 96, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.spinodal(2, 128, 96, seed=5)
+    n, u = I.rest(2, 128, 96)
+    res = []
+    for shift in ((0, 0), (32, 64)):
+        lat = lbm.Lattice(lp)
+        lat.init_fields(n, np.roll(phi, shift, axis=(0, 1)), u).step(60)
+        res.append(lat.moments())
+        lat.close()
+    for a, b in zip(res[0], res[1]):
+        axes = (0, 1) if a.ndim == 2 else (1, 2)
+        assert np.array_equal(np.roll(a, (32, 64), axis=axes), b)
+
+
+def test_tma_collide_refused_where_ineligible(monkeypatch):
+    """Lx % 4 != 0 (a copy's rows must start on 16-byte boundaries), a side
+    below 64, and FP64 storage are refused for the TMA kernel."""
+    for Lx, Ly, prec in ((66, 64, lbm.LBM_F32DEV), (64, 48, lbm.LBM_F32DEV), (64, 64, lbm.LBM_F64)):
+        monkeypatch.setenv("HLBM_TUNING", "4,16,2,3,0")
+        with pytest.raises(lbm.LbmError):
+            lbm.Lattice(lbm.LbmParams(Lx=Lx, Ly=Ly, precision=prec, **CFG1))
