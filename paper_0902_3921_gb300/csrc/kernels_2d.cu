@@ -874,15 +874,19 @@ __global__ void __launch_bounds__(256)
 // ---- FD convection-diffusion: block kernel, one 128-column region per CTA ----
 // FP32 only.  A CTA of NW warps owns a region 128 columns wide and RY =
 // K NW rows high, whose inner (128 - 2H) x (RY - 2H) sites are written
-// (H = 3 SUB).  Warp w owns rows w, w + NW, ...; lane l owns the four
-// columns 4l .. 4l + 3 of each, so every shared-memory access is one float4
-// per lane (row pitch 128 floats: a warp reads 512 contiguous bytes) and the
-// x neighbours come from the adjacent lanes by shuffles.  Columns 0 and 127
-// are never valid, so lanes 0 and 31 need no neighbour outside the warp.
+// (H = 3 SUB).  Warp w owns the K consecutive rows wK .. wK + K - 1; lane l
+// owns the four columns 4l .. 4l + 3 of each, so every shared-memory access
+// is one float4 per lane (row pitch 128 floats: a warp reads 512 contiguous
+// bytes) and the x neighbours come from the adjacent lanes by shuffles.
+// Columns 0 and 127 are never valid, so lanes 0 and 31 need no neighbour
+// outside the warp.  A phase walks the warp's rows top to bottom and passes
+// the stencil rows r - 1, r, r + 1 on in registers, so each input row is
+// read from shared memory once (shared-memory bandwidth bounds the kernel).
 // The advection coefficients of Eqs. 32-35 depend only on u*(t): they are
 // computed once per launch and kept in registers for all SUB substeps.
 // Shared memory: phi, phih and psi planes of RY x 128 floats; each substep
-// is three phases over a region that shrinks by one site per phase.
+// is three phases over a region that shrinks by one site per phase.  The
+// diffusion phases use packed FP32 pairs.
 constexpr int FDB_RX = 128;
 
 template <int SUB, int K, int NW>
@@ -926,7 +930,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
   //    coefficients are in registers)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int r = warp + NW * k;
+    const int r = warp * K + k;
     const long long row = (long long)wrapi(y0 + r, Ly) * Lx;
     float e[4], f[4], g[4];
 #pragma unroll
@@ -947,7 +951,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
   float T[K][NC][4];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int r = warp + NW * k;
+    const int r = warp * K + k;
     const int rm = r > 0 ? r - 1 : r, rp = r < RY - 1 ? r + 1 : r;  // row 0 / RY-1: never valid
     const float4 uc = ld4(sa, r, c), vc = ld4(sq, r, c), vm = ld4(sq, rm, c), vp = ld4(sq, rp, c);
     const float uL0 = __shfl_up_sync(FULL, uc.w, 1), uR3 = __shfl_down_sync(FULL, uc.x, 1);
@@ -971,15 +975,26 @@ __global__ void __launch_bounds__(NW * 32, 1)
     if constexpr (!FLUX) st4(st0, r, c, mk4(c0));
   }
   __syncthreads();
-  // 3. SUB substeps of Eqs. 32-36
-#pragma unroll 1
-  for (int s = 0; s < SUB; ++s) {
-    int lo = 3 * s + 1;  // phih = advected phi
+  // 3. SUB substeps of Eqs. 32-36.  sweep(in, lo, fn) runs one stencil phase
+  //    over this warp's K consecutive rows r (lo <= r < RY - lo, a
+  //    warp-uniform test): fn(k, r, row r - 1, row r, row r + 1 of plane
+  //    `in`), each row of `in` loaded once and passed on in registers
+  auto sweep = [&](const float *in, int lo, auto &&fn) {
+    const int rb = warp * K;
+    float4 up = ld4(in, rb > 0 ? rb - 1 : 0, c), cen = ld4(in, rb, c);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = warp + NW * k;
-      if (r < lo || r >= RY - lo) continue;  // warp-uniform
-      const float4 pc = ld4(sp, r, c), pu = ld4(sp, r - 1, c), pd = ld4(sp, r + 1, c);
+      const int r = rb + k;
+      const float4 dn = ld4(in, r < RY - 1 ? r + 1 : r, c);
+      if (r >= lo && r < RY - lo) fn(k, r, up, cen, dn);
+      up = cen;
+      cen = dn;
+    }
+  };
+#pragma unroll 1
+  for (int s = 0; s < SUB; ++s) {
+    // phih = advected phi (Eqs. 32-35)
+    sweep(sp, 3 * s + 1, [&](int k, int r, const float4 &pu, const float4 &pc, const float4 &pd) {
       float4 t0v = make_float4(0.f, 0.f, 0.f, 0.f);
       if constexpr (!FLUX) t0v = ld4(st0, r, c);
       const float l0 = __shfl_up_sync(FULL, pc.w, 1), r3 = __shfl_down_sync(FULL, pc.x, 1);
@@ -1004,49 +1019,42 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
       }
       st4(sa, r, c, mk4(e));
-    }
+    });
     __syncthreads();
-    lo = 3 * s + 2;  // psi = a phih + b phi^3 - kappa lap phih (Eq. 36)
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int r = warp + NW * k;
-      if (r < lo || r >= RY - lo) continue;
-      const float4 ac = ld4(sa, r, c), au = ld4(sa, r - 1, c), ad = ld4(sa, r + 1, c);
+    // psi = a phih + b phi^3 - kappa lap phih (Eq. 36)
+    sweep(sa, 3 * s + 2, [&](int, int r, const float4 &au, const float4 &ac, const float4 &ad) {
       const float4 pc = ld4(sp, r, c);
       const float l0 = __shfl_up_sync(FULL, ac.w, 1), r3 = __shfl_down_sync(FULL, ac.x, 1);
-      float e[4];
+      // packed pairs (sites 0,1) and (2,3): vertical and centre terms as
+      // pairs, the horizontal neighbour sums (which straddle pairs) scalar
+      float2 o[2];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float hk = comp(ac, j);
-        float lap = comp(au, j);
-        lap += j == 0 ? l0 : comp(ac, j - 1);
-        lap += -4.f * hk;
-        lap += j == 3 ? r3 : comp(ac, j + 1);
-        lap += comp(ad, j);
-        const float cb = cubic_half ? hk : comp(pc, j);
-        e[j] = a * hk + b * (cb * cb * cb) - kappa * lap;
+      for (int q = 0; q < 2; ++q) {
+        const float2 hk = q ? f2(ac.z, ac.w) : f2(ac.x, ac.y);
+        const float2 vs = add2(q ? f2(au.z, au.w) : f2(au.x, au.y), q ? f2(ad.z, ad.w) : f2(ad.x, ad.y));
+        const float2 hs = q ? f2(ac.y + ac.w, ac.z + r3) : f2(l0 + ac.y, ac.x + ac.z);
+        const float2 lap = fma2(f2(-4.f, -4.f), hk, add2(vs, hs));
+        const float2 cb = cubic_half ? hk : (q ? f2(pc.z, pc.w) : f2(pc.x, pc.y));
+        o[q] = fma2(f2(a, a), hk, fma2(f2(b, b), mul2(mul2(cb, cb), cb), mul2(f2(-kappa, -kappa), lap)));
       }
-      st4(sq, r, c, mk4(e));
-    }
+      st4(sq, r, c, make_float4(o[0].x, o[0].y, o[1].x, o[1].y));
+    });
     __syncthreads();
-    lo = 3 * s + 3;  // phi^{n+1} = phih + dt Gamma lap psi
+    // phi^{n+1} = phih + dt Gamma lap psi
     const bool last = s == SUB - 1;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int r = warp + NW * k;
-      if (r < lo || r >= RY - lo) continue;
-      const float4 qc = ld4(sq, r, c), qu = ld4(sq, r - 1, c), qd = ld4(sq, r + 1, c);
+    sweep(sq, 3 * s + 3, [&](int, int r, const float4 &qu, const float4 &qc, const float4 &qd) {
       const float4 ac = ld4(sa, r, c);
       const float l0 = __shfl_up_sync(FULL, qc.w, 1), r3 = __shfl_down_sync(FULL, qc.x, 1);
       float e[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float lap = comp(qu, j);
-        lap += j == 0 ? l0 : comp(qc, j - 1);
-        lap += -4.f * comp(qc, j);
-        lap += j == 3 ? r3 : comp(qc, j + 1);
-        lap += comp(qd, j);
-        e[j] = comp(ac, j) + dtG * lap;
+      for (int q = 0; q < 2; ++q) {
+        const float2 qk = q ? f2(qc.z, qc.w) : f2(qc.x, qc.y);
+        const float2 vs = add2(q ? f2(qu.z, qu.w) : f2(qu.x, qu.y), q ? f2(qd.z, qd.w) : f2(qd.x, qd.y));
+        const float2 hs = q ? f2(qc.y + qc.w, qc.z + r3) : f2(l0 + qc.y, qc.x + qc.z);
+        const float2 lap = fma2(f2(-4.f, -4.f), qk, add2(vs, hs));
+        const float2 o = fma2(f2(dtG, dtG), lap, q ? f2(ac.z, ac.w) : f2(ac.x, ac.y));
+        e[2 * q] = o.x;
+        e[2 * q + 1] = o.y;
       }
       if (!last) {
         st4(sp, r, c, mk4(e));
@@ -1058,7 +1066,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
           if (cc >= H && cc < H + TX && xg < Lx) phi_out[row + xg] = e[j];
         }
       }
-    }
+    });
     if (!last) __syncthreads();
   }
 }
