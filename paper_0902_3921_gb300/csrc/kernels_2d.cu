@@ -991,10 +991,14 @@ __global__ void __launch_bounds__(NW * 32, 1)
       cen = dn;
     }
   };
+  // phi^n and phi^{n+1} alternate between two planes (the psi of Eq. 36
+  // never reaches shared memory)
+  float *pin = sp, *pout = sq;
+  auto clampr = [](int r) { return r < 0 ? 0 : (r > RY - 1 ? RY - 1 : r); };
 #pragma unroll 1
   for (int s = 0; s < SUB; ++s) {
     // phih = advected phi (Eqs. 32-35)
-    sweep(sp, 3 * s + 1, [&](int k, int r, const float4 &pu, const float4 &pc, const float4 &pd) {
+    sweep(pin, 3 * s + 1, [&](int k, int r, const float4 &pu, const float4 &pc, const float4 &pd) {
       float4 t0v = make_float4(0.f, 0.f, 0.f, 0.f);
       if constexpr (!FLUX) t0v = ld4(st0, r, c);
       const float l0 = __shfl_up_sync(FULL, pc.w, 1), r3 = __shfl_down_sync(FULL, pc.x, 1);
@@ -1021,53 +1025,73 @@ __global__ void __launch_bounds__(NW * 32, 1)
       st4(sa, r, c, mk4(e));
     });
     __syncthreads();
-    // psi = a phih + b phi^3 - kappa lap phih (Eq. 36)
-    sweep(sa, 3 * s + 2, [&](int, int r, const float4 &au, const float4 &ac, const float4 &ad) {
-      const float4 pc = ld4(sp, r, c);
-      const float l0 = __shfl_up_sync(FULL, ac.w, 1), r3 = __shfl_down_sync(FULL, ac.x, 1);
-      // packed pairs (sites 0,1) and (2,3): vertical and centre terms as
-      // pairs, the horizontal neighbour sums (which straddle pairs) scalar
-      float2 o[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float2 hk = q ? f2(ac.z, ac.w) : f2(ac.x, ac.y);
-        const float2 vs = add2(q ? f2(au.z, au.w) : f2(au.x, au.y), q ? f2(ad.z, ad.w) : f2(ad.x, ad.y));
-        const float2 hs = q ? f2(ac.y + ac.w, ac.z + r3) : f2(l0 + ac.y, ac.x + ac.z);
-        const float2 lap = fma2(f2(-4.f, -4.f), hk, add2(vs, hs));
-        const float2 cb = cubic_half ? hk : (q ? f2(pc.z, pc.w) : f2(pc.x, pc.y));
-        o[q] = fma2(f2(a, a), hk, fma2(f2(b, b), mul2(mul2(cb, cb), cb), mul2(f2(-kappa, -kappa), lap)));
-      }
-      st4(sq, r, c, make_float4(o[0].x, o[0].y, o[1].x, o[1].y));
-    });
-    __syncthreads();
-    // phi^{n+1} = phih + dt Gamma lap psi
+    // psi = a phih + b phi^3 - kappa lap phih and phi^{n+1} = phih + dt Gamma
+    // lap psi (Eq. 36), fused: the warp computes psi on its rows and one row
+    // either side, keeps the last three psi rows in registers and writes
+    // phi^{n+1} of row r as soon as psi of row r + 1 is known
     const bool last = s == SUB - 1;
-    sweep(sq, 3 * s + 3, [&](int, int r, const float4 &qu, const float4 &qc, const float4 &qd) {
-      const float4 ac = ld4(sa, r, c);
-      const float l0 = __shfl_up_sync(FULL, qc.w, 1), r3 = __shfl_down_sync(FULL, qc.x, 1);
-      float e[4];
+    const int lo3 = 3 * s + 3, rb = warp * K;
+    if (rb + K > lo3 && rb < RY - lo3) {  // warp-uniform: some row of this warp is valid
+      float4 hu = ld4(sa, clampr(rb - 2), c), hc = ld4(sa, clampr(rb - 1), c);
+      float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float2 qk = q ? f2(qc.z, qc.w) : f2(qc.x, qc.y);
-        const float2 vs = add2(q ? f2(qu.z, qu.w) : f2(qu.x, qu.y), q ? f2(qd.z, qd.w) : f2(qd.x, qd.y));
-        const float2 hs = q ? f2(qc.y + qc.w, qc.z + r3) : f2(l0 + qc.y, qc.x + qc.z);
-        const float2 lap = fma2(f2(-4.f, -4.f), qk, add2(vs, hs));
-        const float2 o = fma2(f2(dtG, dtG), lap, q ? f2(ac.z, ac.w) : f2(ac.x, ac.y));
-        e[2 * q] = o.x;
-        e[2 * q + 1] = o.y;
-      }
-      if (!last) {
-        st4(sp, r, c, mk4(e));
-      } else if (r >= H && r < H + TY && y0 + r < Ly) {
-        const long long row = (long long)(y0 + r) * Lx;
+      for (int j = 0; j < K + 2; ++j) {
+        const int rr = rb - 1 + j;  // psi row computed now
+        const float4 hd = ld4(sa, clampr(rr + 1), c), pc = ld4(pin, clampr(rr), c);
+        float4 q2;
+        {
+          const float l0 = __shfl_up_sync(FULL, hc.w, 1), r3 = __shfl_down_sync(FULL, hc.x, 1);
+          // packed pairs (sites 0,1) and (2,3): vertical and centre terms as
+          // pairs, the horizontal neighbour sums (which straddle pairs) scalar
+          float2 o[2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int cc = c + j, xg = x0 + cc;
-          if (cc >= H && cc < H + TX && xg < Lx) phi_out[row + xg] = e[j];
+          for (int q = 0; q < 2; ++q) {
+            const float2 hk = q ? f2(hc.z, hc.w) : f2(hc.x, hc.y);
+            const float2 vs = add2(q ? f2(hu.z, hu.w) : f2(hu.x, hu.y), q ? f2(hd.z, hd.w) : f2(hd.x, hd.y));
+            const float2 hs = q ? f2(hc.y + hc.w, hc.z + r3) : f2(l0 + hc.y, hc.x + hc.z);
+            const float2 lap = fma2(f2(-4.f, -4.f), hk, add2(vs, hs));
+            const float2 cb = cubic_half ? hk : (q ? f2(pc.z, pc.w) : f2(pc.x, pc.y));
+            o[q] = fma2(f2(a, a), hk, fma2(f2(b, b), mul2(mul2(cb, cb), cb), mul2(f2(-kappa, -kappa), lap)));
+          }
+          q2 = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         }
+        const int r = rr - 1;  // phi^{n+1} row: psi rows r - 1, r, r + 1 = q0, q1, q2; phih row r = hu
+        if (j >= 2 && r >= lo3 && r < RY - lo3) {
+          const float l0 = __shfl_up_sync(FULL, q1.w, 1), r3 = __shfl_down_sync(FULL, q1.x, 1);
+          float e[4];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float2 qk = q ? f2(q1.z, q1.w) : f2(q1.x, q1.y);
+            const float2 vs = add2(q ? f2(q0.z, q0.w) : f2(q0.x, q0.y), q ? f2(q2.z, q2.w) : f2(q2.x, q2.y));
+            const float2 hs = q ? f2(q1.y + q1.w, q1.z + r3) : f2(l0 + q1.y, q1.x + q1.z);
+            const float2 lap = fma2(f2(-4.f, -4.f), qk, add2(vs, hs));
+            const float2 o = fma2(f2(dtG, dtG), lap, q ? f2(hu.z, hu.w) : f2(hu.x, hu.y));
+            e[2 * q] = o.x;
+            e[2 * q + 1] = o.y;
+          }
+          if (!last) {
+            st4(pout, r, c, mk4(e));
+          } else if (r >= H && r < H + TY && y0 + r < Ly) {
+            const long long row = (long long)(y0 + r) * Lx;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int cc = c + jj, xg = x0 + cc;
+              if (cc >= H && cc < H + TX && xg < Lx) phi_out[row + xg] = e[jj];
+            }
+          }
+        }
+        q0 = q1;
+        q1 = q2;
+        hu = hc;
+        hc = hd;
       }
-    });
-    if (!last) __syncthreads();
+    }
+    if (!last) {
+      __syncthreads();
+      float *t = pin;
+      pin = pout;
+      pout = t;
+    }
   }
 }
 
