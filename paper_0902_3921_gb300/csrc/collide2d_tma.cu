@@ -20,10 +20,12 @@
 // PACK evaluates the collision of a thread's two rows at a time with packed
 // FP32 pair instructions (add/mul/fma .f32x2); MINB is the number of CTAs
 // per SM the registers are budgeted for.  Variants (the collide_rows value of
-// the handle's launch shapes): 3 scalar (3 CTAs/SM), 5 packed (4), 6 packed (3).
+// the handle's launch shapes): 3 scalar (3 CTAs/SM), 5 packed (4), 6 packed (3),
+// 7 persistent and pipelined (below; packed, 4 CTAs/SM).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "lbm_common.cuh"
@@ -424,6 +426,313 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
+// ---- persistent, pipelined variant ------------------------------------------------
+// The same arithmetic on 32 x 16 tiles, but each CTA stays resident and takes
+// tiles from a per-handle counter (atomicAdd), with two shared-memory stages:
+// while one tile is computed, the ten copies of the next are in flight.  The
+// last CTA to finish resets the counter for the next launch.  A thread owns
+// one column and two rows, whose collisions it evaluates as packed pairs.
+constexpr int PY = 16;            // tile rows
+constexpr int PPHH = PY + 4;      // phi box rows
+constexpr int PMUH = PY + 2;      // mu rows
+__host__ __device__ constexpr int pplane_off(int i) { return PY * (TT * i + 4 * nshift(i)); }
+constexpr int PPOP_FLOATS = pplane_off(9);
+constexpr int PSTAGE = 4 * (PPOP_FLOATS + PHW * PPHH);  // bytes of one stage (= its copies)
+constexpr int P_OFF_STAGE = 128;                        // [0, 128): two mbarriers, two tile slots
+constexpr int P_OFF_MU = P_OFF_STAGE + 2 * PSTAGE;
+constexpr int P_OFF_PN = P_OFF_MU + 4 * MUW * PMUH;
+static_assert(PSTAGE % 128 == 0 && (4 * PPOP_FLOATS) % 128 == 0 && (4 * pplane_off(1)) % 128 == 0 &&
+                  (4 * pplane_off(2)) % 128 == 0,
+              "TMA destinations must be 128-byte aligned");
+template <bool TGEN>
+constexpr size_t pipe_smem() {
+  return 128 + P_OFF_PN + (TGEN ? 4 * MUW * PMUH : 0);
+}
+
+template <bool TGEN, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    collide2d_tma_pipe_kernel(const __grid_constant__ CUtensorMap map_p32,
+                              const __grid_constant__ CUtensorMap map_p36,
+                              const __grid_constant__ CUtensorMap map_phi, const float *__restrict__ hin,
+                              float *__restrict__ hout, const float *__restrict__ phi,
+                              const float *__restrict__ dn, float *__restrict__ uout,
+                              unsigned *__restrict__ sched, KParams<float> p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *base = smem_raw + ((128u - (su32(smem_raw) & 127u)) & 127u);
+  const uint32_t bar0 = su32(base);
+  volatile int *stile = reinterpret_cast<volatile int *>(base + 16);  // tile of stage 0 / 1
+  float(*smu)[MUW] = reinterpret_cast<float(*)[MUW]>(base + P_OFF_MU);
+  float(*spn)[MUW] = reinterpret_cast<float(*)[MUW]>(base + P_OFF_PN);
+  const int Lx = p.Lx, Ly = p.Ly;
+  const long long Sz = (long long)Lx * Ly;
+  const int ntx = (Lx + TT - 1) / TT, ntiles = ntx * ((Ly + PY - 1) / PY);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ly0 = 2 * ty;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();  // phi(t), the populations and the reset counter come from earlier kernels
+  pdl_trigger();
+  // thread 0: the ten copies of `tile` into stage st, completing on its mbarrier
+  auto issue = [&](int tile, int st) {
+    const int x0 = (tile % ntx) * TT, y0 = (tile / ntx) * PY;
+    unsigned char *sb = base + P_OFF_STAGE + st * PSTAGE;
+    const uint32_t bar = bar0 + 8 * st;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic accesses first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)PSTAGE)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      tma_3d(su32(sb + 4 * pplane_off(i)), plane_w(i) == TT ? &map_p32 : &map_p36, x0 + box_dx(i), y0 - q9_ey(i),
+             i, bar);
+    tma_2d(su32(sb + 4 * PPOP_FLOATS), &map_phi, x0 - 4, y0 - 2, bar);
+  };
+  if (tid == 0) {
+    const int t0 = (int)atomicAdd(sched, 1u);
+    stile[0] = t0;
+    if (t0 < ntiles) issue(t0, 0);
+  }
+  __syncthreads();
+  const float om = p.tau_inv, keep = 1.f - p.tau_inv;
+  const float A0 = om * float(q9_w(0)), B0 = p.pref * float(q9_w(0));
+  const float A1 = om * float(q9_w(1)), B1 = p.pref * float(q9_w(1));
+  const float A2 = om * float(q9_w(5)), B2 = p.pref * float(q9_w(5));
+  int k = 0;
+  bool failed = false;
+  while (true) {
+    const int st = k & 1;
+    const int tile = stile[st];
+    if (tile >= ntiles) break;
+    // claim the next tile and start its copies into the other stage (free
+    // since the end of the previous iteration)
+    if (tid == 0) {
+      const int tn = (int)atomicAdd(sched, 1u);
+      stile[st ^ 1] = tn;
+      if (tn < ntiles) issue(tn, st ^ 1);
+    }
+    const int x0 = (tile % ntx) * TT, y0 = (tile / ntx) * PY, x = x0 + tx;
+    float *pops = reinterpret_cast<float *>(base + P_OFF_STAGE + st * PSTAGE);
+    float(*sphi)[PHW] = reinterpret_cast<float(*)[PHW]>(pops + PPOP_FLOATS);
+    if constexpr (TGEN) {
+      for (int q = tid; q < MUW * PMUH; q += 256) {
+        const int ry = q / MUW, rx = q - ry * MUW;
+        const int gx = wrapi(x0 + rx - 1, Lx), gy = wrapi(y0 + ry - 1, Ly);
+        spn[ry][rx] = p.cs2mT * (1.f + dn[(long long)gy * Lx + gx]);
+      }
+    }
+    const bool arrived = bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, 500000000ull);
+    if (!__syncthreads_and(arrived)) {
+      failed = true;
+      break;
+    }
+    // periodic images of the cells the copies left as zeros (edge tiles)
+    if (x0 == 0 || y0 == 0 || x0 + TT + 2 > Lx || y0 + PY + 2 > Ly) {
+      for (int q = tid; q < (TT + 4) * PPHH; q += 256) {
+        const int ry = q / (TT + 4), rx = q - ry * (TT + 4);
+        const int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+        if (gx < 0 || gx >= Lx || gy < 0 || gy >= Ly)
+          sphi[ry][rx + 2] = phi[(long long)wrapi(gy, Ly) * Lx + wrapi(gx, Lx)];
+      }
+      for (int q = tid; q < 8 * (PY + TT); q += 256) {
+        const int i = 1 + q / (PY + TT), j = q % (PY + TT);
+        const int ex = q9_ex(i), ey = q9_ey(i);
+        int xs, ys;
+        if (j < PY) {
+          if (ex == 0) continue;
+          xs = ex > 0 ? 0 : Lx - 1;
+          ys = y0 + j;
+        } else {
+          if (ey == 0) continue;
+          ys = ey > 0 ? 0 : Ly - 1;
+          xs = x0 + j - PY;
+        }
+        if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + PY || ys >= Ly) continue;
+        const int sx = wrapi(xs - ex, Lx), sy = wrapi(ys - ey, Ly);
+        pops[pplane_off(i) + (ys - y0) * plane_w(i) + (xs - x0) + col_off(i)] =
+            hin[i * Sz + (long long)sy * Lx + sx];
+      }
+    }
+    __syncthreads();
+    // mu on the tile + 1: this thread's two rows, then the frame
+    {
+      // site row ly is phi row ly + 2 and mu row ly + 1
+      float w[3][3];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) w[a + 1][j] = sphi[ly0 + 1 + a][tx + 3 + j];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          w[0][j] = w[1][j];
+          w[1][j] = w[2][j];
+          w[2][j] = sphi[ly0 + 3 + r][tx + 3 + j];
+        }
+        smu[ly0 + 1 + r][tx + 1] = mu_at(p, w);
+      }
+      if (tid < 2 * MUW + 2 * PY) {
+        int my, mx;
+        if (tid < MUW) {
+          my = 0;
+          mx = tid;
+        } else if (tid < 2 * MUW) {
+          my = PMUH - 1;
+          mx = tid - MUW;
+        } else {
+          const int q = tid - 2 * MUW;
+          my = 1 + (q >> 1);
+          mx = (q & 1) ? MUW - 1 : 0;
+        }
+        float v[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2) v[a][b2] = sphi[my + a][mx + b2 + 2];
+        smu[my][mx] = mu_at(p, v);
+      }
+    }
+    __syncthreads();
+    // force (Eqs. 28, 30) of the two rows, then the packed collision
+    float2 Fx, Fy;
+    {
+      float m[4][3];  // mu rows ly0 .. ly0 + 3 (tile + 1 coordinates), columns tx .. tx + 2
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) m[a][j] = smu[ly0 + a][tx + j];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float gmx = -p.M * m[r][0];
+        gmx += p.M * m[r][2];
+        gmx += -p.N * m[r + 1][0];
+        gmx += p.N * m[r + 1][2];
+        gmx += -p.M * m[r + 2][0];
+        gmx += p.M * m[r + 2][2];
+        float gmy = -p.M * m[r][0];
+        gmy += -p.N * m[r][1];
+        gmy += -p.M * m[r][2];
+        gmy += p.M * m[r + 2][0];
+        gmy += p.N * m[r + 2][1];
+        gmy += p.M * m[r + 2][2];
+        const float ph = sphi[ly0 + r + 2][tx + 4];
+        float fx = -ph * gmx, fy = -ph * gmy;
+        if constexpr (TGEN) {
+          const int mx = tx + 1, my = ly0 + r + 1;
+          float px = -p.M * spn[my - 1][mx - 1];
+          px += p.M * spn[my - 1][mx + 1];
+          px += -p.N * spn[my][mx - 1];
+          px += p.N * spn[my][mx + 1];
+          px += -p.M * spn[my + 1][mx - 1];
+          px += p.M * spn[my + 1][mx + 1];
+          float py = -p.M * spn[my - 1][mx - 1];
+          py += -p.N * spn[my - 1][mx];
+          py += -p.M * spn[my - 1][mx + 1];
+          py += p.M * spn[my + 1][mx - 1];
+          py += p.N * spn[my + 1][mx];
+          py += p.M * spn[my + 1][mx + 1];
+          fx += px;
+          fy += py;
+        }
+        if (r == 0) {
+          Fx.x = fx;
+          Fy.x = fy;
+        } else {
+          Fx.y = fx;
+          Fy.y = fy;
+        }
+      }
+    }
+    const int ya = y0 + ly0;
+    if (x < Lx && ya < Ly) {
+      const bool row_b = ya + 1 < Ly;
+      auto pop = [&](int i, int ly) { return pops[pplane_off(i) + ly * plane_w(i) + tx + col_off(i)]; };
+      float2 h[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = make_float2(pop(i, ly0), pop(i, ly0 + 1));
+      float2 dens = h[0];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) dens = add2(dens, h[i]);
+      const float2 jx = add2(add2(sub2(h[1], h[3]), sub2(h[5], h[7])), sub2(h[8], h[6]));
+      const float2 jy = add2(add2(sub2(h[2], h[4]), sub2(h[5], h[7])), sub2(h[6], h[8]));
+      const float2 n = add2(s2(1.f), dens);
+      Fx = fma2(n, s2(p.gx), Fx);
+      Fy = fma2(n, s2(p.gy), Fy);
+      const float2 inv_n = make_float2(1.f / n.x, 1.f / n.y);
+      const float2 ux = mul2(fma2(s2(0.5f), Fx, jx), inv_n);
+      const float2 uy = mul2(fma2(s2(0.5f), Fy, jy), inv_n);
+      const float2 usq = fma2(ux, ux, mul2(uy, uy));
+      const float2 uF = fma2(ux, Fx, mul2(uy, Fy));
+      const float2 base2 = fma2(n, mul2(usq, s2(-1.5f)), dens);
+      const float2 n45 = mul2(n, s2(4.5f)), m3uF = mul2(uF, s2(-3.f));
+      const float2 An3_1 = mul2(n, s2(3.f * A1)), An3_2 = mul2(n, s2(3.f * A2));
+      float2 o[9];
+      o[0] = fma2(s2(keep), h[0], fma2(s2(A0), base2, mul2(s2(-3.f * B0), uF)));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = q < 2 ? q + 1 : q + 3, ib = i + 2;
+        const float A = q < 2 ? A1 : A2, B = q < 2 ? B1 : B2;
+        const float2 An3 = q < 2 ? An3_1 : An3_2;
+        float2 eu, eF;
+        if (q == 0) {
+          eu = ux;
+          eF = Fx;
+        } else if (q == 1) {
+          eu = uy;
+          eF = Fy;
+        } else if (q == 2) {
+          eu = add2(ux, uy);
+          eF = add2(Fx, Fy);
+        } else {
+          eu = sub2(uy, ux);
+          eF = sub2(Fy, Fx);
+        }
+        const float2 se = fma2(mul2(n45, eu), eu, base2);
+        const float2 fe = fma2(mul2(eu, s2(9.f)), eF, m3uF);
+        const float2 E = fma2(s2(A), se, mul2(s2(B), fe));
+        const float2 O = fma2(eu, An3, mul2(s2(3.f * B), eF));
+        o[i] = add2(fma2(s2(keep), h[i], E), O);
+        o[ib] = sub2(fma2(s2(keep), h[ib], E), O);
+      }
+      const long long sa = (long long)ya * Lx + x;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) hout[i * Sz + sa] = o[i].x;
+      uout[sa] = ux.x;
+      uout[Sz + sa] = uy.x;
+      if (row_b) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hout[i * Sz + sa + Lx] = o[i].y;
+        uout[sa + Lx] = ux.y;
+        uout[Sz + sa + Lx] = uy.y;
+      }
+    }
+    __syncthreads();  // stage st, smu and spn are free again; the next tile's slot is visible
+    ++k;
+  }
+  if (tid == 0) {
+    if (failed) {
+      // a copy did not complete within 0.5 s: report it and let the copies
+      // still in flight land before the CTA's shared memory is released
+      atomicExch(&g_collide_tma_err, 1);
+      const int st = k & 1;
+      bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, 500000000ull);
+      if (stile[st ^ 1] < ntiles) bar_wait(bar0 + 8 * (st ^ 1), (uint32_t)((k + 1) >> 1) & 1u, 500000000ull);
+    }
+    // every CTA has made its last claim before it counts itself out; the last
+    // one resets the counter for the next launch
+    __threadfence();
+    if (atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+      atomicExch(sched, 0u);
+      atomicExch(sched + 1, 0u);
+      __threadfence();
+    }
+  }
+}
+
 // ---- host side -------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -450,7 +759,8 @@ bool encode(CUtensorMap *map, void *ptr, int rank, const cuuint64_t *dims, const
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// maps per buffer parity b: [b][0] populations 32 wide, [b][1] populations 36 wide, [b][2] phi
+// maps per buffer parity b, [6 b + j]: 32 x 32 tiles: j = 0 populations 32 wide, 1 populations
+// 36 wide, 2 phi 40 x 36; 32 x 16 tiles (pipelined kernel): 3, 4 populations, 5 phi 40 x 20
 CUtensorMap *maps_of(lbm_handle *h) { return reinterpret_cast<CUtensorMap *>(h->tma_maps); }
 
 bool prepare(lbm_handle *h) {
@@ -460,10 +770,13 @@ bool prepare(lbm_handle *h) {
   const cuuint64_t pd[3] = {Lx, Ly, 9}, ps[2] = {4 * Lx, 4 * Lx * Ly};
   const cuuint64_t fd[2] = {Lx, Ly}, fs[1] = {4 * Lx};
   const cuuint32_t b32[3] = {TT, TT, 1}, b36[3] = {TT + 4, TT, 1}, bphi[2] = {PHW, PHH};
+  const cuuint32_t q32[3] = {TT, PY, 1}, q36[3] = {TT + 4, PY, 1}, qphi[2] = {PHW, PPHH};
   CUtensorMap *m = maps_of(h);
   for (int b = 0; b < 2; ++b) {
-    if (!encode(&m[3 * b + 0], h->h[b], 3, pd, ps, b32) || !encode(&m[3 * b + 1], h->h[b], 3, pd, ps, b36) ||
-        !encode(&m[3 * b + 2], h->phi[b], 2, fd, fs, bphi))
+    CUtensorMap *mb = m + 6 * b;
+    if (!encode(&mb[0], h->h[b], 3, pd, ps, b32) || !encode(&mb[1], h->h[b], 3, pd, ps, b36) ||
+        !encode(&mb[2], h->phi[b], 2, fd, fs, bphi) || !encode(&mb[3], h->h[b], 3, pd, ps, q32) ||
+        !encode(&mb[4], h->h[b], 3, pd, ps, q36) || !encode(&mb[5], h->phi[b], 2, fd, fs, qphi))
       return false;
   }
   h->tma_ready = true;
@@ -472,7 +785,7 @@ bool prepare(lbm_handle *h) {
 
 template <bool TGEN, int MODE, bool PACK, int MINB>
 cudaError_t launch_one(lbm_handle *h, int in, const KParams<float> &p) {
-  const CUtensorMap *m = maps_of(h) + 3 * in;
+  const CUtensorMap *m = maps_of(h) + 6 * in;
   dim3 grid((p.Lx + TT - 1) / TT, (p.Ly + TT - 1) / TT), block(32, 256 / 32);
   const float *hin = static_cast<const float *>(h->h[in]);
   float *hout = static_cast<float *>(h->h[1 - in]);
@@ -487,9 +800,35 @@ cudaError_t launch_one(lbm_handle *h, int in, const KParams<float> &p) {
   return cudaGetLastError();
 }
 
+// resident CTAs of a pipelined kernel on this device (queried once per kernel)
+template <bool TGEN, int MINB>
+int pipe_grid() {
+  static const int g = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, collide2d_tma_pipe_kernel<TGEN, MINB>, 256,
+                                                  pipe_smem<TGEN>());
+    return std::max(1, sms * std::max(per, 1));
+  }();
+  return g;
+}
+
+template <bool TGEN, int MINB>
+cudaError_t launch_pipe(lbm_handle *h, int in, const KParams<float> &p) {
+  const CUtensorMap *m = maps_of(h) + 6 * in + 3;
+  const int ntiles = ((p.Lx + TT - 1) / TT) * ((p.Ly + PY - 1) / PY);
+  const int grid = std::min(ntiles, pipe_grid<TGEN, MINB>());
+  return launch_pdl(collide2d_tma_pipe_kernel<TGEN, MINB>, dim3(grid), dim3(32, 256 / 32), pipe_smem<TGEN>(),
+                    h->stream, m[0], m[1], m[2], static_cast<const float *>(h->h[in]),
+                    static_cast<float *>(h->h[1 - in]), static_cast<const float *>(h->phi[in]),
+                    static_cast<const float *>(h->dn), static_cast<float *>(h->u), h->sched, p);
+}
+
 template <bool TGEN>
 cudaError_t launch_step(lbm_handle *h, int in, const KParams<float> &p, int variant) {
   switch (variant) {
+    case 7: return launch_pipe<TGEN, 4>(h, in, p);
     case 5: return launch_one<TGEN, COLLIDE_STEP, true, 4>(h, in, p);
     case 6: return launch_one<TGEN, COLLIDE_STEP, true, 3>(h, in, p);
     default: return launch_one<TGEN, COLLIDE_STEP, false, 3>(h, in, p);
@@ -500,7 +839,7 @@ cudaError_t launch_step(lbm_handle *h, int in, const KParams<float> &p, int vari
 
 bool collide2d_tma_eligible(const lbm_handle *h) {
   return h->dims == 2 && h->P.precision == LBM_F32DEV && h->P.Lx % 4 == 0 && h->P.Lx >= TMA_MIN_SIDE &&
-         h->P.Ly >= TMA_MIN_SIDE && encode_fn() != nullptr;
+         h->P.Ly >= TMA_MIN_SIDE && h->sched != nullptr && encode_fn() != nullptr;
 }
 
 cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant) {
@@ -524,6 +863,8 @@ cudaError_t collide2d_tma_configure() {
   set(collide2d_tma_kernel<true, COLLIDE_STEP, false, 3>, tma_smem<true>());
   set(collide2d_tma_kernel<true, COLLIDE_STEP, true, 4>, tma_smem<true>());
   set(collide2d_tma_kernel<true, COLLIDE_STEP, true, 3>, tma_smem<true>());
+  set(collide2d_tma_pipe_kernel<false, 4>, pipe_smem<false>());
+  set(collide2d_tma_pipe_kernel<true, 4>, pipe_smem<true>());
   set(collide2d_tma_kernel<false, COLLIDE_MOMENTS, false, 3>, tma_smem<false>());
   set(collide2d_tma_kernel<true, COLLIDE_MOMENTS, false, 3>, tma_smem<true>());
   return e;

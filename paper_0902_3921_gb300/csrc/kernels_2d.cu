@@ -1202,8 +1202,9 @@ cudaError_t collide2d_async_configure() {
 template <typename S, typename C>
 cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
   if constexpr (std::is_same<S, C>::value && sizeof(C) == 4) {
-    // 3, 5, 6: TMA staging (scalar, packed-pair 4 CTAs/SM, packed-pair 3 CTAs/SM)
-    if (h->collide_rows == 3 || h->collide_rows == 5 || h->collide_rows == 6)
+    // 3, 5, 6, 7: TMA staging (scalar, packed-pair 4 CTAs/SM, packed-pair 3
+    // CTAs/SM, persistent pipelined)
+    if (h->collide_rows == 3 || (h->collide_rows >= 5 && h->collide_rows <= 7))
       return collide2d_tma(h, in, force_on, mode, h->collide_rows);
   }
   if constexpr (std::is_same<S, C>::value) {

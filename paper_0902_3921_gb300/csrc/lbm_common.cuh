@@ -157,10 +157,12 @@ struct lbm_handle {
   void *phi[3] = {nullptr, nullptr, nullptr};  // [2] = FD scratch between launches
   void *fd_a = nullptr, *fd_p = nullptr;        // 3D FP32 FD: phih and psi planes
   bool adopted = false;                        // h, phi, u belong to the caller
-  // TMA descriptors of the FP32 collide kernel (CUtensorMap, 128 bytes each):
-  // per buffer parity, populations in 32- and 36-column boxes and phi
-  alignas(64) unsigned char tma_maps[6 * 128] = {};
+  // TMA descriptors of the FP32 collide kernels (CUtensorMap, 128 bytes each):
+  // per buffer parity, populations in 32- and 36-column boxes and phi, for
+  // 32 x 32 and 32 x 16 tiles
+  alignas(64) unsigned char tma_maps[12 * 128] = {};
   bool tma_ready = false;
+  unsigned *sched = nullptr;  // tile counter and finished-CTA count of the pipelined collide (2D FP32)
   void *u = nullptr;
   void *dn = nullptr;
   double *staging = nullptr;   // (dims + 3) * S doubles
@@ -214,7 +216,8 @@ KParams<C> make_params(const lbm_handle *h, int force_on);
 
 // collide with TMA staging (collide2d_tma.cu): FP32 deviations, Lx % 4 == 0,
 // Lx, Ly >= 64; variant 3: scalar collision, 5 / 6: packed pairs budgeted for
-// 4 / 3 CTAs per SM (step mode; the moments mode is always scalar)
+// 4 / 3 CTAs per SM, 7: persistent and pipelined (step mode; the moments mode
+// is always the scalar kernel)
 bool collide2d_tma_eligible(const lbm_handle *h);
 cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant);
 cudaError_t collide2d_tma_configure();

@@ -337,7 +337,7 @@ int autotune_2d(lbm_handle *h) {
     if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
         (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV) ||
-         ((v[3] == 3 || v[3] == 5 || v[3] == 6) && collide2d_tma_eligible(h)))) {
+         ((v[3] == 3 || (v[3] >= 5 && v[3] <= 7)) && collide2d_tma_eligible(h)))) {
       h->sub = std::min(v[0], h->m);
       h->fd_rows = v[1];
       h->fd_cols = h->P.precision == LBM_F64 ? 2 : v[2];
@@ -447,7 +447,7 @@ int autotune_2d(lbm_handle *h) {
   h->fd_rows = bestc.rows;
   best = 1e30f;
   int best_cr = 2;
-  for (int cr : {0, 1, 2, 4, 3, 5, 6}) {
+  for (int cr : {0, 1, 2, 4, 3, 5, 6, 7}) {
     if (cr < 2 && h->P.precision == LBM_F16DEV) continue;  // cp.async moves >= 4 bytes
     if (cr >= 5 || cr == 3) {
       if (!collide2d_tma_eligible(h)) continue;
@@ -608,7 +608,8 @@ static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_bu
                 {(void **)&h->dres, sizeof(double) * DIAG_COUNT},
                 {&h->dn, P.T != 1.0 / 3.0 ? cb * (size_t)h->S : 0},
                 {&h->fd_a, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0},
-                {&h->fd_p, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0}};
+                {&h->fd_p, h->dims == 3 && P.precision != LBM_F64 ? h->phibytes : 0},
+                {(void **)&h->sched, h->dims == 2 && P.precision == LBM_F32DEV ? 2 * sizeof(unsigned) : 0}};
   if (adopt) {
     h->adopted = true;
     h->h[0] = adopt->populations[0];
@@ -622,6 +623,10 @@ static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_bu
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc"));
   }
   cudaError_t e = cudaSuccess;
+  if (h->sched) {
+    e = cudaMemsetAsync(h->sched, 0, 2 * sizeof(unsigned), h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMemset"));
+  }
   if (h->dims == 3) {
     // opt in to the largest FD tile any handle may launch (the attribute is
     // per kernel, shared by all handles of the process)
@@ -844,7 +849,7 @@ void lbm_free(lbm_handle *h) {
     cudaEventDestroy(ev.b);
   }
   for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
-  void *owned[] = {h->dn, h->staging, h->partials, h->dres, h->fd_a, h->fd_p};
+  void *owned[] = {h->dn, h->staging, h->partials, h->dres, h->fd_a, h->fd_p, h->sched};
   void *lent[] = {h->h[0], h->h[1], h->phi[0], h->phi[1], h->phi[2], h->u};
   for (void *p : owned)
     if (p) cudaFree(p);

@@ -568,8 +568,9 @@ def test_launch_shapes_flux_variant(shape, monkeypatch):
 
 
 # TMA-staged collide kernel (FP32, Lx % 4 == 0, sides >= 64): 3 scalar
-# collision, 5 / 6 packed-pair collision budgeted for 4 / 3 CTAs per SM
-TMA_VARIANTS = [3, 5, 6]
+# collision, 5 / 6 packed-pair collision budgeted for 4 / 3 CTAs per SM,
+# 7 persistent and pipelined (32 x 16 tiles from a counter, two stages)
+TMA_VARIANTS = [3, 5, 6, 7]
 
 
 @pytest.mark.parametrize("variant", TMA_VARIANTS)
