@@ -47,10 +47,13 @@ FD_FLOPS_PER_SITE_SUBSTEP = 41
 # FP32 pipe peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the 1024^2 workload (profiles/collide2d_fd2d_spinodal1024.md),
-# valid for the kernel shapes captured there: the FD block kernel with 4
-# substeps, 96-row regions and 16 warps, and the collide kernel's 3-CTA variant
-NCU_TRAFFIC_1024 = {"fd": ((128, 96, 4, 2), 12.627456e6), "collide": (1, 41.967872e6 + 2.707712e6)}
+# ncu --set full capture of the 1024^2 workload
+# (profiles/collide2d_fd2d_spinodal1024.md), valid for the kernels captured
+# there: the FD block kernel with 4 substeps, 96-row regions and 16 warps
+# (consecutive rows per warp, psi fused), and the TMA collide kernel with the
+# packed-pair collision (launch-shape variant 5).  ncu flushes the caches
+# before a captured launch: these are cold-cache figures.
+NCU_TRAFFIC_1024 = {"fd": ((128, 96, 4, 2), 12.619776e6), "collide": (5, 41.970176e6 + 2.991872e6)}
 METRIC = "MLUPS (D2Q9 hybrid LB + FD step)"
 WORKLOAD = "spinodal-1024x1024-d2q9-f32dev"
 
