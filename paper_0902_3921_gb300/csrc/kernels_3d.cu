@@ -558,6 +558,141 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---- psi and the new phi in one z-marching kernel (Lx = 128 V, V = 1 or 2) ------
+// The second and third passes of a substep fused: a CTA of F3F_NW warps owns
+// F3F_NW - 2 output rows; warp w computes psi = a phih + b phi^3 - kappa
+// lap phih (Eq. 36) on row y0 - 1 + w, the whole row (V float4 per lane,
+// quad q of lane l at x = 128 q + 4 l, so the periodic x neighbours come from
+// shuffles), and marches in z with phih of planes z, z + 1, z + 2 in
+// registers.  psi goes to a four-plane shared-memory ring; after one barrier
+// the inner warps form phi^{n+1} = phih + dt Gamma lap psi (Eq. 36) of plane
+// z from the ring.  psi never reaches global memory: a substep moves the
+// advection pass's 20 B/site plus about 12 B/site here, instead of 44 B.
+constexpr int F3F_NW = 16;
+
+template <int V>
+__device__ __forceinline__ void xnbr_row(const float4 (&c)[V], float (&l)[V], float (&r)[V]) {
+  const int lane = threadIdx.x & 31;
+  float sl[V], sr[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    sl[q] = __shfl_sync(0xffffffffu, c[q].w, (lane + 31) & 31);
+    sr[q] = __shfl_sync(0xffffffffu, c[q].x, (lane + 1) & 31);
+  }
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    l[q] = lane == 0 ? sl[(q + V - 1) % V] : sl[q];
+    r[q] = lane == 31 ? sr[(q + 1) % V] : sr[q];
+  }
+}
+
+// The loads of iteration z + 1 (phih of plane z + 3, phih of plane z + 2 on
+// the rows y -+ 1 and phi of plane z + 2) are issued before iteration z
+// computes, so that they are in flight across its barrier (1.16x over
+// loading them at the top of their own iteration).
+template <int V, int MINB>
+__global__ void __launch_bounds__(F3F_NW * 32, MINB)
+    fd3f_kernel(const float *__restrict__ A, const float *__restrict__ G, float *__restrict__ out,
+                KParams<float> p, int nz) {
+  constexpr int NW = F3F_NW, W = 128 * V;
+  extern __shared__ __align__(16) float f3f_smem[];
+  float(*sq)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3f_smem);  // [4][NW][W]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Ly = p.Ly, Lz = p.Lz;
+  const long long plane = (long long)W * Ly;
+  const int y0 = blockIdx.y * (NW - 2);
+  const int yr = y0 - 1 + warp;  // this warp's psi row (wrapped below)
+  const int y = wrapi(yr, Ly), ym = wrapi(yr - 1, Ly), yp = wrapi(yr + 1, Ly);
+  const bool outw = warp >= 1 && warp <= NW - 2 && yr < Ly;  // warp-uniform
+  const int z0 = blockIdx.z * nz, z1 = min(z0 + nz, Lz);
+  auto rowp = [&](const float *f, int yy, int zz) { return f + wrapi(zz, Lz) * plane + (long long)yy * W; };
+  auto ld = [&](const float *f, int yy, int zz, float4 (&v)[V]) {
+    const float *row = rowp(f, yy, zz);
+#pragma unroll
+    for (int q = 0; q < V; ++q) v[q] = __ldg(reinterpret_cast<const float4 *>(row + 128 * q + 4 * lane));
+  };
+  auto mv = [](float4 (&d)[V], const float4 (&s2)[V]) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) d[q] = s2[q];
+  };
+  float4 hm[V], hc[V], hp[V];     // phih of this row at planes z, z + 1, z + 2
+  float4 hym[V], hyp[V], gc[V];   // phih of plane z + 1 on rows y -+ 1, phi of plane z + 1
+  ld(A, y, z0 - 2, hm);
+  ld(A, y, z0 - 1, hc);
+  ld(A, y, z0, hp);
+  ld(A, ym, z0 - 1, hym);
+  ld(A, yp, z0 - 1, hyp);
+  ld(G, y, z0 - 1, gc);
+  for (int z = z0 - 2; z < z1; ++z) {
+    float4 nhp[V], nym[V], nyp[V], ngc[V];
+    ld(A, y, z + 3, nhp);
+    ld(A, ym, z + 2, nym);
+    ld(A, yp, z + 2, nyp);
+    ld(G, y, z + 2, ngc);
+    // psi of plane z + 1 on this warp's row
+    {
+      float l[V], r[V];
+      xnbr_row<V>(hc, l, r);
+      float *dst = &sq[(z + 1) & 3][warp][0];
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        float e[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float hk = cmp4(hc[q], j);
+          float lap = cmp4(hm[q], j);
+          lap += cmp4(hym[q], j);
+          lap += j == 0 ? l[q] : cmp4(hc[q], j - 1);
+          lap += -6.f * hk;
+          lap += j == 3 ? r[q] : cmp4(hc[q], j + 1);
+          lap += cmp4(hyp[q], j);
+          lap += cmp4(hp[q], j);
+          const float cb = p.cubic_at_half ? hk : cmp4(gc[q], j);
+          e[j] = p.a * hk + p.b * (cb * cb * cb) - p.kappa * lap;
+        }
+        *reinterpret_cast<float4 *>(dst + 128 * q + 4 * lane) = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    }
+    __syncthreads();
+    // phi^{n+1} of plane z (psi planes z - 1, z, z + 1 are in the ring)
+    if (z >= z0 && outw) {
+      auto sld = [&](int slot, int w, int q) {
+        return *reinterpret_cast<const float4 *>(&sq[slot][w][128 * q + 4 * lane]);
+      };
+      float4 qc[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) qc[q] = sld(z & 3, warp, q);
+      float l[V], r[V];
+      xnbr_row<V>(qc, l, r);
+      float *orow = out + (long long)z * plane + (long long)yr * W;
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float4 qm = sld((z + 3) & 3, warp, q), qp = sld((z + 1) & 3, warp, q);
+        const float4 qym = sld(z & 3, warp - 1, q), qyp = sld(z & 3, warp + 1, q);
+        float e[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float lap = cmp4(qm, j);
+          lap += cmp4(qym, j);
+          lap += j == 0 ? l[q] : cmp4(qc[q], j - 1);
+          lap += -6.f * cmp4(qc[q], j);
+          lap += j == 3 ? r[q] : cmp4(qc[q], j + 1);
+          lap += cmp4(qyp, j);
+          lap += cmp4(qp, j);
+          e[j] = cmp4(hm[q], j) + p.dtG * lap;
+        }
+        *reinterpret_cast<float4 *>(orow + 128 * q + 4 * lane) = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    }
+    mv(hm, hc);
+    mv(hc, hp);
+    mv(hp, nhp);
+    mv(hym, nym);
+    mv(hyp, nyp);
+    mv(gc, ngc);
+  }
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     density3d_kernel(const S *__restrict__ hin, C *__restrict__ dn, KParams<C> p) {
@@ -617,13 +752,28 @@ cudaError_t fd3d_passes(lbm_handle *h, int in) {
   const long long bxy = (long long)((p.Lx / 4 + 31) / 32) * ((p.Ly + 7) / 8);
   const int nz = (int)std::max<long long>(1, std::min<long long>(F3V_NZ, p.Lz * bxy / 1216));
   dim3 gridv((p.Lx / 4 + 31) / 32, (p.Ly + 7) / 8, (p.Lz + nz - 1) / nz);
+  // psi and the new phi fused (whole rows per warp: Lx = 128 or 256); planes
+  // per CTA: about two (Lx = 128) or one (Lx = 256, 128 registers a thread)
+  // CTAs per SM of 152, at least 4
+  const bool fused = vec && (p.Lx == 128 || p.Lx == 256) && std::getenv("HLBM_FD3_UNFUSED") == nullptr;
+  const int rows_f = (p.Ly + F3F_NW - 3) / (F3F_NW - 2);
+  const int nzf = std::max(4, std::min(p.Lz, (int)((long long)p.Lz * rows_f / 304)));
+  dim3 gridf(1, rows_f, (p.Lz + nzf - 1) / nzf);
+  const int nzf1 = std::max(4, std::min(p.Lz, (int)((long long)p.Lz * rows_f / 152)));  // one CTA per SM
+  dim3 gridf1(1, rows_f, (p.Lz + nzf1 - 1) / nzf1);
   for (int j = 0; j < h->m; ++j) {
     float *dst = static_cast<float *>(((h->m - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
     if (vec) {
       if (flux) fd3v_adv_kernel<true><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
       else fd3v_adv_kernel<false><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
-      fd3v_lap_kernel<true><<<gridv, block, 0, h->stream>>>(A, src, P, p, nz);
-      fd3v_lap_kernel<false><<<gridv, block, 0, h->stream>>>(P, A, dst, p, nz);
+      if (fused) {
+        const size_t smf = sizeof(float) * 4 * F3F_NW * p.Lx;
+        if (p.Lx == 128) fd3f_kernel<1, 2><<<gridf, F3F_NW * 32, smf, h->stream>>>(A, src, dst, p, nzf);
+        else fd3f_kernel<2, 1><<<gridf1, F3F_NW * 32, smf, h->stream>>>(A, src, dst, p, nzf1);
+      } else {
+        fd3v_lap_kernel<true><<<gridv, block, 0, h->stream>>>(A, src, P, p, nz);
+        fd3v_lap_kernel<false><<<gridv, block, 0, h->stream>>>(P, A, dst, p, nz);
+      }
     } else {
       if (flux) fd3_adv_kernel<true><<<grid, block, 0, h->stream>>>(src, u, A, p);
       else fd3_adv_kernel<false><<<grid, block, 0, h->stream>>>(src, u, A, p);
@@ -673,8 +823,15 @@ cudaError_t fd3d_configure(int precision, size_t smem) {
   if (precision == LBM_F64)
     return cudaFuncSetAttribute(fd3d_kernel<double, FD3_TX_D, FD3_TY, FD3_TZ>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(fd3d_kernel<float, FD3_TX_F, FD3_TY, FD3_TZ>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fd3d_kernel<float, FD3_TX_F, FD3_TY, FD3_TZ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd3f_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * 4 * F3F_NW * 128));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd3f_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * 4 * F3F_NW * 256));
+  return e;
 }
 
 cudaError_t collide3d_launch(lbm_handle *h, int in, int force_on, int mode) {

@@ -281,15 +281,21 @@ def test_3d_variants_fp64(variant):
 
 @pytest.mark.parametrize("variant", ["paper", "flux"])
 @pytest.mark.parametrize("fd_path,shape", [("vec", (36, 19, 21)), ("vec", (132, 10, 17)),
-                                           ("scalar", (37, 18, 21)), ("tile", (37, 18, 21))])
+                                           ("scalar", (37, 18, 21)), ("tile", (37, 18, 21)),
+                                           ("fused", (128, 19, 21)), ("fused", (256, 9, 13)),
+                                           ("vec", (128, 19, 21))])
 def test_3d_fp32_fd_paths(variant, fd_path, shape, monkeypatch):
     """FP32 3D against the oracle, both advection forms: the three FD passes
     with four x-sites per thread marching in z (Lx a multiple of 4; ragged in
     x against the 128-site warp, in y against 8 rows, in z against 16
-    planes), the one-site-per-thread passes (any Lx) and the shared-memory
-    tile kernel."""
+    planes), the one-site-per-thread passes (any Lx), the shared-memory
+    tile kernel, and the advection pass followed by the fused psi / new-phi
+    kernel (Lx = 128 or 256; ragged in y against 14 rows per CTA, in z
+    against the planes per CTA; 9 rows: fewer than one CTA's)."""
     if fd_path == "tile":
         monkeypatch.setenv("HLBM_FD3_TILE", "1")
+    if fd_path == "vec" and shape[0] in (128, 256):
+        monkeypatch.setenv("HLBM_FD3_UNFUSED", "1")
     Lx, Ly, Lz = shape
     kw = dict(CFG1, N=1 / 6, Q=1 / 3, adv_variant=1 if variant == "flux" else 0)
     op, lp = _pair(Lx, Ly, Lz, dims=3, m=8, precision=lbm.LBM_F32DEV, **kw)
