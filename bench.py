@@ -491,9 +491,11 @@ def run_drop3d(args, rank, world, local):
                   "avg_launch_us": c_s * 1e6, "peak_kind": peak_kind, "share_of_step": cms / (cms + fms)}
         roof_f = {"bound": "hbm", "achieved": af, "peak": peak, "unit": "GB/s", "frac": af / peak,
                   "traffic": None,
-                  "kernel": "fd3d (m = 8 substeps, three passes each: phih, psi, phi)",
+                  "kernel": ("fd3d (m = 8 substeps, each an advection pass and a fused psi / new-phi "
+                             "pass)" if S3 in (128, 256) else
+                             "fd3d (m = 8 substeps, three passes each: phih, psi, phi)"),
                   "bytes_per_site": D3_M * D3_FD_BYTES, "avg_launch_us": f_s * 1e6,
-                  "note": "avg_launch_us covers the 24 launches of one LB step",
+                  "note": f"avg_launch_us covers the {fn} FD launches of one LB step",
                   "peak_kind": peak_kind, "share_of_step": fms / (cms + fms)}
         dom, oth = (roof_c, roof_f) if cms >= fms else (roof_f, roof_c)
         out[name] = {"value": value, "ms_per_step": ms, "roofline": dom, "roofline_other_kernel": oth,

@@ -19,13 +19,21 @@ namespace hlbm {
 
 namespace {
 
-constexpr int C3_TX = 32, C3_TY = 8, C3_TZ = 4;  // block 32 x 8, 4 z-planes per thread
+constexpr int C3_TX = 32, C3_TY = 8;  // block 32 x 8; z-planes per thread: c3_tz<C>()
+template <typename C>
+constexpr int c3_tz() {
+  return sizeof(C) == 8 ? 4 : 8;  // FP64: the phi and mu tiles must fit 48 KB of static shared memory
+}
 
-template <typename S, typename C, bool TGEN, int MODE>
-__global__ void __launch_bounds__(256)
+// Wraps x in [-L, 2L) into [0, L).
+__device__ __forceinline__ int wrap1_3(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
+
+template <typename S, typename C, bool TGEN, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     collide3d_kernel(const S *__restrict__ hin, S *__restrict__ hout, const C *__restrict__ phi,
                      const C *__restrict__ dn, C *__restrict__ uout, double *__restrict__ stg,
                      KParams<C> p) {
+  constexpr int C3_TZ = c3_tz<C>();
   constexpr int PX = C3_TX + 4, PY = C3_TY + 4, PZ = C3_TZ + 4;
   constexpr int MX = C3_TX + 2, MY = C3_TY + 2, MZ = C3_TZ + 2;
   __shared__ C sphi[PZ][PY][PX];
@@ -34,9 +42,49 @@ __global__ void __launch_bounds__(256)
   const long long Sz = (long long)Lx * Ly * Lz;
   const int x0 = blockIdx.x * C3_TX, y0 = blockIdx.y * C3_TY, z0 = blockIdx.z * C3_TZ;
   const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int lx = threadIdx.x, ly = threadIdx.y, x = x0 + lx, y = y0 + ly;
+  const bool site_ok = x < Lx && y < Ly;
+  const int xc = site_ok ? x : 0, yc_ = site_ok ? y : 0;
+  const int xm = xc == 0 ? Lx - 1 : xc - 1, xp = xc == Lx - 1 ? 0 : xc + 1;
+  const int ym = yc_ == 0 ? Ly - 1 : yc_ - 1, yp = yc_ == Ly - 1 ? 0 : yc_ + 1;
+  const long long pl = (long long)Lx * Ly;
+  const long long yc = (long long)yc_ * Lx, ymo = (long long)ym * Lx, ypo = (long long)yp * Lx;
+  // f_i(r) = buf_i(r - e_i) of plane z (clamped into the lattice for threads
+  // without a site; their values are never used)
+  auto load_plane = [&](C (&hv)[19], int z) {
+    const int zm = z == 0 ? Lz - 1 : z - 1, zp = z == Lz - 1 ? 0 : z + 1;
+    const long long zc = (long long)z * pl, zmo = (long long)zm * pl, zpo = (long long)zp * pl;
+#define LD(i, zz, yy, xx) hv[i] = Store<S, C>::ld(hin + (i)*Sz + (zz) + (yy) + (xx), p.inv_scale)
+    LD(0, zc, yc, xc);
+    LD(1, zc, yc, xm);
+    LD(2, zc, yc, xp);
+    LD(3, zc, ymo, xc);
+    LD(4, zc, ypo, xc);
+    LD(5, zmo, yc, xc);
+    LD(6, zpo, yc, xc);
+    LD(7, zc, ymo, xm);    // (1,1,0)
+    LD(8, zc, ypo, xp);    // (-1,-1,0)
+    LD(9, zc, ypo, xm);    // (1,-1,0)
+    LD(10, zc, ymo, xp);   // (-1,1,0)
+    LD(11, zmo, yc, xm);   // (1,0,1)
+    LD(12, zpo, yc, xp);   // (-1,0,-1)
+    LD(13, zpo, yc, xm);   // (1,0,-1)
+    LD(14, zmo, yc, xp);   // (-1,0,1)
+    LD(15, zmo, ymo, xc);  // (0,1,1)
+    LD(16, zpo, ypo, xc);  // (0,-1,-1)
+    LD(17, zpo, ymo, xc);  // (0,1,-1)
+    LD(18, zmo, ypo, xc);  // (0,-1,1)
+#undef LD
+  };
+  // the first plane's populations are in flight while phi and mu are staged
+  C hv[19], hn[19];
+  if (z0 < Lz) load_plane(hv, z0);
+  const bool big = Lx >= PX && Ly >= PY && Lz >= PZ;
   for (int k = tid; k < PX * PY * PZ; k += 256) {
     const int rz = k / (PX * PY), rem = k - rz * PX * PY, ry = rem / PX, rx = rem - ry * PX;
-    const int gx = wrapi(x0 + rx - 2, Lx), gy = wrapi(y0 + ry - 2, Ly), gz = wrapi(z0 + rz - 2, Lz);
+    const int gx = big ? wrap1_3(x0 + rx - 2, Lx) : wrapi(x0 + rx - 2, Lx);
+    const int gy = big ? wrap1_3(y0 + ry - 2, Ly) : wrapi(y0 + ry - 2, Ly);
+    const int gz = big ? wrap1_3(z0 + rz - 2, Lz) : wrapi(z0 + rz - 2, Lz);
     sphi[rz][ry][rx] = phi[((long long)gz * Ly + gy) * Lx + gx];
   }
   __syncthreads();
@@ -59,15 +107,13 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
 
-  const int lx = threadIdx.x, ly = threadIdx.y, x = x0 + lx, y = y0 + ly;
-  if (x >= Lx || y >= Ly) return;
-  const int xm = x == 0 ? Lx - 1 : x - 1, xp = x == Lx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? Ly - 1 : y - 1, yp = y == Ly - 1 ? 0 : y + 1;
+  if (!site_ok) return;
 #pragma unroll 1
   for (int lz = 0; lz < C3_TZ; ++lz) {
     const int z = z0 + lz;
     if (z >= Lz) break;
-    const int zm = z == 0 ? Lz - 1 : z - 1, zp = z == Lz - 1 ? 0 : z + 1;
+    // the next plane's populations are issued before this plane is computed
+    if (lz + 1 < C3_TZ && z + 1 < Lz) load_plane(hn, z + 1);
     const int mx = lx + 1, my = ly + 1, mz = lz + 1;
     // d_D mu along x, y, z
     auto grad = [&](const C (*f)[MY][MX], C &gx_, C &gy_, C &gz_) {
@@ -108,32 +154,7 @@ __global__ void __launch_bounds__(256)
             p.M * (((pn(-1, 0, 1) - pn(-1, 0, -1)) + (pn(1, 0, 1) - pn(1, 0, -1))) +
                    ((pn(0, -1, 1) - pn(0, -1, -1)) + (pn(0, 1, 1) - pn(0, 1, -1))));
     }
-    const long long pl = (long long)Lx * Ly;
-    const long long zc = (long long)z * pl, zmo = (long long)zm * pl, zpo = (long long)zp * pl;
-    const long long yc = (long long)y * Lx, ymo = (long long)ym * Lx, ypo = (long long)yp * Lx;
-    // f_i(r) = buf_i(r - e_i)
-    C hv[19];
-#define LD(i, zz, yy, xx) hv[i] = Store<S, C>::ld(hin + (i)*Sz + (zz) + (yy) + (xx), p.inv_scale)
-    LD(0, zc, yc, x);
-    LD(1, zc, yc, xm);
-    LD(2, zc, yc, xp);
-    LD(3, zc, ymo, x);
-    LD(4, zc, ypo, x);
-    LD(5, zmo, yc, x);
-    LD(6, zpo, yc, x);
-    LD(7, zc, ymo, xm);    // (1,1,0)
-    LD(8, zc, ypo, xp);    // (-1,-1,0)
-    LD(9, zc, ypo, xm);    // (1,-1,0)
-    LD(10, zc, ymo, xp);   // (-1,1,0)
-    LD(11, zmo, yc, xm);   // (1,0,1)
-    LD(12, zpo, yc, xp);   // (-1,0,-1)
-    LD(13, zpo, yc, xm);   // (1,0,-1)
-    LD(14, zmo, yc, xp);   // (-1,0,1)
-    LD(15, zmo, ymo, x);   // (0,1,1)
-    LD(16, zpo, ypo, x);   // (0,-1,-1)
-    LD(17, zpo, ymo, x);   // (0,1,-1)
-    LD(18, zmo, ypo, x);   // (0,-1,1)
-#undef LD
+    const long long zc = (long long)z * pl;
     C dens = hv[0];
 #pragma unroll
     for (int i = 1; i < 19; ++i) dens += hv[i];
@@ -162,6 +183,8 @@ __global__ void __launch_bounds__(256)
       stg[2 * Sz + s] = (double)ux;
       stg[3 * Sz + s] = (double)uy;
       stg[4 * Sz + s] = (double)uz;
+#pragma unroll
+      for (int i = 0; i < 19; ++i) hv[i] = hn[i];
       continue;
     }
     const C usq = ux * ux + uy * uy + uz * uz;
@@ -192,6 +215,8 @@ __global__ void __launch_bounds__(256)
     uout[s] = ux;
     uout[Sz + s] = uy;
     uout[2 * Sz + s] = uz;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) hv[i] = hn[i];
   }
 }
 
@@ -713,7 +738,7 @@ __global__ void __launch_bounds__(256)
 template <typename S, typename C>
 cudaError_t collide3d(lbm_handle *h, int in, int force_on, int mode) {
   KParams<C> p = make_params<C>(h, force_on);
-  dim3 grid((p.Lx + C3_TX - 1) / C3_TX, (p.Ly + C3_TY - 1) / C3_TY, (p.Lz + C3_TZ - 1) / C3_TZ);
+  dim3 grid((p.Lx + C3_TX - 1) / C3_TX, (p.Ly + C3_TY - 1) / C3_TY, (p.Lz + c3_tz<C>() - 1) / c3_tz<C>());
   dim3 block(32, C3_TY);
   const S *hin = static_cast<const S *>(h->h[in]);
   S *hout = static_cast<S *>(h->h[1 - in]);
@@ -721,20 +746,18 @@ cudaError_t collide3d(lbm_handle *h, int in, int force_on, int mode) {
   const C *dn = static_cast<const C *>(h->dn);
   C *u = static_cast<C *>(h->u);
   const bool tgen = p.cs2mT != C(0);
+  // registers budgeted for 3 CTAs per SM (85 a thread, no spill in FP32): 576 us
+  // at 256^3 against 698 us for 2 and 618 us for 4 (spilling)
   if (mode == COLLIDE_STEP) {
     if (tgen)
-      collide3d_kernel<S, C, true, COLLIDE_STEP>
-          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+      collide3d_kernel<S, C, true, COLLIDE_STEP, 3><<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
     else
-      collide3d_kernel<S, C, false, COLLIDE_STEP>
-          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+      collide3d_kernel<S, C, false, COLLIDE_STEP, 3><<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   } else {
     if (tgen)
-      collide3d_kernel<S, C, true, COLLIDE_MOMENTS>
-          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+      collide3d_kernel<S, C, true, COLLIDE_MOMENTS, 3><<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
     else
-      collide3d_kernel<S, C, false, COLLIDE_MOMENTS>
-          <<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
+      collide3d_kernel<S, C, false, COLLIDE_MOMENTS, 3><<<grid, block, 0, h->stream>>>(hin, hout, phi, dn, u, h->staging, p);
   }
   return cudaGetLastError();
 }
