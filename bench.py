@@ -337,10 +337,56 @@ def run_ours(args, rank, world, local):
             "gpu_launches": gpu_launches,
             "clocks": clocks.summary(),
         }
+        if side == L and not args.no_large:
+            line["large_lattice"] = large_lattice(args.large_side, stream)
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def large_lattice(side, stream):
+    """The same scheme on side^2 (default 4096^2, 1.5 GB of populations: far
+    beyond L2), where the collide kernel is HBM-bound: whole-step MLUPS over
+    3 x 100 LB steps and both kernels' per-launch event times."""
+    import torch
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    S = side * side
+    lat = lbm.Lattice(lbm.LbmParams(Lx=side, Ly=side, fd_substeps=M_SUB, precision=lbm.LBM_F32DEV, **CFG),
+                      stream=stream.cuda_stream)
+    n, u = I.rest(2, side, side)
+    lat.init_fields(n, I.spinodal(2, side, side, seed=0), u)
+    del n, u
+    with torch.cuda.stream(stream):
+        lat.step(100)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for _ in range(3):
+            lat.step(100)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    lbm.lbm_set_kernel_timing(lat.handle, True)
+    lbm.lbm_kernel_times(lat.handle, reset=True)
+    with torch.cuda.stream(stream):
+        lat.step(100)
+    kt = lbm.lbm_kernel_times(lat.handle, reset=True)
+    tuning = lbm.lbm_tuning(lat.handle)
+    lat.close()
+    (cms, cn), (fms, fn) = kt["collide"], kt["fd"]
+    c_s = cms / cn / 1000.0
+    peak, peak_kind = measured_peak()
+    ach = COLLIDE_BYTES_PER_SITE * S / c_s / 1e9
+    return {"lattice": [side, side], "value": S * 300 / (ms / 1000.0) / 1e6, "unit": "MLUPS",
+            "lb_steps_timed": 300, "tuning": tuning,
+            "collide": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "avg_launch_us": c_s * 1e6, "bytes_per_site": COLLIDE_BYTES_PER_SITE,
+                        "peak_kind": peak_kind},
+            "fd_avg_launch_us": fms / fn * 1000.0, "fd_launches_per_lb_step": fn / 100.0}
 
 
 def run_batched(args, rank, world, local):
@@ -687,6 +733,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (the workload is 1024; other sides are for profiling)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4096^2 (--large-side) line")
+    ap.add_argument("--large-side", type=int, default=4096)
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no kernel timing, e2e or CPU baseline)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one")
