@@ -58,6 +58,31 @@ def test_batch_fp64_matches_oracle(graphs):
     b.close()
 
 
+def test_batch_flux_variant_odd_substeps_fp64():
+    """The conservative advection form and m = 5 (sweeps of 2 + 2 + 1 FD
+    substeps over the shared-memory tiles), on instances smaller than the
+    halo (4 x 3), one tile (50 x 20) and several tiles (150 x 70)."""
+    insts = [(4, 3, (0.0, 0.0), 0), (50, 20, (1e-5, 0.0), 6), (150, 70, (0.0, -2e-5), 100)]
+    common = lbm.LbmParams(precision=lbm.LBM_F64, fd_substeps=5, adv_variant=1, **CFG1)
+    b = lbm.Batch(common, insts)
+    fields = []
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        f = _instance_fields(Lx, Ly, R=min(Lx, Ly) / 4, seed=10 + k)
+        fields.append(f)
+        b.init_fields(k, *f)
+    b.step(13)
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        op = O.Params(Lx=Lx, Ly=Ly, m=5, adv_variant=1, g=(g[0], g[1], 0.0), force_steps=fs, **CFG1)
+        st = O.State.create(op, *fields[k])
+        st.run(13)
+        rn, ru = st.moments()
+        gn, gphi, gu = b.moments(k)
+        assert np.max(np.abs(gphi - st.phi)) <= 1e-11, k
+        assert np.max(np.abs(gu - ru)) <= 1e-12, k
+        assert np.max(np.abs(gn - rn)) <= 1e-11, k
+    b.close()
+
+
 def test_batch_config_fp32_sampled_instances():
     """512 instances, sides in {32, 48, ..., 256}, drop radius in [6, side/3],
     half of them pushed by g_x = 1e-5 (here for the first 40 of 60 steps).
