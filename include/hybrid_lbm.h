@@ -282,9 +282,11 @@ int lbm_net_train_step(lbm_net *net, const float *x0, const float *x1, int N, in
 int lbm_surrogate_state(lbm_handle *h, float *out);
 /* Advances h by `windows` windows of `window_steps` LB steps each with the
  * network: state -> prediction -> residual check (mean change of phi per site
- * |d sum phi| / sites <= mass_tol; max |phi| <= max(1.1 phi0, 1.05 max|phi_t|);
- * max |u*| <= max(1.5 max|u*_t|, 0.01 c_s); max |n - 1| <= max(2 max|n_t - 1|,
- * 1e-3); every value finite; with _t the state the window starts from;
+ * |d sum phi| / sites <= mass_tol; max |phi| <= min(max(1.1 phi0, 1.05
+ * max|phi_t|), 1.5 phi0); max |u*| <= min(max(1.5 max|u*_t|, 0.01 c_s),
+ * 0.5 c_s); max |n - 1| <= min(max(2 max|n_t - 1|, 1e-3), 0.3); every value
+ * finite; with _t the state the window starts from; the ceilings keep
+ * accepted windows from compounding the relative bounds;
  * HLBM_SURROGATE_VERBOSE=1 prints the values per window); a passing
  * prediction becomes the new state (populations rebuilt as f_eq(n, u* - F/2n)
  * with phi shifted to keep sum phi if conserve_mass), a failing one is
@@ -294,6 +296,16 @@ int lbm_surrogate_state(lbm_handle *h, float *out);
  * windows * window_steps. */
 int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_steps,
                           double mass_tol, int conserve_mass, double phi_clamp, int *fallbacks);
+/* As lbm_surrogate_advance, with relax_steps >= 0 plain LB steps after every
+ * prediction: the predicted state becomes the lattice state, relax_steps
+ * steps run, and the residual check applies to the relaxed state; a failing
+ * window restores the populations and phi of its start (kept in a device
+ * copy owned by net) and runs window_steps + relax_steps plain steps.  Each
+ * window advances t by window_steps + relax_steps; relax_steps = 0 is
+ * lbm_surrogate_advance. */
+int lbm_surrogate_advance_relaxed(lbm_handle *h, lbm_net *net, int windows, int window_steps,
+                                  int relax_steps, double mass_tol, int conserve_mass, double phi_clamp,
+                                  int *fallbacks);
 void lbm_net_free(lbm_net *net);
 const char *lbm_net_last_error(const lbm_net *net);
 

@@ -397,6 +397,8 @@ struct lbm_net {
   long long cap = 0;     // pixels the workspace holds
   bf16 *act[8] = {nullptr};
   float *yout = nullptr, *x0 = nullptr, *x1 = nullptr;
+  void *bk = nullptr;     // a lattice's populations and phi (relaxed surrogate windows)
+  size_t bk_cap = 0;
   bf16 *dz[2] = {nullptr, nullptr};
   float *partial = nullptr;
   double *dpart = nullptr;
@@ -800,7 +802,14 @@ int lbm_surrogate_state(lbm_handle *h, float *out) {
 
 int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_steps,
                           double mass_tol, int conserve_mass, double phi_clamp, int *fallbacks) {
-  if (!h || !net || windows < 0 || window_steps < 1) return LBM_EINVAL;
+  return lbm_surrogate_advance_relaxed(h, net, windows, window_steps, 0, mass_tol, conserve_mass,
+                                       phi_clamp, fallbacks);
+}
+
+int lbm_surrogate_advance_relaxed(lbm_handle *h, lbm_net *net, int windows, int window_steps,
+                                  int relax_steps, double mass_tol, int conserve_mass, double phi_clamp,
+                                  int *fallbacks) {
+  if (!h || !net || windows < 0 || window_steps < 1 || relax_steps < 0) return LBM_EINVAL;
   if (h->err) return h->err;
   if (!h->inited || h->dims != 2) return LBM_ESTATE;
   if (h->P.force_steps > h->t) return nfail(net, LBM_EINVAL, "the surrogate needs the body force off");
@@ -812,6 +821,29 @@ int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_s
   cudaStream_t s = h->stream;
   const int sb = 512;
   int nfb = 0;
+  if (relax_steps > 0 && net->bk_cap < h->hbytes + h->phibytes) {
+    cudaFree(net->bk);
+    net->bk = nullptr;
+    NCK(net, cudaMalloc(&net->bk, h->hbytes + h->phibytes), "cudaMalloc");
+    net->bk_cap = h->hbytes + h->phibytes;
+  }
+  // sums and maxima (NSTAT each) of a state array, reduced on the host
+  std::vector<double> part(NSTAT * sb);
+  auto stats_of = [&](const float *x, double (&out)[NSTAT]) -> int {
+    state_stats_kernel<<<sb, 256, 0, s>>>(x, S, net->dpart);
+    NCK(net, cudaGetLastError(), "surrogate kernels");
+    NCK(net, cudaMemcpyAsync(part.data(), net->dpart, sizeof(double) * NSTAT * sb, cudaMemcpyDeviceToHost, s),
+        "copy");
+    NCK(net, cudaStreamSynchronize(s), "synchronize");
+    for (int j = 0; j < NSTAT; j++) out[j] = 0.0;
+    for (int b = 0; b < sb; b++) {
+      const double *q = &part[b * NSTAT];
+      out[0] += q[0];
+      out[1] += q[1];
+      for (int j = 2; j < NSTAT; j++) out[j] = std::max(out[j], q[j]);
+    }
+    return LBM_OK;
+  };
   for (int w = 0; w < windows; w++) {
     rc = lbm_surrogate_state(h, net->x0);
     if (rc) return rc;
@@ -819,33 +851,43 @@ int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_s
     if (rc) return rc;
     predict_kernel<<<nblk(S, 256), 256, 0, s>>>(net->yout, net->x0, S, net->nrm, net->x1);
     NCK(net, cudaGetLastError(), "surrogate kernels");
-    double st[2][NSTAT] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
-    std::vector<double> part(NSTAT * sb);
-    for (int k = 0; k < 2; k++) {
-      state_stats_kernel<<<sb, 256, 0, s>>>(k == 0 ? net->x0 : net->x1, S, net->dpart);
-      NCK(net, cudaGetLastError(), "surrogate kernels");
-      NCK(net, cudaMemcpyAsync(part.data(), net->dpart, sizeof(double) * NSTAT * sb,
-                               cudaMemcpyDeviceToHost, s),
+    double st[2][NSTAT];
+    if ((rc = stats_of(net->x0, st[0]))) return rc;
+    if (phi_clamp > 0.0) {
+      clamp_phi_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, (float)(phi_clamp * st[0][2]));
+      NCK(net, cudaGetLastError(), "clamp kernel");
+    }
+    if ((rc = stats_of(net->x1, st[1]))) return rc;
+    // relaxation: the prediction becomes the lattice state and relax_steps
+    // plain steps damp its short-wavelength errors before the check (the
+    // state of the window's start is kept to fall back to)
+    const long long t_start = h->t;
+    const int cur_start = h->cur;
+    if (relax_steps > 0) {
+      char *bk = static_cast<char *>(net->bk);
+      NCK(net, cudaMemcpyAsync(bk, h->h[cur_start], h->hbytes, cudaMemcpyDeviceToDevice, s), "copy");
+      NCK(net, cudaMemcpyAsync(bk + h->hbytes, h->phi[cur_start], h->phibytes, cudaMemcpyDeviceToDevice, s),
           "copy");
-      NCK(net, cudaStreamSynchronize(s), "synchronize");
-      for (int b = 0; b < sb; b++) {
-        const double *q = &part[b * NSTAT];
-        st[k][0] += q[0];
-        st[k][1] += q[1];
-        for (int j = 2; j < NSTAT; j++) st[k][j] = std::max(st[k][j], q[j]);
-      }
-      if (k == 0 && phi_clamp > 0.0) {
-        clamp_phi_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, (float)(phi_clamp * st[0][2]));
-        NCK(net, cudaGetLastError(), "clamp kernel");
-      }
+      const double shift0 = conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0;
+      staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift0, h->staging);
+      NCK(net, cudaGetLastError(), "staging kernel");
+      if (launch_init(h, h->cur) != cudaSuccess) return LBM_ECUDA;
+      h->t += window_steps;
+      if ((rc = lbm_step(h, relax_steps))) return rc;
+      if ((rc = lbm_surrogate_state(h, net->x1))) return rc;
+      if ((rc = stats_of(net->x1, st[1]))) return rc;
     }
     // residual check: the mean change of phi per site, and bounds on |phi|,
     // |u*| and |n - 1| relative to the state the window starts from (an
     // unbounded, non-finite or runaway prediction fails them)
     const double drift = std::fabs(st[1][0] - st[0][0]) / (double)S;
-    const double phi_cap = std::max(1.1 * h->phi0, 1.05 * st[0][2]);
-    const double u_cap = std::max(1.5 * st[0][3], 0.01 / std::sqrt(3.0));
-    const double n_cap = std::max(2.0 * st[0][4], 1e-3);
+    // (relative bounds, each under an absolute ceiling so that accepted
+    // windows cannot compound them into a runaway: |phi| <= 1.5 phi0,
+    // |u*| <= 0.5 c_s, |n - 1| <= 0.3; plain spinodal states with the
+    // benchmark's parameters reach |u*| = 0.2 c_s and |n - 1| = 0.07)
+    const double phi_cap = std::min(std::max(1.1 * h->phi0, 1.05 * st[0][2]), 1.5 * h->phi0);
+    const double u_cap = std::min(std::max(1.5 * st[0][3], 0.01 / std::sqrt(3.0)), 0.5 / std::sqrt(3.0));
+    const double n_cap = std::min(std::max(2.0 * st[0][4], 1e-3), 0.3);
     const bool ok = std::isfinite(st[1][2]) && std::isfinite(st[1][3]) && std::isfinite(st[1][4]) &&
                     drift <= mass_tol && st[1][2] <= phi_cap && st[1][3] <= u_cap && st[1][4] <= n_cap;
     if (std::getenv("HLBM_SURROGATE_VERBOSE"))
@@ -854,7 +896,18 @@ int lbm_surrogate_advance(lbm_handle *h, lbm_net *net, int windows, int window_s
                    "(state %.3e) max|n-1| %.3e (state %.3e) -> %s\n",
                    h->t, drift, st[1][2], st[0][2], st[1][3], st[0][3], st[1][4], st[0][4],
                    ok ? "accepted" : "plain steps");
-    if (ok) {
+    if (relax_steps > 0) {
+      if (!ok) {  // back to the window's start, then the plain steps
+        nfb++;
+        const char *bk = static_cast<const char *>(net->bk);
+        h->cur = cur_start;
+        h->t = t_start;
+        NCK(net, cudaMemcpyAsync(h->h[cur_start], bk, h->hbytes, cudaMemcpyDeviceToDevice, s), "copy");
+        NCK(net, cudaMemcpyAsync(h->phi[cur_start], bk + h->hbytes, h->phibytes, cudaMemcpyDeviceToDevice, s),
+            "copy");
+        if ((rc = lbm_step(h, window_steps + relax_steps))) return rc;
+      }
+    } else if (ok) {
       const double shift = conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0;
       staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift, h->staging);
       NCK(net, cudaGetLastError(), "staging kernel");
@@ -876,7 +929,7 @@ void lbm_net_free(lbm_net *net) {
   cudaDeviceSynchronize();
   void *ptrs[] = {net->w32, net->b32, net->gw, net->gb, net->mw, net->vw, net->mb, net->vb, net->wbf,
                   net->wtbf, net->nrm, net->yout, net->x0, net->x1, net->dz[0], net->dz[1],
-                  net->partial, net->dpart};
+                  net->partial, net->dpart, net->bk};
   for (void *p : ptrs) if (p) cudaFree(p);
   for (auto &a : net->act) if (a) cudaFree(a);
   delete net;

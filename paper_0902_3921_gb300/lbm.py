@@ -36,7 +36,8 @@ EXPORTS = ("lbm_create", "lbm_buffer_bytes", "lbm_create_with_buffers", "lbm_ini
            "lbm_net_param_count", "lbm_net_params", "lbm_net_grads", "lbm_net_set_normalisation",
            "lbm_net_normalisation", "lbm_net_forward", "lbm_net_layer_times", "lbm_net_train_step",
            "lbm_surrogate_state",
-           "lbm_surrogate_advance", "lbm_net_free", "lbm_net_last_error")
+           "lbm_surrogate_advance", "lbm_surrogate_advance_relaxed", "lbm_net_free",
+           "lbm_net_last_error")
 
 
 class c_lbm_buffers(ctypes.Structure):
@@ -149,13 +150,15 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_surrogate_state.argtypes = [H, vp]
     lib.lbm_surrogate_advance.argtypes = [H, Nt, ip, ip, ctypes.c_double, ip, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int)]
+    lib.lbm_surrogate_advance_relaxed.argtypes = [H, Nt, ip, ip, ip, ctypes.c_double, ip, ctypes.c_double,
+                                                  ctypes.POINTER(ctypes.c_int)]
     lib.lbm_net_free.argtypes = [Nt]
     lib.lbm_net_free.restype = None
     lib.lbm_net_last_error.argtypes = [Nt]
     lib.lbm_net_last_error.restype = ctypes.c_char_p
     for name in ("lbm_net_create", "lbm_net_params", "lbm_net_grads", "lbm_net_set_normalisation",
                  "lbm_net_normalisation", "lbm_net_forward", "lbm_net_layer_times", "lbm_net_train_step",
-                 "lbm_surrogate_state", "lbm_surrogate_advance"):
+                 "lbm_surrogate_state", "lbm_surrogate_advance", "lbm_surrogate_advance_relaxed"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_moments",
                  "lbm_batch_set_graphs", "lbm_batch_shape", "lbm_batch_synchronize"):
@@ -617,11 +620,11 @@ def lbm_surrogate_state(h, out_ptr):
 
 
 def lbm_surrogate_advance(h, net: Net, windows, window_steps, mass_tol=2e-3, conserve_mass=True,
-                          phi_clamp=0.0):
+                          phi_clamp=0.0, relax_steps=0):
     fb = ctypes.c_int()
-    rc = load_library().lbm_surrogate_advance(h, net.handle, int(windows), int(window_steps),
-                                              float(mass_tol), int(conserve_mass), float(phi_clamp),
-                                              ctypes.byref(fb))
+    rc = load_library().lbm_surrogate_advance_relaxed(h, net.handle, int(windows), int(window_steps),
+                                                      int(relax_steps), float(mass_tol), int(conserve_mass),
+                                                      float(phi_clamp), ctypes.byref(fb))
     if rc != LBM_OK:
         msg = load_library().lbm_net_last_error(net.handle).decode() or lbm_last_error(h)
         raise LbmError(rc, "lbm_surrogate_advance: " + msg)

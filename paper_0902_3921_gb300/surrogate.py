@@ -127,7 +127,7 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
 
 
 def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 16000),
-             window=50, mass_tol=2e-3, phi_clamp=0.0, log=None):
+             window=50, mass_tol=2e-3, phi_clamp=0.0, relax=0, log=None):
     import torch
     stream = torch.cuda.Stream()
     n, u = I.rest(2, side, side)
@@ -149,8 +149,11 @@ def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 1
         stream.synchronize()
         with torch.cuda.stream(stream):
             ev[2].record(stream)
-            fb = lbm.lbm_surrogate_advance(surr.handle, net, dt // window, window, mass_tol, True,
-                                           phi_clamp)
+            nwin = dt // (window + relax)
+            fb = lbm.lbm_surrogate_advance(surr.handle, net, nwin, window, mass_tol, True,
+                                           phi_clamp, relax_steps=relax)
+            if dt - nwin * (window + relax):
+                surr.step(dt - nwin * (window + relax))
             ev[3].record(stream)
         stream.synchronize()
         tp, ts = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
@@ -164,7 +167,7 @@ def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 1
         row = {"t": tc, "L_plain": OB.domain_size(pp), "L_surrogate": OB.domain_size(ps),
                "S_rel_l2": float(np.linalg.norm(Ss - Sp) / np.linalg.norm(Sp)),
                "sum_phi_plain": float(pp.sum()), "sum_phi_surrogate": float(ps.sum()),
-               "sum_phi_start": float(phi0.sum()), "fallbacks": fb, "windows": dt // window,
+               "sum_phi_start": float(phi0.sum()), "fallbacks": fb, "windows": dt // (window + relax),
                "ms_plain": tp, "ms_surrogate": ts}
         rows.append(row)
         if log:
@@ -189,6 +192,7 @@ def main():
     ap.add_argument("--window", type=int, default=50)
     ap.add_argument("--mass-tol", type=float, default=2e-3)
     ap.add_argument("--phi-clamp", type=float, default=0.0)
+    ap.add_argument("--relax", type=int, default=0, help="plain LB steps after each prediction, before the check")
     ap.add_argument("--reservoir", type=int, default=0, help="pairs kept for sampling (0: none)")
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--updates", type=int, default=1, help="training steps per window")
@@ -215,8 +219,9 @@ def main():
         np.savez(args.save, params=net.get_params(), normalisation=np.asarray(net.normalisation()))
     res = evaluate(net, args.eval_side, checkpoints=tuple(int(c) for c in args.checkpoints.split(",")),
                    window=args.window, mass_tol=args.mass_tol, phi_clamp=args.phi_clamp,
-                   log=lambda m: print(m, flush=True))
-    print(json.dumps({"training": hist, "evaluation": res, "window": args.window}), flush=True)
+                   relax=args.relax, log=lambda m: print(m, flush=True))
+    print(json.dumps({"training": hist, "evaluation": res, "window": args.window, "relax": args.relax}),
+          flush=True)
 
 
 if __name__ == "__main__":

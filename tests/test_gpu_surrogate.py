@@ -297,6 +297,39 @@ def test_residual_check_rejects_nonfinite_and_runaway_density():
         net.close()
 
 
+def test_relaxed_windows_fall_back_to_the_exact_start_state():
+    """With relax_steps > 0 the prediction becomes the lattice state before
+    the check; a rejected window (a NaN prediction) restores the saved
+    populations and phi of its start and runs window + relax plain steps, so
+    the lattice stays bitwise equal to one stepped plainly; an accepted
+    "no change" prediction advances t by window + relax per window."""
+    cfg = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    p = lbm.LbmParams(Lx=64, Ly=32, precision=lbm.LBM_F32DEV, fd_substeps=4, **cfg)
+    phi = I.spinodal(2, 64, 32, seed=7, amp=0.1)
+    n, u = I.rest(2, 64, 32)
+    a = lbm.Lattice(p).init_fields(n, phi, u)
+    b = lbm.Lattice(p).init_fields(n, phi, u)
+    a.step(5)
+    b.step(5)
+    net = lbm.Net(16, 3, seed=3)
+    net.set_normalisation(*NORM)
+    w = np.zeros(net.nparams, dtype=np.float32)
+    w[-1] = np.nan
+    net.set_params(w)
+    fb = lbm.lbm_surrogate_advance(a.handle, net, windows=3, window_steps=10, mass_tol=1.0, relax_steps=3)
+    b.step(39)
+    assert fb == 3 and a.t == b.t == 44
+    for xa, xb in zip(a.moments(), b.moments()):
+        assert np.array_equal(xa, xb)
+    net.set_params(np.zeros(net.nparams, dtype=np.float32))
+    fb = lbm.lbm_surrogate_advance(a.handle, net, windows=2, window_steps=10, mass_tol=1e-3, relax_steps=3)
+    assert fb == 0 and a.t == 70
+    assert np.all(np.isfinite(a.moments()[1]))
+    net.close()
+    a.close()
+    b.close()
+
+
 def test_train_and_evaluate_end_to_end():
     """A short version of the training/evaluation pipeline: the loss falls
     and the surrogate-advanced lattice keeps its mass and domain size close
