@@ -691,6 +691,7 @@ def run_surrogate(args, rank, world, local):
     ms_plain = t0.elapsed_time(t1) / 4
     plain = P * SURR_WINDOW / (ms_plain / 1000.0) / 1e6
     lat.close()
+    fixed = None if args.no_fixed_error else surrogate_fixed_error(S)
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         pxs, secs = cpu_surrogate_forward(side=256, reps=3)
@@ -716,11 +717,43 @@ def run_surrogate(args, rank, world, local):
             "layer_us": [v * 1000.0 for v in layer_ms],
             "plain_scheme": {"value": plain, "unit": "MLUPS", "lattice": [S, S]},
             "speedup_vs_plain_per_window": value / plain,
+            "fixed_error": fixed,
             "cpu_baseline": cpu,
             "e2e": {"value": P * SURR_WINDOW / (ms_e2e / 1000.0) / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": P * 16, "d2h_bytes_per_step": P * 16},
             "gpu_launches": 8 * steps,
             "clocks": clocks.summary()}), flush=True)
+
+
+SURR_WEIGHTS = os.path.join(ROOT, "paper_0902_3921_gb300", "weights", "surrogate_32ch6_spinodal.npz")
+
+
+def surrogate_fixed_error(side):
+    """The trained network (paper_0902_3921_gb300/weights, trained on 512^2
+    spinodal trajectories, t = 2000 ... 12000) against the plain scheme on
+    the side^2 spinodal lattice (seed 1000) from t = 2000 to 16000, windows of
+    50 LB steps with the residual check: wall-clock speedup and the errors of
+    L(t) and S(k) at t = 4000, 8000, 16000."""
+    import numpy as np
+    from paper_0902_3921_gb300 import lbm
+    from paper_0902_3921_gb300 import surrogate as SG
+
+    if not os.path.exists(SURR_WEIGHTS):
+        return None
+    z = np.load(SURR_WEIGHTS)
+    net = lbm.Net(32, 6, seed=0)
+    net.set_params(z["params"])
+    nrm = z["normalisation"]
+    net.set_normalisation(nrm[0], nrm[1], nrm[2])
+    res = SG.evaluate(net, side, checkpoints=(4000, 8000, 16000))
+    net.close()
+    rows = res["checkpoints"]
+    return {"speedup": res["speedup"], "t": [2000, 16000], "lattice": [side, side], "seed": 1000,
+            "windows": sum(r["windows"] for r in rows), "fallbacks": res["fallbacks"],
+            "L_rel_err": [abs(r["L_surrogate"] - r["L_plain"]) / r["L_plain"] for r in rows],
+            "S_rel_l2": [r["S_rel_l2"] for r in rows], "checkpoints": [r["t"] for r in rows],
+            "ms_plain": res["ms_plain"], "ms_surrogate": res["ms_surrogate"],
+            "weights": os.path.relpath(SURR_WEIGHTS, ROOT)}
 
 
 def main():
@@ -743,6 +776,8 @@ def main():
     ap.add_argument("--side3d", type=int, default=D3_SIDE,
                     help="3D lattice side (the workload is 256; smaller sides are for profiling)")
     ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--no-fixed-error", action="store_true",
+                    help="surrogate workload: skip the trained network's speedup-at-fixed-error run")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -332,6 +332,60 @@ __global__ void staging_from_state_kernel(const float *__restrict__ x, long long
   stg[3 * S + s] = (double)x[s * 4 + 2];
 }
 
+// Rebuild of a 2D FP32-deviation lattice (T = 1/3, body force off) from a
+// network state, in FP32: mu = a phi + b phi^3 - kappa lap_D phi (Eqs. 5, 31)
+// of the shifted phi on every site, then per site F = -phi d_D mu (Eqs. 28,
+// 30), the velocity u = u* - F / 2n (Eq. 18) and f_i - w_i = f_i^eq(n, u) - w_i
+// (Eq. 15) stored at r - e_i (pull layout), and phi.  The same construction
+// as the library's initialisation, which runs in FP64.
+__device__ __forceinline__ int wrap_1(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+__global__ void rebuild_mu_kernel(const float *__restrict__ x, hlbm::KParams<float> p, float shift,
+                                  float *__restrict__ mu) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int Lx = p.Lx, Ly = p.Ly;
+  if (s >= (long long)Lx * Ly) return;
+  const int xx = (int)(s % Lx), yy = (int)(s / Lx);
+  auto ph = [&](int dx, int dy) {
+    return x[4 * ((long long)wrap_1(yy + dy, Ly) * Lx + wrap_1(xx + dx, Lx))] - shift;
+  };
+  const float c = ph(0, 0);
+  float lap = p.R * ph(-1, -1);
+  lap += p.Q * ph(0, -1);
+  lap += p.R * ph(1, -1);
+  lap += p.Q * ph(-1, 0);
+  lap += p.C0 * c;
+  lap += p.Q * ph(1, 0);
+  lap += p.R * ph(-1, 1);
+  lap += p.Q * ph(0, 1);
+  lap += p.R * ph(1, 1);
+  mu[s] = p.a * c + p.b * c * c * c - p.kappa * lap;
+}
+
+__global__ void rebuild_pop_kernel(const float *__restrict__ x, const float *__restrict__ mu,
+                                   hlbm::KParams<float> p, float shift, float *__restrict__ hout,
+                                   float *__restrict__ phiout) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int Lx = p.Lx, Ly = p.Ly;
+  const long long S = (long long)Lx * Ly;
+  if (s >= S) return;
+  const int xx = (int)(s % Lx), yy = (int)(s / Lx);
+  auto m = [&](int dx, int dy) { return mu[(long long)wrap_1(yy + dy, Ly) * Lx + wrap_1(xx + dx, Lx)]; };
+  const float gmx = p.N * (m(1, 0) - m(-1, 0)) + p.M * ((m(1, -1) - m(-1, -1)) + (m(1, 1) - m(-1, 1)));
+  const float gmy = p.N * (m(0, 1) - m(0, -1)) + p.M * ((m(-1, 1) - m(-1, -1)) + (m(1, 1) - m(1, -1)));
+  const float ph = x[4 * s] - shift, n = 1.f + x[4 * s + 3];
+  const float ux = x[4 * s + 1] + ph * gmx / (2.f * n), uy = x[4 * s + 2] + ph * gmy / (2.f * n);
+  const float uu = ux * ux + uy * uy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int ex = hlbm::q9_ex(i), ey = hlbm::q9_ey(i);
+    const float eu = ex * ux + ey * uy;
+    const float h = float(hlbm::q9_w(i)) * ((n - 1.f) + n * (3.f * eu + 4.5f * eu * eu - 1.5f * uu));
+    hout[i * S + (long long)wrap_1(yy - ey, Ly) * Lx + wrap_1(xx - ex, Lx)] = h;
+  }
+  phiout[s] = ph;
+}
+
 // |phi| <= cap on the predicted state (the bulk value of the state the
 // window starts from bounds phi under the Cahn-Hilliard dynamics)
 __global__ void clamp_phi_kernel(float *__restrict__ x, long long S, float cap) {
@@ -827,6 +881,22 @@ int lbm_surrogate_advance_relaxed(lbm_handle *h, lbm_net *net, int windows, int 
     NCK(net, cudaMalloc(&net->bk, h->hbytes + h->phibytes), "cudaMalloc");
     net->bk_cap = h->hbytes + h->phibytes;
   }
+  // the predicted state net->x1 (phi shifted down by `shift`) becomes the
+  // lattice's state at its current buffer parity
+  auto rebuild = [&](double shift) -> int {
+    if (h->P.precision == LBM_F32DEV && h->P.T == 1.0 / 3.0) {
+      const KParams<float> kp = make_params<float>(h, 0);
+      rebuild_mu_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, kp, (float)shift, net->yout);
+      rebuild_pop_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, net->yout, kp, (float)shift,
+                                                       static_cast<float *>(h->h[h->cur]),
+                                                       static_cast<float *>(h->phi[h->cur]));
+      NCK(net, cudaGetLastError(), "rebuild kernels");
+      return LBM_OK;
+    }
+    staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift, h->staging);
+    NCK(net, cudaGetLastError(), "staging kernel");
+    return launch_init(h, h->cur) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+  };
   // sums and maxima (NSTAT each) of a state array, reduced on the host
   std::vector<double> part(NSTAT * sb);
   auto stats_of = [&](const float *x, double (&out)[NSTAT]) -> int {
@@ -868,10 +938,7 @@ int lbm_surrogate_advance_relaxed(lbm_handle *h, lbm_net *net, int windows, int 
       NCK(net, cudaMemcpyAsync(bk, h->h[cur_start], h->hbytes, cudaMemcpyDeviceToDevice, s), "copy");
       NCK(net, cudaMemcpyAsync(bk + h->hbytes, h->phi[cur_start], h->phibytes, cudaMemcpyDeviceToDevice, s),
           "copy");
-      const double shift0 = conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0;
-      staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift0, h->staging);
-      NCK(net, cudaGetLastError(), "staging kernel");
-      if (launch_init(h, h->cur) != cudaSuccess) return LBM_ECUDA;
+      if ((rc = rebuild(conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0))) return rc;
       h->t += window_steps;
       if ((rc = lbm_step(h, relax_steps))) return rc;
       if ((rc = lbm_surrogate_state(h, net->x1))) return rc;
@@ -908,10 +975,7 @@ int lbm_surrogate_advance_relaxed(lbm_handle *h, lbm_net *net, int windows, int 
         if ((rc = lbm_step(h, window_steps + relax_steps))) return rc;
       }
     } else if (ok) {
-      const double shift = conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0;
-      staging_from_state_kernel<<<nblk(S, 256), 256, 0, s>>>(net->x1, S, shift, h->staging);
-      NCK(net, cudaGetLastError(), "staging kernel");
-      if (launch_init(h, h->cur) != cudaSuccess) return LBM_ECUDA;
+      if ((rc = rebuild(conserve_mass ? (st[1][0] - st[0][0]) / (double)S : 0.0))) return rc;
       h->t += window_steps;
     } else {
       nfb++;

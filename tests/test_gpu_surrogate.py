@@ -261,13 +261,16 @@ def test_surrogate_state_and_fallback():
     for xa, xb in zip(a.moments(), b.moments()):
         assert np.array_equal(xa, xb)
     # a network with all-zero parameters predicts "no change": accepted, and
-    # the state keeps its moments (populations rebuilt from them)
+    # the state keeps its moments (populations rebuilt from them as
+    # f_eq(n, u* - F/2n), whose moments are n and u* again)
     net.set_params(np.zeros(net.nparams, dtype=np.float32))
     before = a.moments()
     fb = lbm.lbm_surrogate_advance(a.handle, net, windows=2, window_steps=50, mass_tol=1e-3)
     after = a.moments()
     assert fb == 0 and a.t == 150
+    np.testing.assert_allclose(after[0], before[0], atol=1e-6)
     np.testing.assert_allclose(after[1], before[1], atol=1e-6)
+    np.testing.assert_allclose(after[2], before[2], atol=1e-7)
     net.close()
 
 
