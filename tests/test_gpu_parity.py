@@ -640,3 +640,46 @@ def test_tma_collide_refused_where_ineligible(monkeypatch):
         monkeypatch.setenv("HLBM_TUNING", "4,16,2,3,0")
         with pytest.raises(lbm.LbmError):
             lbm.Lattice(lbm.LbmParams(Lx=Lx, Ly=Ly, precision=prec, **CFG1))
+
+
+@pytest.mark.parametrize("gx", [1e-5, 3e-5, 5e-5])
+def test_paper_drop_convection_full_size(gx):
+    """Sec. III, Figs. 5-6 at the paper's size: a drop of diameter 64 on 256 x
+    128 (-a = b = 1e-3, kappa = 3e-3, Gamma = 5, tau = 1, OC, dt_FD = dt_LB)
+    pushed by G = n (g_x, 0) for t < 500 over the printed range of g_x, then
+    free: the whole fluid moves at 500 g_x, the drop's centre of mass (Eq. 40)
+    moves with the fluid velocity there (v_CM = v_f within 1 %), and its
+    horizontal and vertical diameters stay within 3 % of each other."""
+    Lx, Ly = 256, 128
+    kw = dict(a=-1e-3, b=1e-3, kappa=3e-3, tau=1.0, Gamma=5.0, N=0.3, Q=2.5)
+    op = O.Params(Lx=Lx, Ly=Ly, m=1, **kw)
+    lp = lbm.LbmParams(Lx=Lx, Ly=Ly, g=(gx, 0.0, 0.0), force_steps=500, fd_substeps=1,
+                       precision=lbm.LBM_F64, **kw)
+    phi = I.drop(2, Lx, Ly, R=32, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, Lx, Ly)
+    lat = lbm.Lattice(lp).init_fields(n, phi, u)
+    lat.step(600)
+    d = lat.diagnostics()
+    xs, vfs = [d["r_cm"][0]], []
+    for _ in range(4):
+        lat.step(100)
+        d = lat.diagnostics()
+        xs.append(d["r_cm"][0])
+        vfs.append(d["v_f"][0])
+    v_cm = np.diff(xs) / 100.0
+    gn, gphi, gu = lat.moments()
+    lat.close()
+    assert np.sum(gn * gu[0]) / np.sum(gn) == pytest.approx(500 * gx, rel=5e-3)
+    np.testing.assert_allclose(np.mean(v_cm), np.mean(vfs), rtol=1e-2)
+    cx, cy = d["r_cm"][0], d["r_cm"][1]
+
+    def width(profile, c):
+        prof = np.roll(profile, len(profile) // 2 - int(round(c)))
+        s = np.sign(prof)
+        idx = np.where(s[:-1] != s[1:])[0]
+        zs = [i + prof[i] / (prof[i] - prof[i + 1]) for i in idx]
+        return zs[-1] - zs[0]
+
+    ratio = width(gphi[int(round(cy)) % Ly], cx) / width(gphi[:, int(round(cx)) % Lx], cy)
+    print(f"g_x {gx}: v_CM {np.mean(v_cm):.4e}, v_f {np.mean(vfs):.4e}, diameter ratio {ratio:.4f}")
+    assert abs(ratio - 1) < 0.03
