@@ -54,6 +54,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # packed-pair collision (launch-shape variant 5).  ncu flushes the caches
 # before a captured launch: these are cold-cache figures.
 NCU_TRAFFIC_1024 = {"fd": ((128, 96, 4, 2), 12.619776e6), "collide": (5, 41.970176e6 + 2.991872e6)}
+# the same collide kernel (variant 5) captured on 2048^2 (4.19 M sites; the
+# lattice no longer fits L2): 168.389120 MB read + 129.996032 MB written per
+# launch = 71.2 B/site; the 4096^2 line scales it by the site count
+NCU_TRAFFIC_COLLIDE_2048 = (5, 168.389120e6 + 129.996032e6)
 METRIC = "MLUPS (D2Q9 hybrid LB + FD step)"
 WORKLOAD = "spinodal-1024x1024-d2q9-f32dev"
 
@@ -401,7 +405,10 @@ def large_lattice(side, stream):
             "lb_steps_timed": 300, "tuning": tuning, "step_roofline": step_roofline(value),
             "collide": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "avg_launch_us": c_s * 1e6, "bytes_per_site": COLLIDE_BYTES_PER_SITE,
-                        "peak_kind": peak_kind},
+                        "peak_kind": peak_kind,
+                        "traffic": (NCU_TRAFFIC_COLLIDE_2048[1] * S / 2048 ** 2
+                                    if tuning["collide_sites_per_thread"] == NCU_TRAFFIC_COLLIDE_2048[0] else None),
+                        "traffic_note": "ncu capture on 2048^2 scaled by the site count"},
             "fd_avg_launch_us": fms / fn * 1000.0, "fd_launches_per_lb_step": fn / 100.0}
 
 
