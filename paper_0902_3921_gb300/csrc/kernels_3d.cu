@@ -592,7 +592,8 @@ __global__ void __launch_bounds__(256)
 // registers.  psi goes to a four-plane shared-memory ring; after one barrier
 // the inner warps form phi^{n+1} = phih + dt Gamma lap psi (Eq. 36) of plane
 // z from the ring.  psi never reaches global memory: a substep moves the
-// advection pass's 20 B/site plus about 12 B/site here, instead of 44 B.
+// advection pass's 20 B/site plus about 12 B/site here, instead of 44 B.  The
+// arithmetic runs on packed FP32 pairs.
 constexpr int F3F_NW = 16;
 
 template <int V>
@@ -615,6 +616,24 @@ __device__ __forceinline__ void xnbr_row(const float4 (&c)[V], float (&l)[V], fl
 // the rows y -+ 1 and phi of plane z + 2) are issued before iteration z
 // computes, so that they are in flight across its barrier (1.16x over
 // loading them at the top of their own iteration).
+// packed FP32 pairs (sites 0,1 and 2,3 of a quad)
+__device__ __forceinline__ float2 pf2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
+// 7-point Laplacian of the quad c (x neighbours l, r of its ends; m, p in z,
+// ym, yp in y) as two packed pairs: the z and y neighbours and the centre as
+// pairs, the x neighbour sums (which straddle the pairs) scalar
+__device__ __forceinline__ void lap7_quad(const float4 &c, const float4 &m, const float4 &p, const float4 &ym,
+                                          const float4 &yp, float l, float r, float2 &lo, float2 &hi) {
+  const float2 m6 = pf2(-6.f, -6.f);
+  lo = pfma(m6, lo2(c), padd(padd(padd(lo2(m), lo2(p)), padd(lo2(ym), lo2(yp))), pf2(l + c.y, c.x + c.z)));
+  hi = pfma(m6, hi2(c), padd(padd(padd(hi2(m), hi2(p)), padd(hi2(ym), hi2(yp))), pf2(c.y + c.w, c.z + r)));
+}
+
 template <int V, int MINB>
 __global__ void __launch_bounds__(F3F_NW * 32, MINB)
     fd3f_kernel(const float *__restrict__ A, const float *__restrict__ G, float *__restrict__ out,
@@ -661,21 +680,16 @@ __global__ void __launch_bounds__(F3F_NW * 32, MINB)
       float *dst = &sq[(z + 1) & 3][warp][0];
 #pragma unroll
       for (int q = 0; q < V; ++q) {
-        float e[4];
+        float2 L[2];
+        lap7_quad(hc[q], hm[q], hp[q], hym[q], hyp[q], l[q], r[q], L[0], L[1]);
+        float2 o[2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float hk = cmp4(hc[q], j);
-          float lap = cmp4(hm[q], j);
-          lap += cmp4(hym[q], j);
-          lap += j == 0 ? l[q] : cmp4(hc[q], j - 1);
-          lap += -6.f * hk;
-          lap += j == 3 ? r[q] : cmp4(hc[q], j + 1);
-          lap += cmp4(hyp[q], j);
-          lap += cmp4(hp[q], j);
-          const float cb = p.cubic_at_half ? hk : cmp4(gc[q], j);
-          e[j] = p.a * hk + p.b * (cb * cb * cb) - p.kappa * lap;
+        for (int k = 0; k < 2; ++k) {
+          const float2 hk = k ? hi2(hc[q]) : lo2(hc[q]);
+          const float2 cb = p.cubic_at_half ? hk : (k ? hi2(gc[q]) : lo2(gc[q]));
+          o[k] = pfma(pf2(p.a, p.a), hk, pfma(pf2(p.b, p.b), pmul(pmul(cb, cb), cb), pmul(pf2(-p.kappa, -p.kappa), L[k])));
         }
-        *reinterpret_cast<float4 *>(dst + 128 * q + 4 * lane) = make_float4(e[0], e[1], e[2], e[3]);
+        *reinterpret_cast<float4 *>(dst + 128 * q + 4 * lane) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
       }
     }
     __syncthreads();
@@ -694,19 +708,11 @@ __global__ void __launch_bounds__(F3F_NW * 32, MINB)
       for (int q = 0; q < V; ++q) {
         const float4 qm = sld((z + 3) & 3, warp, q), qp = sld((z + 1) & 3, warp, q);
         const float4 qym = sld(z & 3, warp - 1, q), qyp = sld(z & 3, warp + 1, q);
-        float e[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float lap = cmp4(qm, j);
-          lap += cmp4(qym, j);
-          lap += j == 0 ? l[q] : cmp4(qc[q], j - 1);
-          lap += -6.f * cmp4(qc[q], j);
-          lap += j == 3 ? r[q] : cmp4(qc[q], j + 1);
-          lap += cmp4(qyp, j);
-          lap += cmp4(qp, j);
-          e[j] = cmp4(hm[q], j) + p.dtG * lap;
-        }
-        *reinterpret_cast<float4 *>(orow + 128 * q + 4 * lane) = make_float4(e[0], e[1], e[2], e[3]);
+        float2 L[2];
+        lap7_quad(qc[q], qm, qp, qym, qyp, l[q], r[q], L[0], L[1]);
+        const float2 g = pf2(p.dtG, p.dtG);
+        const float2 o0 = pfma(g, L[0], lo2(hm[q])), o1 = pfma(g, L[1], hi2(hm[q]));
+        *reinterpret_cast<float4 *>(orow + 128 * q + 4 * lane) = make_float4(o0.x, o0.y, o1.x, o1.y);
       }
     }
     mv(hm, hc);
