@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "lbm_common.cuh"
 
@@ -48,19 +49,43 @@ __host__ __device__ constexpr int col_off(int i) { return q9_ex(i) > 0 ? 3 : (q9
 __host__ __device__ constexpr int box_dx(int i) { return q9_ex(i) > 0 ? -4 : 0; }
 
 constexpr int POP_FLOATS = plane_off(9);
-constexpr int OFF_POP = 128;  // bytes [0, 128): the mbarrier
-constexpr int OFF_PHI = OFF_POP + 4 * POP_FLOATS;
-constexpr int OFF_MU = OFF_PHI + 4 * PHW * PHH;
-constexpr int OFF_PN = OFF_MU + 4 * MUW * MUW;
-constexpr uint32_t TX_BYTES = 4u * (POP_FLOATS + PHW * PHH);
-static_assert(OFF_PHI % 128 == 0 && (4 * plane_off(1)) % 128 == 0 && (4 * plane_off(2)) % 128 == 0,
-              "TMA destinations must be 128-byte aligned");
+
+// Population planes of a 32 x 32 tile for storage type S (FP32 or FP16
+// deviations): a copy's x origin must be a multiple of A = 16 / sizeof(S)
+// elements, so planes pulled from x - 1 start A columns left of the tile and
+// planes pulled from x +- 1 are TT + A wide.  (FP32: the functions above.)
+template <typename S>
+struct TmaGeo {
+  static constexpr int A = 16 / (int)sizeof(S);
+  __host__ __device__ static constexpr int w(int i) { return q9_ex(i) == 0 ? TT : TT + A; }
+  __host__ __device__ static constexpr int off(int i) { return TT * (TT * i + A * nshift(i)); }  // elements
+  __host__ __device__ static constexpr int col(int i) { return q9_ex(i) > 0 ? A - 1 : (q9_ex(i) < 0 ? 1 : 0); }
+  __host__ __device__ static constexpr int dx(int i) { return q9_ex(i) > 0 ? -A : 0; }
+  static constexpr int POP_BYTES = (int)sizeof(S) * off(9);
+  static constexpr int OFF_POP = 128;  // bytes [0, 128): the mbarrier
+  static constexpr int OFF_PHI = OFF_POP + POP_BYTES;
+  static constexpr int OFF_MU = OFF_PHI + 4 * PHW * PHH;
+  static constexpr int OFF_PN = OFF_MU + 4 * MUW * MUW;
+  static constexpr uint32_t TX_BYTES = (uint32_t)(POP_BYTES + 4 * PHW * PHH);
+  static_assert(OFF_PHI % 128 == 0 && ((int)sizeof(S) * off(1)) % 128 == 0 &&
+                    ((int)sizeof(S) * off(2)) % 128 == 0,
+                "TMA destinations must be 128-byte aligned");
+};
+static_assert(TmaGeo<float>::off(9) == POP_FLOATS && TmaGeo<float>::col(1) == col_off(1) &&
+                  TmaGeo<float>::dx(1) == box_dx(1),
+              "FP32 geometry");
 
 // + 128: room to align the dynamic shared-memory base to 128 bytes
-template <bool TGEN>
+template <typename S, bool TGEN>
 constexpr size_t tma_smem() {
-  return 128 + OFF_PN + (TGEN ? 4 * MUW * MUW : 0);
+  return 128 + TmaGeo<S>::OFF_PN + (TGEN ? 4 * MUW * MUW : 0);
 }
+
+// storage <-> compute conversions (FP16 deviations carry the scale 2^s)
+__device__ __forceinline__ float cvt_ld(float v, float) { return v; }
+__device__ __forceinline__ float cvt_ld(__half v, float inv_scale) { return __half2float(v) * inv_scale; }
+__device__ __forceinline__ void cvt_st(float *d, float v, float) { *d = v; }
+__device__ __forceinline__ void cvt_st(__half *d, float v, float scale) { *d = __float2half_rn(v * scale); }
 
 __device__ int g_collide_tma_err = 0;
 
@@ -126,21 +151,22 @@ __device__ __forceinline__ float mu_at(const KParams<float> &p, const float (&w)
   return rn_fma(p.a, c, rn_fma(p.b, c3, rn_mul(-p.kappa, lap)));
 }
 
-template <bool TGEN, int MODE, bool PACK, int MINB>
+template <typename S, bool TGEN, int MODE, bool PACK, int MINB>
 __global__ void __launch_bounds__(256, MINB)
     collide2d_tma_kernel(const __grid_constant__ CUtensorMap map_p32,
                          const __grid_constant__ CUtensorMap map_p36,
-                         const __grid_constant__ CUtensorMap map_phi, const float *__restrict__ hin,
-                         float *__restrict__ hout, const float *__restrict__ phi,
+                         const __grid_constant__ CUtensorMap map_phi, const S *__restrict__ hin,
+                         S *__restrict__ hout, const float *__restrict__ phi,
                          const float *__restrict__ dn, float *__restrict__ uout,
                          double *__restrict__ stg, KParams<float> p) {
+  using G = TmaGeo<S>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *base = smem_raw + ((128u - (su32(smem_raw) & 127u)) & 127u);
   const uint32_t bar = su32(base);
-  float *pops = reinterpret_cast<float *>(base + OFF_POP);
-  float(*sphi)[PHW] = reinterpret_cast<float(*)[PHW]>(base + OFF_PHI);
-  float(*smu)[MUW] = reinterpret_cast<float(*)[MUW]>(base + OFF_MU);
-  float(*spn)[MUW] = reinterpret_cast<float(*)[MUW]>(base + OFF_PN);
+  S *pops = reinterpret_cast<S *>(base + G::OFF_POP);
+  float(*sphi)[PHW] = reinterpret_cast<float(*)[PHW]>(base + G::OFF_PHI);
+  float(*smu)[MUW] = reinterpret_cast<float(*)[MUW]>(base + G::OFF_MU);
+  float(*spn)[MUW] = reinterpret_cast<float(*)[MUW]>(base + G::OFF_PN);
   const int Lx = p.Lx, Ly = p.Ly;
   const long long Sz = (long long)Lx * Ly;
   const int x0 = blockIdx.x * TT, y0 = blockIdx.y * TT;
@@ -156,11 +182,11 @@ __global__ void __launch_bounds__(256, MINB)
   pdl_trigger();
   // 1. the ten copies (one thread), the T != 1/3 pressure by plain loads meanwhile
   if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TX_BYTES)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(G::TX_BYTES)
                  : "memory");
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-      tma_3d(su32(pops + plane_off(i)), plane_w(i) == TT ? &map_p32 : &map_p36, x0 + box_dx(i),
+      tma_3d(su32(pops + G::off(i)), G::w(i) == TT ? &map_p32 : &map_p36, x0 + G::dx(i),
              y0 - q9_ey(i), i, bar);
     tma_2d(su32(&sphi[0][0]), &map_phi, x0 - 4, y0 - 2, bar);
   }
@@ -205,8 +231,7 @@ __global__ void __launch_bounds__(256, MINB)
       }
       if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + TT || ys >= Ly) continue;
       const int sx = wrapi(xs - ex, Lx), sy = wrapi(ys - ey, Ly);
-      pops[plane_off(i) + (ys - y0) * plane_w(i) + (xs - x0) + col_off(i)] =
-          hin[i * Sz + (long long)sy * Lx + sx];
+      pops[G::off(i) + (ys - y0) * G::w(i) + (xs - x0) + G::col(i)] = hin[i * Sz + (long long)sy * Lx + sx];
     }
   }
   __syncthreads();
@@ -298,7 +323,7 @@ __global__ void __launch_bounds__(256, MINB)
       Fy += py;
     }
   };
-  auto pop = [&](int i, int ly) { return pops[plane_off(i) + ly * plane_w(i) + tx + col_off(i)]; };
+  auto pop = [&](int i, int ly) { return cvt_ld(pops[G::off(i) + ly * G::w(i) + tx + G::col(i)], p.inv_scale); };
   const float om = p.tau_inv, keep = 1.f - p.tau_inv;
 
   if constexpr (!PACK) {
@@ -336,7 +361,7 @@ __global__ void __launch_bounds__(256, MINB)
         const float w = float(q9_w(0));
         const float heq = w * (dens - n * (1.5f * usq));
         const float Fi = p.pref * w * (-3.f * uF);
-        hout[s] = keep * h[0] + om * heq + Fi;
+        cvt_st(hout + s, keep * h[0] + om * heq + Fi, p.scale);
       }
       const float base = dens - n * (1.5f * usq);
       const float n3 = 3.f * n, n45 = 4.5f * n;
@@ -351,8 +376,8 @@ __global__ void __launch_bounds__(256, MINB)
         const float odd = w * (n3 * eu);
         const float Feven = w * (pF9 * eu * eF - puF);
         const float Fodd = w * (pF3 * eF);
-        hout[i * Sz + s] = keep * h[i] + om * (even + odd) + (Feven + Fodd);
-        hout[ib * Sz + s] = keep * h[ib] + om * (even - odd) + (Feven - Fodd);
+        cvt_st(hout + i * Sz + s, keep * h[i] + om * (even + odd) + (Feven + Fodd), p.scale);
+        cvt_st(hout + ib * Sz + s, keep * h[ib] + om * (even - odd) + (Feven - Fodd), p.scale);
       }
       uout[s] = ux;
       uout[Sz + s] = uy;
@@ -413,12 +438,12 @@ __global__ void __launch_bounds__(256, MINB)
       }
       const long long s = (long long)ya * Lx + x;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) hout[i * Sz + s] = o[i].x;
+      for (int i = 0; i < 9; ++i) cvt_st(hout + i * Sz + s, o[i].x, p.scale);
       uout[s] = ux.x;
       uout[Sz + s] = uy.x;
       if (row_b) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) hout[i * Sz + s + Lx] = o[i].y;
+        for (int i = 0; i < 9; ++i) cvt_st(hout + i * Sz + s + Lx, o[i].y, p.scale);
         uout[s + Lx] = ux.y;
         uout[Sz + s + Lx] = uy.y;
       }
@@ -749,54 +774,62 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool encode(CUtensorMap *map, void *ptr, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
-            const cuuint32_t *box) {
+bool encode(CUtensorMap *map, CUtensorMapDataType type, void *ptr, int rank, const cuuint64_t *dims,
+            const cuuint64_t *strides, const cuuint32_t *box) {
   auto fn = encode_fn();
   if (fn == nullptr) return false;
   const cuuint32_t ones[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, ptr, dims, strides, box, ones,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+  return fn(map, type, rank, ptr, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // maps per buffer parity b, [6 b + j]: 32 x 32 tiles: j = 0 populations 32 wide, 1 populations
-// 36 wide, 2 phi 40 x 36; 32 x 16 tiles (pipelined kernel): 3, 4 populations, 5 phi 40 x 20
+// 32 + A wide (A = 4 FP32, 8 FP16), 2 phi 40 x 36; 32 x 16 tiles (pipelined kernel, FP32
+// only): 3, 4 populations, 5 phi 40 x 20
 CUtensorMap *maps_of(lbm_handle *h) { return reinterpret_cast<CUtensorMap *>(h->tma_maps); }
 
 bool prepare(lbm_handle *h) {
   if (h->tma_ready) return true;
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  const bool half = h->P.precision == LBM_F16DEV;
+  const cuuint64_t es = half ? 2 : 4;
+  const CUtensorMapDataType pt = half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint32_t A = (cuuint32_t)(16 / es);
   const cuuint64_t Lx = (cuuint64_t)h->P.Lx, Ly = (cuuint64_t)h->P.Ly;
-  const cuuint64_t pd[3] = {Lx, Ly, 9}, ps[2] = {4 * Lx, 4 * Lx * Ly};
+  const cuuint64_t pd[3] = {Lx, Ly, 9}, ps[2] = {es * Lx, es * Lx * Ly};
   const cuuint64_t fd[2] = {Lx, Ly}, fs[1] = {4 * Lx};
-  const cuuint32_t b32[3] = {TT, TT, 1}, b36[3] = {TT + 4, TT, 1}, bphi[2] = {PHW, PHH};
+  const cuuint32_t b32[3] = {TT, TT, 1}, bw[3] = {TT + A, TT, 1}, bphi[2] = {PHW, PHH};
   const cuuint32_t q32[3] = {TT, PY, 1}, q36[3] = {TT + 4, PY, 1}, qphi[2] = {PHW, PPHH};
+  const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUtensorMap *m = maps_of(h);
   for (int b = 0; b < 2; ++b) {
     CUtensorMap *mb = m + 6 * b;
-    if (!encode(&mb[0], h->h[b], 3, pd, ps, b32) || !encode(&mb[1], h->h[b], 3, pd, ps, b36) ||
-        !encode(&mb[2], h->phi[b], 2, fd, fs, bphi) || !encode(&mb[3], h->h[b], 3, pd, ps, q32) ||
-        !encode(&mb[4], h->h[b], 3, pd, ps, q36) || !encode(&mb[5], h->phi[b], 2, fd, fs, qphi))
+    if (!encode(&mb[0], pt, h->h[b], 3, pd, ps, b32) || !encode(&mb[1], pt, h->h[b], 3, pd, ps, bw) ||
+        !encode(&mb[2], f32, h->phi[b], 2, fd, fs, bphi))
+      return false;
+    if (!half && (!encode(&mb[3], f32, h->h[b], 3, pd, ps, q32) || !encode(&mb[4], f32, h->h[b], 3, pd, ps, q36) ||
+                  !encode(&mb[5], f32, h->phi[b], 2, fd, fs, qphi)))
       return false;
   }
   h->tma_ready = true;
   return true;
 }
 
-template <bool TGEN, int MODE, bool PACK, int MINB>
+template <typename S, bool TGEN, int MODE, bool PACK, int MINB>
 cudaError_t launch_one(lbm_handle *h, int in, const KParams<float> &p) {
   const CUtensorMap *m = maps_of(h) + 6 * in;
   dim3 grid((p.Lx + TT - 1) / TT, (p.Ly + TT - 1) / TT), block(32, 256 / 32);
-  const float *hin = static_cast<const float *>(h->h[in]);
-  float *hout = static_cast<float *>(h->h[1 - in]);
+  const S *hin = static_cast<const S *>(h->h[in]);
+  S *hout = static_cast<S *>(h->h[1 - in]);
   const float *phi = static_cast<const float *>(h->phi[in]);
   const float *dn = static_cast<const float *>(h->dn);
   float *u = static_cast<float *>(h->u);
-  auto kern = collide2d_tma_kernel<TGEN, MODE, PACK, MINB>;
+  auto kern = collide2d_tma_kernel<S, TGEN, MODE, PACK, MINB>;
   if (MODE == COLLIDE_STEP)
-    return launch_pdl(kern, grid, block, tma_smem<TGEN>(), h->stream, m[0], m[1], m[2], hin, hout, phi, dn, u,
-                      h->staging, p);
-  kern<<<grid, block, tma_smem<TGEN>(), h->stream>>>(m[0], m[1], m[2], hin, hout, phi, dn, u, h->staging, p);
+    return launch_pdl(kern, grid, block, tma_smem<S, TGEN>(), h->stream, m[0], m[1], m[2], hin, hout, phi, dn,
+                      u, h->staging, p);
+  kern<<<grid, block, tma_smem<S, TGEN>(), h->stream>>>(m[0], m[1], m[2], hin, hout, phi, dn, u, h->staging, p);
   return cudaGetLastError();
 }
 
@@ -825,48 +858,73 @@ cudaError_t launch_pipe(lbm_handle *h, int in, const KParams<float> &p) {
                     static_cast<const float *>(h->dn), static_cast<float *>(h->u), h->sched, p);
 }
 
-template <bool TGEN>
+template <typename S, bool TGEN>
 cudaError_t launch_step(lbm_handle *h, int in, const KParams<float> &p, int variant) {
+  if constexpr (std::is_same<S, float>::value)
+    if (variant == 7) return launch_pipe<TGEN, 4>(h, in, p);
   switch (variant) {
-    case 7: return launch_pipe<TGEN, 4>(h, in, p);
-    case 5: return launch_one<TGEN, COLLIDE_STEP, true, 4>(h, in, p);
-    case 6: return launch_one<TGEN, COLLIDE_STEP, true, 3>(h, in, p);
-    default: return launch_one<TGEN, COLLIDE_STEP, false, 3>(h, in, p);
+    case 5: return launch_one<S, TGEN, COLLIDE_STEP, true, 4>(h, in, p);
+    case 6: return launch_one<S, TGEN, COLLIDE_STEP, true, 3>(h, in, p);
+    default: return launch_one<S, TGEN, COLLIDE_STEP, false, 3>(h, in, p);
   }
+}
+
+template <typename S>
+cudaError_t collide2d_tma_s(lbm_handle *h, int in, int force_on, int mode, int variant) {
+  const KParams<float> p = make_params<float>(h, force_on);
+  const bool tgen = p.cs2mT != 0.f;
+  if (mode == COLLIDE_STEP)
+    return tgen ? launch_step<S, true>(h, in, p, variant) : launch_step<S, false>(h, in, p, variant);
+  return tgen ? launch_one<S, true, COLLIDE_MOMENTS, false, 3>(h, in, p)
+              : launch_one<S, false, COLLIDE_MOMENTS, false, 3>(h, in, p);
+}
+
+template <typename S>
+void configure_s(cudaError_t &e) {
+  auto set = [&](auto fn, size_t smem) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  };
+  set(collide2d_tma_kernel<S, false, COLLIDE_STEP, false, 3>, tma_smem<S, false>());
+  set(collide2d_tma_kernel<S, false, COLLIDE_STEP, true, 4>, tma_smem<S, false>());
+  set(collide2d_tma_kernel<S, false, COLLIDE_STEP, true, 3>, tma_smem<S, false>());
+  set(collide2d_tma_kernel<S, true, COLLIDE_STEP, false, 3>, tma_smem<S, true>());
+  set(collide2d_tma_kernel<S, true, COLLIDE_STEP, true, 4>, tma_smem<S, true>());
+  set(collide2d_tma_kernel<S, true, COLLIDE_STEP, true, 3>, tma_smem<S, true>());
+  set(collide2d_tma_kernel<S, false, COLLIDE_MOMENTS, false, 3>, tma_smem<S, false>());
+  set(collide2d_tma_kernel<S, true, COLLIDE_MOMENTS, false, 3>, tma_smem<S, true>());
 }
 
 }  // namespace
 
-bool collide2d_tma_eligible(const lbm_handle *h) {
-  return h->dims == 2 && h->P.precision == LBM_F32DEV && h->P.Lx % 4 == 0 && h->P.Lx >= TMA_MIN_SIDE &&
-         h->P.Ly >= TMA_MIN_SIDE && h->sched != nullptr && encode_fn() != nullptr;
+bool collide2d_tma_eligible(const lbm_handle *h, int variant) {
+  const bool half = h->P.precision == LBM_F16DEV;
+  if (h->dims != 2 || (h->P.precision != LBM_F32DEV && !half)) return false;
+  if (variant != 3 && variant != 5 && variant != 6 && variant != 7) return false;
+  if (variant == 7 && (half || h->sched == nullptr)) return false;  // the pipelined kernel is FP32
+  return h->P.Lx % (half ? 8 : 4) == 0 && h->P.Lx >= TMA_MIN_SIDE && h->P.Ly >= TMA_MIN_SIDE &&
+         encode_fn() != nullptr;
 }
 
 cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant) {
-  if (!collide2d_tma_eligible(h)) return cudaErrorInvalidValue;
+  if (!collide2d_tma_eligible(h, variant)) return cudaErrorInvalidValue;
   if (!prepare(h)) return cudaErrorInvalidValue;
-  const KParams<float> p = make_params<float>(h, force_on);
-  const bool tgen = p.cs2mT != 0.f;
-  if (mode == COLLIDE_STEP) return tgen ? launch_step<true>(h, in, p, variant) : launch_step<false>(h, in, p, variant);
-  return tgen ? launch_one<true, COLLIDE_MOMENTS, false, 3>(h, in, p)
-              : launch_one<false, COLLIDE_MOMENTS, false, 3>(h, in, p);
+  return h->P.precision == LBM_F16DEV ? collide2d_tma_s<__half>(h, in, force_on, mode, variant)
+                                      : collide2d_tma_s<float>(h, in, force_on, mode, variant);
 }
 
-cudaError_t collide2d_tma_configure() {
+cudaError_t collide2d_tma_configure(int precision) {
   cudaError_t e = cudaSuccess;
-  auto set = [&](auto fn, size_t smem) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  };
-  set(collide2d_tma_kernel<false, COLLIDE_STEP, false, 3>, tma_smem<false>());
-  set(collide2d_tma_kernel<false, COLLIDE_STEP, true, 4>, tma_smem<false>());
-  set(collide2d_tma_kernel<false, COLLIDE_STEP, true, 3>, tma_smem<false>());
-  set(collide2d_tma_kernel<true, COLLIDE_STEP, false, 3>, tma_smem<true>());
-  set(collide2d_tma_kernel<true, COLLIDE_STEP, true, 4>, tma_smem<true>());
-  set(collide2d_tma_kernel<true, COLLIDE_STEP, true, 3>, tma_smem<true>());
-  set(collide2d_tma_pipe_kernel<false, 4>, pipe_smem<false>());
-  set(collide2d_tma_pipe_kernel<true, 4>, pipe_smem<true>());
-  set(collide2d_tma_kernel<false, COLLIDE_MOMENTS, false, 3>, tma_smem<false>());
-  set(collide2d_tma_kernel<true, COLLIDE_MOMENTS, false, 3>, tma_smem<true>());
+  if (precision == LBM_F16DEV) {
+    configure_s<__half>(e);
+    return e;
+  }
+  configure_s<float>(e);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(collide2d_tma_pipe_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pipe_smem<false>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(collide2d_tma_pipe_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pipe_smem<true>());
   return e;
 }
 

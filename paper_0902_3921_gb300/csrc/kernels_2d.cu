@@ -1201,9 +1201,9 @@ cudaError_t collide2d_async_configure() {
 
 template <typename S, typename C>
 cudaError_t collide2d(lbm_handle *h, int in, int force_on, int mode) {
-  if constexpr (std::is_same<S, C>::value && sizeof(C) == 4) {
+  if constexpr (sizeof(C) == 4) {
     // 3, 5, 6, 7: TMA staging (scalar, packed-pair 4 CTAs/SM, packed-pair 3
-    // CTAs/SM, persistent pipelined)
+    // CTAs/SM, persistent pipelined; FP32 and FP16 storage, 7 FP32 only)
     if (h->collide_rows == 3 || (h->collide_rows >= 5 && h->collide_rows <= 7))
       return collide2d_tma(h, in, force_on, mode, h->collide_rows);
   }
@@ -1350,9 +1350,9 @@ cudaError_t collide2d_configure(int precision) {
   if (precision == LBM_F64) return collide2d_async_configure<double>();
   if (precision == LBM_F32DEV) {
     e = collide2d_async_configure<float>();
-    return e == cudaSuccess ? collide2d_tma_configure() : e;
+    return e == cudaSuccess ? collide2d_tma_configure(precision) : e;
   }
-  return cudaSuccess;
+  return collide2d_tma_configure(precision);  // FP16 deviations
 }
 
 cudaError_t fd2d_launch(lbm_handle *h, int in) {

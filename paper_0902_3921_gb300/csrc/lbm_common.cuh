@@ -214,13 +214,13 @@ enum { COLLIDE_STEP = 0, COLLIDE_MOMENTS = 1 };
 template <typename C>
 KParams<C> make_params(const lbm_handle *h, int force_on);
 
-// collide with TMA staging (collide2d_tma.cu): FP32 deviations, Lx % 4 == 0,
-// Lx, Ly >= 64; variant 3: scalar collision, 5 / 6: packed pairs budgeted for
-// 4 / 3 CTAs per SM, 7: persistent and pipelined (step mode; the moments mode
-// is always the scalar kernel)
-bool collide2d_tma_eligible(const lbm_handle *h);
+// collide with TMA staging (collide2d_tma.cu): FP32 or FP16 deviations,
+// Lx % 4 == 0 (FP16: % 8), Lx, Ly >= 64; variant 3: scalar collision, 5 / 6:
+// packed pairs budgeted for 4 / 3 CTAs per SM, 7: persistent and pipelined
+// (FP32; step mode; the moments mode is always the scalar kernel)
+bool collide2d_tma_eligible(const lbm_handle *h, int variant);
 cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant);
-cudaError_t collide2d_tma_configure();
+cudaError_t collide2d_tma_configure(int precision);
 int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
 
 }  // namespace hlbm

@@ -337,7 +337,7 @@ int autotune_2d(lbm_handle *h) {
     if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
         (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV) ||
-         ((v[3] == 3 || (v[3] >= 5 && v[3] <= 7)) && collide2d_tma_eligible(h)))) {
+         collide2d_tma_eligible(h, v[3]))) {
       h->sub = std::min(v[0], h->m);
       h->fd_rows = v[1];
       h->fd_cols = h->P.precision == LBM_F64 ? 2 : v[2];
@@ -449,9 +449,7 @@ int autotune_2d(lbm_handle *h) {
   int best_cr = 2;
   for (int cr : {0, 1, 2, 4, 3, 5, 6, 7}) {
     if (cr < 2 && h->P.precision == LBM_F16DEV) continue;  // cp.async moves >= 4 bytes
-    if (cr >= 5 || cr == 3) {
-      if (!collide2d_tma_eligible(h)) continue;
-    }
+    if ((cr >= 5 || cr == 3) && !collide2d_tma_eligible(h, cr)) continue;
     h->collide_rows = cr;
     const float ms =
         time_launches(h, e0, e1, [&] { return launch_collide(h, 0, 0, COLLIDE_STEP); });

@@ -683,3 +683,50 @@ def test_paper_drop_convection_full_size(gx):
     ratio = width(gphi[int(round(cy)) % Ly], cx) / width(gphi[:, int(round(cx)) % Lx], cy)
     print(f"g_x {gx}: v_CM {np.mean(v_cm):.4e}, v_f {np.mean(vfs):.4e}, diameter ratio {ratio:.4f}")
     assert abs(ratio - 1) < 0.03
+
+
+@pytest.mark.parametrize("variant", [3, 5])
+@pytest.mark.parametrize("size", [(64, 64), (104, 72), (304, 217)])
+def test_tma_collide_fp16_storage(variant, size, monkeypatch):
+    """FP16 deviations (scale 2^10) through the TMA kernel (copies of 32- and
+    40-half boxes, 8-element x origins): against the FP16 register kernel,
+    which stores the same FP16 values and differs only in the FP32
+    arithmetic's order, and loosely against the FP64 oracle."""
+    Lx, Ly = size
+    op, _ = _pair(Lx, Ly, m=4, **CFG1)
+    phi = I.drop(2, Lx, Ly, R=min(Lx, Ly) // 4, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, Lx, Ly)
+    u = u + 0.003 * np.sin(np.arange(Lx) / 4.0)[None, None, :]
+    res = {}
+    for shape in (f"4,80,2,{variant},128", "4,80,2,2,128"):
+        monkeypatch.setenv("HLBM_TUNING", shape)
+        lat = lbm.Lattice(lbm.LbmParams(Lx=Lx, Ly=Ly, fd_substeps=-4, precision=lbm.LBM_F16DEV, **CFG1))
+        lat.init_fields(n, phi, u).step(12)
+        assert lbm.lbm_tuning(lat.handle)["collide_sites_per_thread"] == int(shape.split(",")[3])
+        res[shape] = lat.moments()
+        lat.close()
+    a, b = res[f"4,80,2,{variant},128"], res["4,80,2,2,128"]
+    ref = O.State.create(op, n, phi, u)
+    ref.run(12)
+    rn, ru = ref.moments()
+    umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-4
+    assert np.max(np.abs(a[2] - b[2])) <= 2e-2 * umax
+    assert np.max(np.abs(a[1] - ref.phi)) <= 1e-3
+    assert np.max(np.abs(a[2] - ru)) <= 0.1 * umax
+
+
+def test_tma_collide_fp16_translation_equivariance_bitwise(monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", "4,80,2,5,128")
+    lp = lbm.LbmParams(Lx=128, Ly=96, fd_substeps=-4, precision=lbm.LBM_F16DEV, **CFG1)
+    phi = I.spinodal(2, 128, 96, seed=5)
+    n, u = I.rest(2, 128, 96)
+    res = []
+    for shift in ((0, 0), (32, 64)):
+        lat = lbm.Lattice(lp)
+        lat.init_fields(n, np.roll(phi, shift, axis=(0, 1)), u).step(60)
+        res.append(lat.moments())
+        lat.close()
+    for a, b in zip(res[0], res[1]):
+        axes = (0, 1) if a.ndim == 2 else (1, 2)
+        assert np.array_equal(np.roll(a, (32, 64), axis=axes), b)
