@@ -344,6 +344,8 @@ def run_ours(args, rank, world, local):
         }
         if side == L and not args.no_large:
             line["large_lattice"] = large_lattice(args.large_side, stream)
+            line["f16_storage"] = {"1024": f16_storage(side, 2000, stream),
+                                   str(args.large_side): f16_storage(args.large_side, 200, stream)}
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
@@ -362,6 +364,50 @@ def step_roofline(mlups):
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "bytes_per_site": STEP_BYTES_PER_SITE, "peak_kind": kind,
             "note": "u* (16 B/site written and read between the two kernels) is not counted"}
+
+
+def f16_storage(side, lb_steps, stream):
+    """The same workload with FP16 deviation storage (scale 2^10; FP32
+    arithmetic): whole-step MLUPS over lb_steps LB steps after as many
+    warm-up steps, and the collide kernel's per-launch event time against
+    its 40 B/site (populations 9 x 2 B read and written, phi 4 B)."""
+    import torch
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    S = side * side
+    lat = lbm.Lattice(lbm.LbmParams(Lx=side, Ly=side, fd_substeps=M_SUB, precision=lbm.LBM_F16DEV, **CFG),
+                      stream=stream.cuda_stream)
+    n, u = I.rest(2, side, side)
+    lat.init_fields(n, I.spinodal(2, side, side, seed=0), u)
+    del n, u
+    with torch.cuda.stream(stream):
+        lat.step(lb_steps)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        lat.step(lb_steps)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    lbm.lbm_set_kernel_timing(lat.handle, True)
+    lbm.lbm_kernel_times(lat.handle, reset=True)
+    with torch.cuda.stream(stream):
+        lat.step(min(lb_steps, 200))
+    kt = lbm.lbm_kernel_times(lat.handle, reset=True)
+    tuning = lbm.lbm_tuning(lat.handle)
+    lat.close()
+    (cms, cn), (fms, fn) = kt["collide"], kt["fd"]
+    c_s = cms / cn / 1000.0
+    peak, peak_kind = measured_peak()
+    ach = 40 * S / c_s / 1e9
+    return {"lattice": [side, side], "value": S * lb_steps / (ms / 1000.0) / 1e6, "unit": "MLUPS",
+            "lb_steps_timed": lb_steps, "precision": "f16 deviations (scale 2^10), f32 arithmetic",
+            "tuning": tuning,
+            "collide": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "avg_launch_us": c_s * 1e6, "bytes_per_site": 40, "peak_kind": peak_kind},
+            "fd_avg_launch_us": fms / fn * 1000.0}
 
 
 def large_lattice(side, stream):
