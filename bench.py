@@ -610,7 +610,9 @@ def run_drop3d(args, rank, world, local):
                              "pass)" if S3 in (128, 256) else
                              "fd3d (m = 8 substeps, three passes each: phih, psi, phi)"),
                   "bytes_per_site": D3_M * D3_FD_BYTES, "avg_launch_us": f_s * 1e6,
-                  "note": f"avg_launch_us covers the {fn} FD launches of one LB step",
+                  "note": ("avg_launch_us covers all FD launches of one LB step (8 substeps x "
+                           "(advection + fused pass))" if S3 in (128, 256) else
+                           "avg_launch_us covers all FD launches of one LB step (8 substeps x 3 passes)"),
                   "peak_kind": peak_kind, "share_of_step": fms / (cms + fms)}
         dom, oth = (roof_c, roof_f) if cms >= fms else (roof_f, roof_c)
         out[name] = {"value": value, "ms_per_step": ms, "roofline": dom, "roofline_other_kernel": oth,
