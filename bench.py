@@ -69,6 +69,18 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job_mlups(ms_local, world, site_updates_per_rank, dist=None, device="cuda"):
+    """Whole-job throughput of `world` replicas: every rank did
+    site_updates_per_rank lattice updates; the job took the slowest rank's
+    time (the maximum over ranks).  Returns (MLUPS, that time in ms)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * site_updates_per_rank / (ms_max / 1000.0) / 1e6, ms_max
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -233,11 +245,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
     barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * S * LB_PER_STEP * args.steps / (ms_max / 1000.0) / 1e6
+    value, ms_max = whole_job_mlups(ms, world, S * LB_PER_STEP * args.steps, dist, "cuda")
     tuning = lbm.lbm_tuning(lat.handle)
     if args.quick:
         # profiling runs: the timed region only

@@ -51,3 +51,38 @@ def test_cuda_arm_refuses_without_a_gpu():
     r = _bench("--steps", "1", "--warmup", "3")
     assert r.returncode != 0
     assert "needs a CUDA GPU" in (r.stdout + r.stderr)
+
+
+def _replica_rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    value, ms_max = bench.whole_job_mlups(10.0 * (rank + 1), world, 100 * 1000, dist, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((rank, value, ms_max))
+
+
+def test_whole_job_throughput_over_gloo_ranks():
+    """Two replicas on the CPU (gloo): the job's time is the slowest rank's
+    (20 ms) on every rank, and the value counts both ranks' updates."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_replica_rank, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    for rank, value, ms_max in res:
+        assert ms_max == 20.0
+        assert value == pytest.approx(2 * 100 * 1000 / 0.020 / 1e6)
