@@ -80,30 +80,49 @@ __global__ void __launch_bounds__(256, MINB)
   C hv[19], hn[19];
   if (z0 < Lz) load_plane(hv, z0);
   const bool big = Lx >= PX && Ly >= PY && Lz >= PZ;
-  for (int k = tid; k < PX * PY * PZ; k += 256) {
-    const int rz = k / (PX * PY), rem = k - rz * PX * PY, ry = rem / PX, rx = rem - ry * PX;
+  // phi on the tile + halo 2: one (x, y) column per thread, the z loop inside
+  for (int k = tid; k < PX * PY; k += 256) {
+    const int ry = k / PX, rx = k - ry * PX;
     const int gx = big ? wrap1_3(x0 + rx - 2, Lx) : wrapi(x0 + rx - 2, Lx);
     const int gy = big ? wrap1_3(y0 + ry - 2, Ly) : wrapi(y0 + ry - 2, Ly);
-    const int gz = big ? wrap1_3(z0 + rz - 2, Lz) : wrapi(z0 + rz - 2, Lz);
-    sphi[rz][ry][rx] = phi[((long long)gz * Ly + gy) * Lx + gx];
+    const C *col = phi + (long long)gy * Lx + gx;
+#pragma unroll 4
+    for (int rz = 0; rz < PZ; ++rz) {
+      const int gz = big ? wrap1_3(z0 + rz - 2, Lz) : wrapi(z0 + rz - 2, Lz);
+      sphi[rz][ry][rx] = col[(long long)gz * pl];
+    }
   }
   __syncthreads();
-  for (int k = tid; k < MX * MY * MZ; k += 256) {
-    const int mz = k / (MX * MY), rem = k - mz * MX * MY, my = rem / MX, mx = rem - my * MX;
-    const int cz = mz + 1, cy = my + 1, cx = mx + 1;
-    const C c = sphi[cz][cy][cx];
-    const C faces = ((sphi[cz][cy][cx - 1] + sphi[cz][cy][cx + 1]) +
-                     (sphi[cz][cy - 1][cx] + sphi[cz][cy + 1][cx])) +
-                    (sphi[cz - 1][cy][cx] + sphi[cz + 1][cy][cx]);
-    const C edges =
-        ((sphi[cz][cy - 1][cx - 1] + sphi[cz][cy - 1][cx + 1]) +
-         (sphi[cz][cy + 1][cx - 1] + sphi[cz][cy + 1][cx + 1])) +
-        ((sphi[cz - 1][cy][cx - 1] + sphi[cz - 1][cy][cx + 1]) +
-         (sphi[cz + 1][cy][cx - 1] + sphi[cz + 1][cy][cx + 1])) +
-        ((sphi[cz - 1][cy - 1][cx] + sphi[cz - 1][cy + 1][cx]) +
-         (sphi[cz + 1][cy - 1][cx] + sphi[cz + 1][cy + 1][cx]));
-    const C lap = p.Q * faces + p.R * edges + p.C0 * c;
-    smu[mz][my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
+  // mu on the tile + 1: one (x, y) column per thread marching in z, the 3 x 3
+  // neighbourhoods of phi on planes z - 1, z, z + 1 in registers (9 new
+  // loads per site)
+  for (int k = tid; k < MX * MY; k += 256) {
+    const int my = k / MX, mx = k - my * MX, cy = my + 1, cx = mx + 1;
+    C w[3][3][3];  // [plane][dy][dx]
+#pragma unroll
+    for (int pz = 0; pz < 2; ++pz)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) w[pz + 1][a][b] = sphi[pz][cy - 1 + a][cx - 1 + b];
+#pragma unroll 2
+    for (int mz = 0; mz < MZ; ++mz) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          w[0][a][b] = w[1][a][b];
+          w[1][a][b] = w[2][a][b];
+          w[2][a][b] = sphi[mz + 2][cy - 1 + a][cx - 1 + b];
+        }
+      const C c = w[1][1][1];
+      const C faces = ((w[1][1][0] + w[1][1][2]) + (w[1][0][1] + w[1][2][1])) + (w[0][1][1] + w[2][1][1]);
+      const C edges = ((w[1][0][0] + w[1][0][2]) + (w[1][2][0] + w[1][2][2])) +
+                      ((w[0][1][0] + w[0][1][2]) + (w[2][1][0] + w[2][1][2])) +
+                      ((w[0][0][1] + w[0][2][1]) + (w[2][0][1] + w[2][2][1]));
+      const C lap = p.Q * faces + p.R * edges + p.C0 * c;
+      smu[mz][my][mx] = p.a * c + p.b * c * c * c - p.kappa * lap;
+    }
   }
   __syncthreads();
 
