@@ -1,6 +1,6 @@
 """FP64 reference of the learned surrogate: a stack of periodic 3x3
 convolutions (ReLU between layers, none after the last), its gradients, the
-MSE loss, one Adam step, and the observables that judge the surrogate against
+MSE loss, one Adam step, and the observables that compare the surrogate with
 the plain scheme (structure factor S(k), domain size L(t), mass drift).
 
 TEST INFRASTRUCTURE ONLY (the tests, the package smoke check and the CPU
@@ -11,7 +11,7 @@ Layouts: activations NHWC [N][H][W][C]; a layer's weights [Cout][3][3][Cin]
 (tap index (dy + 1, dx + 1)), biases [Cout].  The convolution is periodic:
     y[n, h, w, co] = b[co] + sum_{dy, dx, ci} x[n, h + dy, w + dx, ci] W[co, dy+1, dx+1, ci]
 with indices wrapped.  The paper has no counterpart of this network; it is
-the learned-surrogate extension, judged by the paper's observables.
+the learned-surrogate extension, measured with the paper's observables.
 """
 from __future__ import annotations
 
