@@ -128,6 +128,25 @@ def test_flat_interface_profile():
     assert errs[(1.0, 0.14)] / errs[(1.0, 0.56)] > 3.3, errs
 
 
+def test_flat_interface_profile_3d():
+    """The same relaxation in 3D (D3Q19, stencil weights N = 1/6, Q = 1/3, the
+    7-point Laplacian in Eq. 36, m = 8) on a quasi-1D 48 x 4 x 4 lattice: the
+    profile reaches phi0 tanh(x/xi) within the 2D band, stays exactly flat
+    along y and z, and the velocities decay."""
+    p = O.Params(dims=3, Lx=48, Ly=4, Lz=4, **{**CFG1, "N": 1 / 6, "Q": 1 / 3, "m": 8})
+    phi0, xi = O.phi0_of(p), O.xi_of(p)
+    phi = I.flat_interface(3, 48, 4, 4, phi0=phi0, xi=xi / 2)
+    n, u = I.rest(3, 48, 4, 4)
+    st = O.State.create(p, n, phi, u)
+    st.run(3000)
+    exact = I.flat_interface(3, 48, 4, 4, phi0=phi0, xi=xi)
+    err = np.max(np.abs(st.phi - exact))
+    assert 0.015 < err < 0.025, err
+    assert np.max(np.abs(st.phi - st.phi[:1, :1])) < 1e-12
+    _, uu = st.moments()
+    assert np.max(np.abs(uu)) < 5e-6
+
+
 @pytest.mark.slow
 def test_laplace_law():
     """Drop of radius 16 on 64^2 (the FP64 drop configuration, 2000 steps):
