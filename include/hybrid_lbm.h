@@ -169,11 +169,14 @@ long long lbm_time(const lbm_handle *h);       /* current LB step t, or -1     *
 
 /* The launch shapes picked by the autotuner of lbm_create (2D; it times the
  * candidates with CUDA events on the handle's own buffers): writes up to n of
- * {FD substeps per launch, FD output rows per warp, FD columns per lane,
- * collide sites per thread (0 / 1: asynchronous shared-memory staging sized
- * for 4 / 3 CTAs per SM), m, FD
- * kernel (0: warp-marching; 32 or 64: shared-memory tile of that width)} into
- * values and returns 6 (EINVAL on NULL).
+ * {FD substeps per launch, FD output rows per warp (block kernel: region
+ * rows), FD columns per lane (block kernel: warps / 8), collide kernel (0 / 1:
+ * cp.async staging sized for 4 / 3 CTAs per SM; 2 / 4: sites per thread of
+ * the register kernel; 3, 5, 6: TMA staging with the scalar collision or the
+ * packed-pair collision for 4 / 3 CTAs per SM, FP32 and FP16 storage; 7:
+ * persistent pipelined TMA kernel, FP32), m, FD kernel (0: warp-marching;
+ * 32 or 64: shared-memory tile of that width; 128: block kernel)} into values
+ * and returns 6 (EINVAL on NULL).
  * Environment: HLBM_TUNING="sub,rows,cols,collide_rows[,tile]" fixes the shapes
  * instead of timing them (reproducible profiling); HLBM_TUNE_VERBOSE=1 prints
  * every candidate's time to stderr. */
