@@ -758,3 +758,40 @@ def test_laplace_law_3d_drop_64():
           f"ratio {np.mean(dps) / laplace:.4f}, R_eff {d['R_eff']:.3f}")
     np.testing.assert_allclose(np.mean(dps), laplace, rtol=0.06)
     assert d["u_max"] < 2e-3
+
+
+def test_drop3d_full_size_sampled():
+    """The 3D drop workload at its full size and in its benchmark launch
+    configuration (256^3, R = 48, D3Q19, N = 1/6, Q = 1/3, m chosen by the
+    library = 8, the fused fd3f FD kernel of Lx = 256), with a uniform flow
+    (0.01, -0.005, 0.007) added so that advection acts along every axis:
+    after one LB step, the 36^3 inner blocks of three 96^3 boxes (on the
+    drop's interface along x and along z, and one wrapping around all three
+    faces) against the oracle run on those boxes (sampled parity: the inner
+    block is exact, tests/test_oracle_boxes.py).  FP32 deviations to the
+    64^3 test's bar, FP16 deviations to theirs."""
+    from sampling import box_oracle
+    L, W, steps = 256, 96, 1
+    kw = dict(CFG1, N=1 / 6, Q=1 / 3)
+    op = O.Params(dims=3, Lx=L, Ly=L, Lz=L, m=8, **kw)
+    phi = I.drop(3, L, L, L, R=48, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(3, L, L, L)
+    for k, v in enumerate((0.01, -0.005, 0.007)):
+        u[k] += v
+    boxes = [box_oracle(dict(kw, m=8), n, phi, u, c, W, steps)
+             for c in ((128, 128, 176), (80, 128, 128), (2, 250, 5))]  # (z, y, x)
+    for prec, bphi, bu in ((lbm.LBM_F32DEV, 1e-5, 1e-3), (lbm.LBM_F16DEV, 1e-2, 0.2)):
+        lat = lbm.Lattice(lbm.LbmParams(dims=3, Lx=L, Ly=L, Lz=L, precision=prec, **kw))
+        assert lat.m == 8
+        lat.init_fields(n, phi, u).step(steps)
+        gn, gphi, gu = lat.moments()
+        lat.close()
+        for inner, rn, rphi, ru in boxes:
+            ix = np.ix_(*inner)
+            dphi = float(np.max(np.abs(gphi[ix] - rphi)))
+            du = float(np.max(np.abs(np.stack([gu[k][ix] for k in range(3)]) - ru)))
+            dn = float(np.max(np.abs(gn[ix] - rn)))
+            umax = float(np.max(np.abs(ru)))
+            print(f"256^3 sampled, precision {prec}: |dphi|={dphi:.3e} |du|={du:.3e} "
+                  f"|dn|={dn:.3e} umax={umax:.3e}")
+            assert dphi <= bphi and du <= bu * umax and dn <= 10 * bphi, (prec, dphi, du, dn)
