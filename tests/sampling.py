@@ -7,10 +7,11 @@ per substep (upwind advection and the central divergence of u* 1, the two
 Laplacians of Eq. 36 1 each), so phi(t + 1) depends on phi(t) and u*(t)
 within 3m; u*(t) depends on phi(t) within 2 (the half-force shift, F of
 Eq. 28 with the stencil gradient of mu); the moments at t + 1 add the force
-at t + 1 (2 more) and the pull stream 1.  An output at distance more than
-steps x (3m + 6) from the box's faces therefore depends only on inputs inside
-the box, which the box's false periodic boundary has not changed: such sites
-are exact samples of the full lattice's evolution.  `test_oracle_boxes`
+at t + 1 (2 more, which covers the pull stream's 1): 3m + 4 per step.  An
+output at distance more than steps x (3m + 6) (a margin of 2) from the box's
+faces therefore depends only on inputs inside the box, which the box's false
+periodic boundary has not changed: such sites are exact samples of the full
+lattice's evolution.  `test_oracle_boxes`
 checks this bound against whole-lattice runs."""
 import numpy as np
 
@@ -18,8 +19,8 @@ import oracle as O
 
 
 def reach(m: int, steps: int) -> int:
-    """Distance (in sites, along any axis) an LB step with m FD substeps can
-    carry information, times the number of steps, with a margin of 2."""
+    """Distance (in sites, along any axis) that `steps` LB steps with m FD
+    substeps can carry information, with a margin of 2 per step."""
     return steps * (3 * m + 6)
 
 
