@@ -197,7 +197,10 @@ int lbm_kernel_times(lbm_handle *h, double *ms, long long *launches, int reset);
 
 /* Raw checkpoint: header (magic, version, parameters, t, precision, CRC32)
  * followed by the device state.  lbm_load needs a handle created with equal
- * parameters and restores t; it returns EINVAL on a mismatch or bad CRC. */
+ * parameters and restores t.  A file it cannot use (unreadable, another
+ * format or version, other parameters, truncated, CRC mismatch) returns
+ * EINVAL without latching: the handle stays usable and lbm_last_error names
+ * the reason. */
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
 

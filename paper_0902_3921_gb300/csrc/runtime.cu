@@ -102,6 +102,13 @@ int fail(lbm_handle *h, int code, const std::string &msg) {
   return code;
 }
 
+// A refusal that leaves the handle usable: the text is kept for
+// lbm_last_error, nothing is latched.
+int refuse(lbm_handle *h, int code, const std::string &msg) {
+  if (h->err == 0) h->msg = msg;
+  return code;
+}
+
 int cuda_fail(lbm_handle *h, cudaError_t e, const char *what) {
   return fail(h, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
@@ -814,19 +821,23 @@ int lbm_load(lbm_handle *h, const char *path) {
   if (rc) return rc;
   if (!path) return fail(h, LBM_EINVAL, "lbm_load: NULL path");
   FILE *fp = std::fopen(path, "rb");
-  if (!fp) return LBM_EINVAL;
+  if (!fp) return refuse(h, LBM_EINVAL, std::string("lbm_load: cannot open ") + path);
   CkptHeader hd;
   std::vector<unsigned char> buf;
-  bool ok = std::fread(&hd, sizeof hd, 1, fp) == 1 && std::memcmp(hd.magic, "HLBMCKP", 8) == 0 &&
-            hd.version == 1 && hd.payload == (long long)(h->hbytes + h->phibytes) &&
-            same_params(hd.P, h->P);
-  if (ok) {
+  const char *why = nullptr;
+  if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "HLBMCKP", 8) != 0 ||
+      hd.version != 1)
+    why = "not a version-1 checkpoint";
+  else if (hd.payload != (long long)(h->hbytes + h->phibytes) || !same_params(hd.P, h->P))
+    why = "written by a handle with other parameters";
+  if (!why) {
     buf.resize(hd.payload);
-    ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size() &&
-         crc32_update(0, buf.data(), buf.size()) == hd.crc;
+    if (std::fread(buf.data(), 1, buf.size(), fp) != buf.size()) why = "truncated";
+    else if (crc32_update(0, buf.data(), buf.size()) != hd.crc) why = "CRC mismatch";
   }
   std::fclose(fp);
-  if (!ok) return LBM_EINVAL;  // a bad file does not poison the handle
+  // a bad file does not poison the handle
+  if (why) return refuse(h, LBM_EINVAL, std::string("lbm_load: ") + path + ": " + why);
   CK(h, cudaMemcpyAsync(h->h[0], buf.data(), h->hbytes, cudaMemcpyHostToDevice, h->stream),
      "host-to-device copy");
   CK(h, cudaMemcpyAsync(h->phi[0], buf.data() + h->hbytes, h->phibytes, cudaMemcpyHostToDevice,

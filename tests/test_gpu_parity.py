@@ -461,6 +461,10 @@ def test_checkpoint_roundtrip_bitwise(tmp_path):
     raw[-5] ^= 0xFF
     open(path, "wb").write(bytes(raw))
     assert lbm.lbm_load(b.handle, path) == lbm.LBM_EINVAL
+    assert "CRC mismatch" in lbm.load_library().lbm_last_error(b.handle).decode()
+    b.step(1)
+    assert lbm.lbm_load(b.handle, str(tmp_path / "missing.bin")) == lbm.LBM_EINVAL
+    assert "cannot open" in lbm.load_library().lbm_last_error(b.handle).decode()
     b.step(1)
 
 
