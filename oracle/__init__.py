@@ -10,8 +10,10 @@ with ``-ffp-contract=off``); this module builds it with gcc, loads it with
 ctypes and adds the FP64 diagnostics of Sec. III (sums, maximum spurious
 speed, Laplace pressure jump, centre of mass) in plain numpy.
 
-parity unpinned: the 3D (D3Q19) stencil weights generalise Eqs. 30-31, which
-the paper states for 2D only.
+The 3D (D3Q19) stencil weights generalise Eqs. 30-31, which the paper states
+for 2D only: no printed 3D value exists, and the 3D operators are pinned by
+closed forms (polynomial exactness, Fourier symbols, the flat interface of
+Eq. 2 in 3D) instead.
 """
 from __future__ import annotations
 

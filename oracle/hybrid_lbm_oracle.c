@@ -25,10 +25,11 @@
  *   - within one LB step both halves read the state at time t: the LB update
  *     uses phi(t), the FD update uses u*(t) (explicit operator splitting).
  *
- * parity unpinned: the D3Q19 stencil weights of orc_stencil_weights (3D
- * branch) generalise Eqs. 30-31, which the paper gives in 2D only; they are
- * checked for consistency (exact first/second derivatives of low-order
- * polynomials, Fourier symbols) but no printed 3D value exists to pin them.
+ * The D3Q19 stencil weights of orc_stencil_weights (3D branch) generalise
+ * Eqs. 30-31, which the paper gives in 2D only, so no printed 3D value exists.
+ * The 3D operators are pinned by closed forms instead: exact first and second
+ * derivatives of low-order polynomials, their Fourier symbols, and the flat
+ * interface relaxing to phi0 tanh(x/xi) of Eq. 2 in 3D.
  */
 #include <math.h>
 #include <stdlib.h>
