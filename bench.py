@@ -609,6 +609,12 @@ def run_drop3d(args, rank, world, local):
         kt = lbm.lbm_kernel_times(lat.handle, reset=True)
         lbm.lbm_set_kernel_timing(lat.handle, False)
         (cms, cn), (fms, fn) = kt["collide"], kt["fd"]
+        if S3 in (128, 256) and os.environ.get("HLBM_FD3_FUSED_ADV"):
+            fd_kind = "fd3g (m = 8 substeps, one kernel each: advection, psi and the new phi)"
+        elif S3 in (128, 256):
+            fd_kind = "fd3d (m = 8 substeps, each an advection pass and a fused psi / new-phi pass)"
+        else:
+            fd_kind = "fd3d (m = 8 substeps, three passes each: phih, psi, phi)"
         c_s, f_s = cms / cn / 1000.0, fms / fn / 1000.0  # f_s: all FD launches of one LB step
         ac = D3_COLLIDE_BYTES[name] * S / c_s / 1e9
         af = D3_M * D3_FD_BYTES * S / f_s / 1e9
@@ -617,13 +623,9 @@ def run_drop3d(args, rank, world, local):
                   "avg_launch_us": c_s * 1e6, "peak_kind": peak_kind, "share_of_step": cms / (cms + fms)}
         roof_f = {"bound": "hbm", "achieved": af, "peak": peak, "unit": "GB/s", "frac": af / peak,
                   "traffic": None,
-                  "kernel": ("fd3d (m = 8 substeps, each an advection pass and a fused psi / new-phi "
-                             "pass)" if S3 in (128, 256) else
-                             "fd3d (m = 8 substeps, three passes each: phih, psi, phi)"),
+                  "kernel": fd_kind,
                   "bytes_per_site": D3_M * D3_FD_BYTES, "avg_launch_us": f_s * 1e6,
-                  "note": ("avg_launch_us covers all FD launches of one LB step (8 substeps x "
-                           "(advection + fused pass))" if S3 in (128, 256) else
-                           "avg_launch_us covers all FD launches of one LB step (8 substeps x 3 passes)"),
+                  "note": f"avg_launch_us covers all FD launches of one LB step ({fn} launches)",
                   "peak_kind": peak_kind, "share_of_step": fms / (cms + fms)}
         dom, oth = (roof_c, roof_f) if cms >= fms else (roof_f, roof_c)
         out[name] = {"value": value, "ms_per_step": ms, "roofline": dom, "roofline_other_kernel": oth,

@@ -489,6 +489,39 @@ __device__ __forceinline__ float cmp4(const float4 &v, int j) {
   return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
+// phih of one site (Eqs. 32-35, or the flux form): phi at the site and its
+// six neighbours, the u* components along each axis at the neighbours that
+// the central divergence (or the face velocities) needs
+template <bool FLUX>
+__device__ __forceinline__ float adv_site(float ph, float pxm, float pxp, float pym, float pyp, float pzm,
+                                          float pzp, float uxm, float ua, float uxp, float vym, float va,
+                                          float vyp, float wzm, float wa, float wzp, float dt) {
+  float tend;
+  if constexpr (!FLUX) {
+    const float dux = (uxp - uxm) / 2.f;
+    const float dpx = ua < 0.f ? pxp - ph : ph - pxm;
+    const float duy = (vyp - vym) / 2.f;
+    const float dpy = va < 0.f ? pyp - ph : ph - pym;
+    const float duz = (wzp - wzm) / 2.f;
+    const float dpz = wa < 0.f ? pzp - ph : ph - pzm;
+    tend = (ph * dux + ua * dpx);
+    tend += (ph * duy + va * dpy);
+    tend += (ph * duz + wa * dpz);
+  } else {
+    auto flux = [&](float cm, float cc, float cp, float fm, float fp) {
+      const float Up = 0.5f * (cc + cp);
+      const float Um = 0.5f * (cm + cc);
+      const float Jp = Up > 0.f ? Up * ph : Up * fp;
+      const float Jm = Um > 0.f ? Um * fm : Um * ph;
+      return Jp - Jm;
+    };
+    tend = flux(uxm, ua, uxp, pxm, pxp);
+    tend += flux(vym, va, vyp, pym, pyp);
+    tend += flux(wzm, wa, wzp, pzm, pzp);
+  }
+  return ph - dt * tend;
+}
+
 template <bool FLUX>
 __global__ void __launch_bounds__(256)
     fd3v_adv_kernel(const float *__restrict__ phi, const float *__restrict__ u,
@@ -518,31 +551,9 @@ __global__ void __launch_bounds__(256)
       const float ph = cmp4(pc, j);
       const float pxm = j == 0 ? pl : cmp4(pc, j - 1), pxp = j == 3 ? pr : cmp4(pc, j + 1);
       const float uxm = j == 0 ? ul : cmp4(uc, j - 1), uxp = j == 3 ? ur : cmp4(uc, j + 1);
-      float tend;
-      if constexpr (!FLUX) {
-        const float ua = cmp4(uc, j), va = cmp4(vc, j), wa = cmp4(wc, j);
-        const float dux = (uxp - uxm) / 2.f;
-        const float dpx = ua < 0.f ? pxp - ph : ph - pxm;
-        const float duy = (cmp4(vyp, j) - cmp4(vym, j)) / 2.f;
-        const float dpy = va < 0.f ? cmp4(pyp, j) - ph : ph - cmp4(pym, j);
-        const float duz = (cmp4(wp, j) - cmp4(wm, j)) / 2.f;
-        const float dpz = wa < 0.f ? cmp4(pp, j) - ph : ph - cmp4(pm, j);
-        tend = (ph * dux + ua * dpx);
-        tend += (ph * duy + va * dpy);
-        tend += (ph * duz + wa * dpz);
-      } else {
-        auto flux = [&](float cm, float cc, float cp, float fm, float fp) {
-          const float Up = 0.5f * (cc + cp);
-          const float Um = 0.5f * (cm + cc);
-          const float Jp = Up > 0.f ? Up * ph : Up * fp;
-          const float Jm = Um > 0.f ? Um * fm : Um * ph;
-          return Jp - Jm;
-        };
-        tend = flux(uxm, cmp4(uc, j), uxp, pxm, pxp);
-        tend += flux(cmp4(vym, j), cmp4(vc, j), cmp4(vyp, j), cmp4(pym, j), cmp4(pyp, j));
-        tend += flux(cmp4(wm, j), cmp4(wc, j), cmp4(wp, j), cmp4(pm, j), cmp4(pp, j));
-      }
-      e[j] = ph - p.dt * tend;
+      e[j] = adv_site<FLUX>(ph, pxm, pxp, cmp4(pym, j), cmp4(pyp, j), cmp4(pm, j), cmp4(pp, j), uxm,
+                            cmp4(uc, j), uxp, cmp4(vym, j), cmp4(vc, j), cmp4(vyp, j), cmp4(wm, j),
+                            cmp4(wc, j), cmp4(wp, j), p.dt);
     }
     if (q.ok)
       *reinterpret_cast<float4 *>(A + ((long long)z * Ly + q.y) * Lx + q.x4) =
@@ -743,6 +754,145 @@ __global__ void __launch_bounds__(F3F_NW * 32, MINB)
   }
 }
 
+// ---- one whole FD substep in one z-marching kernel (Lx = 128 V, V = 1 or 2) ----
+// The advection of Eqs. 32-35 fused with psi and the new phi of Eq. 36: a CTA
+// of F3G_NW warps owns F3G_NW - 4 output rows; warp w owns row y0 - 2 + w,
+// the whole row (V float4 per lane, quad q of lane l at x = 128 q + 4 l; the
+// periodic x neighbours by shuffles), and marches in z.  For plane k every
+// warp advects its row of plane k + 2 (phih, kept in registers for planes
+// k .. k + 2 and copied to a two-plane shared-memory ring for the rows either
+// side); after a barrier warps 1 .. NW - 2 form psi of plane k + 1 into a
+// four-plane ring; after a second barrier warps 2 .. NW - 3 form phi^{n+1} of
+// plane k.  Neither phih nor psi reaches global memory: a substep reads phi
+// and u* and writes the new phi, 20 B/site, against 32 B/site for the
+// advection pass followed by fd3f.  The two barriers per plane make each ring
+// slot's next write come after every read of its previous plane.  Its results
+// equal those of the two-kernel path bitwise, but it is latency-bound (the
+// advection's twelve loads per quad wait within the CTA's barrier phases, and
+// 128 registers leave no room to prefetch them), so it is opt-in
+// (HLBM_FD3_FUSED_ADV).
+constexpr int F3G_NW = 16;
+
+constexpr size_t fd3g_smem_bytes(int V) { return sizeof(float) * 6 * F3G_NW * 128 * V; }
+
+template <bool FLUX, int V, int MINB>
+__global__ void __launch_bounds__(F3G_NW * 32, MINB)
+    fd3g_kernel(const float *__restrict__ G, const float *__restrict__ u, float *__restrict__ out,
+                KParams<float> p, int nz) {
+  constexpr int NW = F3G_NW, W = 128 * V;
+  extern __shared__ __align__(16) float f3g_smem[];
+  float(*sh)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3g_smem);               // [2][NW][W] phih
+  float(*sq)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3g_smem + 2 * NW * W);  // [4][NW][W] psi
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Ly = p.Ly, Lz = p.Lz;
+  const long long plane = (long long)W * Ly, Sz = plane * Lz;
+  const float *vv = u + Sz, *ww = u + 2 * Sz;
+  const int y0 = blockIdx.y * (NW - 4);
+  const int yr = y0 - 2 + warp;  // this warp's row (wrapped below)
+  const int y = wrapi(yr, Ly), ym = wrapi(yr - 1, Ly), yp = wrapi(yr + 1, Ly);
+  const bool psiw = warp >= 1 && warp <= NW - 2;              // warp-uniform
+  const bool outw = warp >= 2 && warp <= NW - 3 && yr < Ly;   // warp-uniform
+  const int z0 = blockIdx.z * nz, z1 = min(z0 + nz, Lz);
+  auto g4 = [&](const float *f, int yy, int zz, int x) {
+    return __ldg(reinterpret_cast<const float4 *>(f + wrapi(zz, Lz) * plane + (long long)yy * W + x));
+  };
+  auto mv = [](float4 (&d)[V], const float4 (&s2)[V]) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) d[q] = s2[q];
+  };
+  // phih of this warp's row on plane zz
+  auto advect = [&](int zz, float4 (&h)[V]) {
+    float4 pc[V], uc[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      pc[q] = g4(G, y, zz, 128 * q + 4 * lane);
+      uc[q] = g4(u, y, zz, 128 * q + 4 * lane);
+    }
+    float pl[V], pr[V], ul[V], ur[V];
+    xnbr_row<V>(pc, pl, pr);
+    xnbr_row<V>(uc, ul, ur);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const int x = 128 * q + 4 * lane;
+      const float4 pzm = g4(G, y, zz - 1, x), pzp = g4(G, y, zz + 1, x);
+      const float4 pym = g4(G, ym, zz, x), pyp = g4(G, yp, zz, x);
+      const float4 vc = g4(vv, y, zz, x), vym = g4(vv, ym, zz, x), vyp = g4(vv, yp, zz, x);
+      const float4 wc = g4(ww, y, zz, x), wzm = g4(ww, y, zz - 1, x), wzp = g4(ww, y, zz + 1, x);
+      float e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float ph = cmp4(pc[q], j);
+        const float pxm = j == 0 ? pl[q] : cmp4(pc[q], j - 1), pxp = j == 3 ? pr[q] : cmp4(pc[q], j + 1);
+        const float uxm = j == 0 ? ul[q] : cmp4(uc[q], j - 1), uxp = j == 3 ? ur[q] : cmp4(uc[q], j + 1);
+        e[j] = adv_site<FLUX>(ph, pxm, pxp, cmp4(pym, j), cmp4(pyp, j), cmp4(pzm, j), cmp4(pzp, j), uxm,
+                              cmp4(uc[q], j), uxp, cmp4(vym, j), cmp4(vc, j), cmp4(vyp, j), cmp4(wzm, j),
+                              cmp4(wc, j), cmp4(wzp, j), p.dt);
+      }
+      h[q] = make_float4(e[0], e[1], e[2], e[3]);
+    }
+  };
+  auto put = [&](float (*ring)[NW][W], int slot, const float4 (&v)[V]) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) *reinterpret_cast<float4 *>(&ring[slot][warp][128 * q + 4 * lane]) = v[q];
+  };
+  auto get = [&](float (*ring)[NW][W], int slot, int w, int q) {
+    return *reinterpret_cast<const float4 *>(&ring[slot][w][128 * q + 4 * lane]);
+  };
+  float4 hm[V], hc[V], hp[V];  // phih of this row at planes k, k + 1, k + 2
+  advect(z0 - 2, hm);
+  advect(z0 - 1, hc);
+  put(sh, (z0 - 1) & 1, hc);
+  for (int k = z0 - 2; k < z1; ++k) {
+    advect(k + 2, hp);
+    put(sh, (k + 2) & 1, hp);
+    __syncthreads();
+    // psi of plane k + 1 (phih of rows y -+ 1 from the ring, phi for the cube)
+    if (psiw) {
+      float l[V], r[V];
+      xnbr_row<V>(hc, l, r);
+      float4 o4[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float4 hym = get(sh, (k + 1) & 1, warp - 1, q), hyp = get(sh, (k + 1) & 1, warp + 1, q);
+        const float4 gc = g4(G, y, k + 1, 128 * q + 4 * lane);
+        float2 L[2];
+        lap7_quad(hc[q], hm[q], hp[q], hym, hyp, l[q], r[q], L[0], L[1]);
+        float2 o[2];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const float2 hk = kk ? hi2(hc[q]) : lo2(hc[q]);
+          const float2 cb = p.cubic_at_half ? hk : (kk ? hi2(gc) : lo2(gc));
+          o[kk] = pfma(pf2(p.a, p.a), hk, pfma(pf2(p.b, p.b), pmul(pmul(cb, cb), cb), pmul(pf2(-p.kappa, -p.kappa), L[kk])));
+        }
+        o4[q] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+      }
+      put(sq, (k + 1) & 3, o4);
+    }
+    __syncthreads();
+    // phi^{n+1} of plane k (psi planes k - 1, k, k + 1 are in the ring)
+    if (k >= z0 && outw) {
+      float4 qc[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) qc[q] = get(sq, k & 3, warp, q);
+      float l[V], r[V];
+      xnbr_row<V>(qc, l, r);
+      float *orow = out + (long long)k * plane + (long long)yr * W;
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float4 qm = get(sq, (k + 3) & 3, warp, q), qp = get(sq, (k + 1) & 3, warp, q);
+        const float4 qym = get(sq, k & 3, warp - 1, q), qyp = get(sq, k & 3, warp + 1, q);
+        float2 L[2];
+        lap7_quad(qc[q], qm, qp, qym, qyp, l[q], r[q], L[0], L[1]);
+        const float2 g = pf2(p.dtG, p.dtG);
+        const float2 o0 = pfma(g, L[0], lo2(hm[q])), o1 = pfma(g, L[1], hi2(hm[q]));
+        *reinterpret_cast<float4 *>(orow + 128 * q + 4 * lane) = make_float4(o0.x, o0.y, o1.x, o1.y);
+      }
+    }
+    mv(hm, hc);
+    mv(hc, hp);
+  }
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     density3d_kernel(const S *__restrict__ hin, C *__restrict__ dn, KParams<C> p) {
@@ -809,9 +959,26 @@ cudaError_t fd3d_passes(lbm_handle *h, int in) {
   dim3 gridf(1, rows_f, (p.Lz + nzf - 1) / nzf);
   const int nzf1 = std::max(4, std::min(p.Lz, (int)((long long)p.Lz * rows_f / 152)));  // one CTA per SM
   dim3 gridf1(1, rows_f, (p.Lz + nzf1 - 1) / nzf1);
+  // the advection fused as well, one kernel per substep (opt-in: one CTA per
+  // SM, within one wave of z chunks; at 256^3 it takes 150 us a substep
+  // against 110 us for the advection pass and fd3f)
+  const bool fusedg = fused && std::getenv("HLBM_FD3_FUSED_ADV") != nullptr;
+  const int rows_g = (p.Ly + F3G_NW - 5) / (F3G_NW - 4);
+  const int zch = std::max(1, std::min(p.Lz, 152 / rows_g));
+  const int nzg = std::max(std::min(8, p.Lz), (p.Lz + zch - 1) / zch);
+  dim3 gridg(1, rows_g, (p.Lz + nzg - 1) / nzg);
   for (int j = 0; j < h->m; ++j) {
     float *dst = static_cast<float *>(((h->m - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
-    if (vec) {
+    if (fusedg) {
+      const size_t smg = fd3g_smem_bytes(p.Lx / 128);
+      if (p.Lx == 128) {
+        if (flux) fd3g_kernel<true, 1, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
+        else fd3g_kernel<false, 1, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
+      } else {
+        if (flux) fd3g_kernel<true, 2, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
+        else fd3g_kernel<false, 2, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
+      }
+    } else if (vec) {
       if (flux) fd3v_adv_kernel<true><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
       else fd3v_adv_kernel<false><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
       if (fused) {
@@ -879,6 +1046,18 @@ cudaError_t fd3d_configure(int precision, size_t smem) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fd3f_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(float) * 4 * F3F_NW * 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd3g_kernel<false, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fd3g_smem_bytes(1));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd3g_kernel<true, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fd3g_smem_bytes(1));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd3g_kernel<false, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fd3g_smem_bytes(2));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd3g_kernel<true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fd3g_smem_bytes(2));
   return e;
 }
 

@@ -283,17 +283,22 @@ def test_3d_variants_fp64(variant):
 @pytest.mark.parametrize("fd_path,shape", [("vec", (36, 19, 21)), ("vec", (132, 10, 17)),
                                            ("scalar", (37, 18, 21)), ("tile", (37, 18, 21)),
                                            ("fused", (128, 19, 21)), ("fused", (256, 9, 13)),
+                                           ("psi", (128, 19, 21)), ("psi", (256, 9, 13)),
                                            ("vec", (128, 19, 21))])
 def test_3d_fp32_fd_paths(variant, fd_path, shape, monkeypatch):
     """FP32 3D against the oracle, both advection forms: the three FD passes
     with four x-sites per thread marching in z (Lx a multiple of 4; ragged in
     x against the 128-site warp, in y against 8 rows, in z against 16
     planes), the one-site-per-thread passes (any Lx), the shared-memory
-    tile kernel, and the advection pass followed by the fused psi / new-phi
-    kernel (Lx = 128 or 256; ragged in y against 14 rows per CTA, in z
-    against the planes per CTA; 9 rows: fewer than one CTA's)."""
+    tile kernel, the advection pass followed by the fused psi / new-phi
+    kernel ("psi", the default for Lx = 128 or 256), and the whole substep
+    in one kernel ("fused", opt-in); both ragged in y against the rows per
+    CTA (14 and 12) and in z against the planes per CTA; 9 rows: fewer than
+    one CTA's."""
     if fd_path == "tile":
         monkeypatch.setenv("HLBM_FD3_TILE", "1")
+    if fd_path == "fused":
+        monkeypatch.setenv("HLBM_FD3_FUSED_ADV", "1")
     if fd_path == "vec" and shape[0] in (128, 256):
         monkeypatch.setenv("HLBM_FD3_UNFUSED", "1")
     Lx, Ly, Lz = shape
@@ -308,6 +313,36 @@ def test_3d_fp32_fd_paths(variant, fd_path, shape, monkeypatch):
     _, ru = ref.moments()
     umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
     assert dphi <= 1e-5 and du <= 1e-3 * umax, (variant, fd_path, dphi, du, umax)
+
+
+@pytest.mark.parametrize("shape", [(128, 19, 21), (256, 30, 17)])
+def test_3d_fused_substep_matches_two_kernel_path(shape, monkeypatch):
+    """The one-kernel FD substep (advection, psi and the new phi fused;
+    opt-in) against the advection pass followed by the psi / new-phi kernel:
+    the same FP32 arithmetic per site (the advection of both is one device
+    function, psi and the new phi the same packed operations), so after 10
+    LB steps they agree to rounding at most (bitwise when measured)."""
+    Lx, Ly, Lz = shape
+    kw = dict(CFG1, N=1 / 6, Q=1 / 3)
+    lp = lbm.LbmParams(dims=3, Lx=Lx, Ly=Ly, Lz=Lz, fd_substeps=-8, precision=lbm.LBM_F32DEV, **kw)
+    op = O.Params(dims=3, Lx=Lx, Ly=Ly, Lz=Lz, m=8, **kw)
+    phi = I.drop(3, Lx, Ly, Lz, R=7, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(3, Lx, Ly, Lz)
+    u = u + 0.003 * np.sin(np.arange(Lx) / 5.0)[None, None, None, :]
+    u[2] -= 0.002 * np.cos(np.arange(Ly) / 3.0)[None, :, None]
+    res = []
+    for fused in (True, False):
+        if fused:
+            monkeypatch.setenv("HLBM_FD3_FUSED_ADV", "1")
+        else:
+            monkeypatch.delenv("HLBM_FD3_FUSED_ADV")
+        lat = lbm.Lattice(lp)
+        lat.init_fields(n, phi, u).step(10)
+        res.append(lat.moments())
+        lat.close()
+    d = [float(np.max(np.abs(a - b))) for a, b in zip(res[0], res[1])]
+    print(f"fused vs two-kernel FD, {shape}: |dn|={d[0]:.3e} |dphi|={d[1]:.3e} |du|={d[2]:.3e}")
+    assert d[1] <= 1e-6 and d[2] <= 1e-8 and d[0] <= 1e-6
 
 
 def test_3d_drop_64_fp32_and_fp16():
