@@ -83,3 +83,22 @@ def test_box_reach_is_needed():
     bad = np.argwhere(st.phi != full.phi[ix])
     dist = np.minimum(bad, W - 1 - bad).min(axis=1)
     assert dist.max() < r
+
+
+def test_box_inner_block_is_exact_3d_m8():
+    """The configuration the 256^3 sampled GPU test relies on: D3Q19,
+    N = 1/6, Q = 1/3, m = 8, one step, a drop with a uniform flow; a 64^3
+    box of a 72^3 lattice, across its faces, keeps its 4^3 inner block exact."""
+    shape, m, W, steps = (72, 72, 72), 8, 64, 1
+    kw = dict(KW, N=1 / 6, Q=1 / 3, m=m)
+    op = O.Params(dims=3, Lx=72, Ly=72, Lz=72, **kw)
+    n, phi, u = _fields(3, shape, 18, (0.01, -0.005, 0.007), op)
+    full = O.State.create(op, n, phi, u)
+    full.run(steps)
+    fn, fu = full.moments()
+    inner, bn, bphi, bu = box_oracle(kw, n, phi, u, (36 + 18, 36, 70), W, steps)
+    ix = np.ix_(*inner)
+    assert bphi.shape == (4, 4, 4)
+    assert np.array_equal(bphi, full.phi[ix])
+    assert np.array_equal(bn, fn[ix])
+    assert np.array_equal(bu, np.stack([fu[k][ix] for k in range(3)]))
