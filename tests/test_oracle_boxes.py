@@ -102,3 +102,24 @@ def test_box_inner_block_is_exact_3d_m8():
     assert np.array_equal(bphi, full.phi[ix])
     assert np.array_equal(bn, fn[ix])
     assert np.array_equal(bu, np.stack([fu[k][ix] for k in range(3)]))
+
+
+def test_box_inner_block_is_exact_2d_4096_configuration():
+    """The configuration the 4096^2 sampled GPU test relies on: D2Q9 with
+    the workload's stencil weights, m = 4, three steps, a 160^2 box of a
+    176 x 184 lattice across its faces keeps its 52^2 inner block exact."""
+    shape, m, W, steps = (176, 184), 4, 160, 3
+    kw = dict(KW, N=0.3, Q=2.5, m=m)
+    op = O.Params(dims=2, Lx=shape[1], Ly=shape[0], **kw)
+    n, phi, u = _fields(2, shape, 40, (0.003, -0.002), op)
+    phi = phi + 0.01 * np.sin(np.arange(shape[1]) / 4.0)[None, :]
+    full = O.State.create(op, n, phi, u)
+    full.run(steps)
+    fn, fu = full.moments()
+    for centre in ((88, 92), (170, 5)):
+        inner, bn, bphi, bu = box_oracle(kw, n, phi, u, centre, W, steps)
+        ix = np.ix_(*inner)
+        assert bphi.shape == (52, 52)
+        assert np.array_equal(bphi, full.phi[ix])
+        assert np.array_equal(bn, fn[ix])
+        assert np.array_equal(bu, np.stack([fu[k][ix] for k in range(2)]))
