@@ -124,3 +124,63 @@ def test_buffer_bytes_and_adoption_checks(lib):
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_create_with_buffers(p, pops, phi, u)
         assert e.value.code == lbm.LBM_EINVAL
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) of every function declared in
+    include/*.h (comments stripped; parameter names dropped)."""
+    protos = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for ret, name, params in re.findall(r"([\w\s\*]+?)\b(lbm_\w+)\s*\(([^)]*)\)\s*;", src):
+            ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+            types = []
+            for p_ in ps:
+                is_ptr = "*" in p_ or "[" in p_
+                words = re.sub(r"\[\d*\]", "", p_).replace("*", " ").split()
+                base = " ".join(w for w in words[:-1] if w != "const") if len(words) > 1 else words[0]
+                types.append("ptr" if is_ptr else base)
+            r = ret.replace("const", "").split()
+            protos[name] = ("ptr" if "*" in ret else " ".join(r[-3:]).strip(), types)
+    return protos
+
+
+_SCALAR = {"int": ctypes.c_int, "double": ctypes.c_double, "float": ctypes.c_float,
+           "long long": ctypes.c_longlong, "unsigned long long": ctypes.c_ulonglong}
+
+
+def _is_pointer_type(t):
+    return (t in (ctypes.c_void_p, ctypes.c_char_p) or isinstance(t, type(ctypes.POINTER(ctypes.c_int)))
+            or hasattr(t, "from_param") and t not in _SCALAR.values())
+
+
+def test_binding_argtypes_match_prototypes(lib):
+    """Every binding that declares argtypes has one per C parameter, scalars
+    of the C type and pointers where the C side takes a pointer; restypes of
+    the functions that do not return int match too."""
+    protos = _prototypes()
+    assert len(protos) >= 40
+    checked = 0
+    for name, (ret, params) in protos.items():
+        f = getattr(lib, name)
+        at = getattr(f, "argtypes", None)
+        if at is None:
+            continue
+        checked += 1
+        assert len(at) == len(params), (name, len(at), params)
+        for i, (c, t) in enumerate(zip(params, at)):
+            if c == "ptr":
+                assert _is_pointer_type(t), (name, i, t)
+            else:
+                assert t is _SCALAR[c.replace("const ", "")], (name, i, c, t)
+        if ret == "ptr":
+            assert f.restype in (ctypes.c_char_p, ctypes.c_void_p), (name, f.restype)
+        elif ret in ("long long", "unsigned long long", "double", "float"):
+            assert f.restype is _SCALAR[ret], (name, ret, f.restype)
+        elif ret == "void":
+            assert f.restype is None, (name, f.restype)
+    assert checked >= 30
