@@ -184,3 +184,35 @@ def test_binding_argtypes_match_prototypes(lib):
         elif ret == "void":
             assert f.restype is None, (name, f.restype)
     assert checked >= 30
+
+
+_OK_INST = (32, 48, (0.0, 0.0), 0)
+
+
+@pytest.mark.parametrize("common,instances,needle", [
+    (dict(dims=3), [_OK_INST], "batches are 2D"),
+    (dict(precision=lbm.LBM_F16DEV), [_OK_INST], "FP64 or FP32-deviation"),
+    (dict(T=0.25), [_OK_INST], "T = 1/3"),
+    (dict(tau=0.5), [_OK_INST], "bad common parameters"),
+    (dict(adv_variant=7), [_OK_INST], "adv_variant"),
+    (dict(fd_substeps=1), [_OK_INST], "Euler bound"),
+    (dict(), [_OK_INST, (2, 48, (0.0, 0.0), 0)], "bad instance 1"),
+    (dict(), [_OK_INST, _OK_INST, (32, 32, (float("nan"), 0.0), 0)], "bad instance 2"),
+    (dict(), [(32, 32, (0.0, 0.0), -5)], "bad instance 0"),
+    (dict(), [], "NULL or empty batch"),
+])
+def test_invalid_batches_are_rejected(lib, common, instances, needle):
+    """lbm_batch_create validates its parameters and every instance before
+    any CUDA call: EINVAL with the reason, no handle."""
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Batch(lbm.LbmParams(**common), instances)
+    assert ei.value.code == lbm.LBM_EINVAL
+    assert needle in str(ei.value)
+
+
+@pytest.mark.parametrize("channels,layers", [(24, 6), (32, 1), (16, 9)])
+def test_invalid_networks_are_rejected(lib, channels, layers):
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Net(channels, layers)
+    assert ei.value.code == lbm.LBM_EINVAL
+    assert "channels must be 16 or 32" in str(ei.value)
