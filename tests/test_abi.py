@@ -76,6 +76,10 @@ def test_lattice_tables(lib):
     (dict(T=0.0), "T > 0"),
     (dict(force_steps=-1), "force_steps"),
     (dict(f16_scale_log2=20), "f16_scale_log2"),
+    (dict(dims=3, Lx=2048, Ly=2048, Lz=1024), "2^31"),
+    (dict(fd_substeps=-5000), "fd_substeps too large"),
+    (dict(g=(float("inf"), 0.0, 0.0)), "g must be finite"),
+    (dict(a=float("nan")), "a must be finite"),
 ])
 def test_invalid_parameters_are_rejected(lib, change, needle):
     p = lbm.LbmParams(**change)
