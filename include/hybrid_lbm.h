@@ -175,7 +175,9 @@ long long lbm_time(const lbm_handle *h);       /* current LB step t, or -1     *
  * the register kernel; 3, 5, 6: TMA staging with the scalar collision or the
  * packed-pair collision for 4 / 3 CTAs per SM, FP32 and FP16 storage; 7:
  * persistent pipelined TMA kernel, FP32), m, FD kernel (0: warp-marching;
- * 32 or 64: shared-memory tile of that width; 128: block kernel)} into values
+ * 32 or 64: shared-memory tile of that width; 128: block kernel; 1:
+ * y-marching wavefront kernel, whose "rows" are the output rows of one
+ * segment and whose substeps per launch are 2 or 4)} into values
  * and returns 6 (EINVAL on NULL).
  * Environment: HLBM_TUNING="sub,rows,cols,collide_rows[,tile]" fixes the shapes
  * instead of timing them (reproducible profiling); HLBM_TUNE_VERBOSE=1 prints

@@ -1262,6 +1262,7 @@ cudaError_t fd2d_block(lbm_handle *h, const KParams<C> &p, const C *src, C *dst,
     // a remainder launch with fewer substeps than the shape
     if (sub == 1) return flux ? fd2d_block_one<true, 1, 4, 16>(h, p, src, dst) : fd2d_block_one<false, 1, 4, 16>(h, p, src, dst);
     if (sub == 2) return flux ? fd2d_block_one<true, 2, 4, 16>(h, p, src, dst) : fd2d_block_one<false, 2, 4, 16>(h, p, src, dst);
+    if (sub == 3) return flux ? fd2d_block_one<true, 3, 4, 16>(h, p, src, dst) : fd2d_block_one<false, 3, 4, 16>(h, p, src, dst);
     return flux ? fd2d_block_one<true, 4, 5, 16>(h, p, src, dst) : fd2d_block_one<false, 4, 5, 16>(h, p, src, dst);
   }
   return cudaErrorInvalidValue;
@@ -1285,6 +1286,7 @@ cudaError_t fd2d_block_configure() {
                              cudaFuncAttributeMaxDynamicSharedMemorySize,                        \
                              (int)FDBlock<SB, RYY / NWW, NWW>::smem_of(true));
   FDB_SHAPES(FDB_CFG)
+  FDB_CFG(3, 64, 16)  // the remainder launch of m = 3 (mod 4)
 #undef FDB_CFG
   return e;
 }
@@ -1307,6 +1309,13 @@ cudaError_t fd2d_tile_configure() {
 
 template <typename C, int V>
 cudaError_t fd2d_sub(lbm_handle *h, const KParams<C> &p, const C *src, C *dst, int sub, int TY) {
+  if constexpr (std::is_same<C, float>::value) {
+    // wavefront kernel: 2 or 4 substeps; an odd remainder goes to the block kernel
+    if (h->fd_tile_w == 1) {
+      if (sub == 2 || sub == 4) return fd2d_wave(h, p, src, dst, sub, h->fd_rows);
+      return fd2d_block<C>(h, p, src, dst, sub);
+    }
+  }
   if (h->fd_tile_w == 128) return fd2d_block<C>(h, p, src, dst, sub);
   if (h->fd_tile_w > 0) return fd2d_tile<C>(h, p, src, dst, sub);
   switch (sub) {

@@ -146,7 +146,7 @@ struct lbm_handle {
   int dims = 2, q = 9, m = 1, sub = 1;  // sub = FD substeps fused per launch
   int fd_rows = 32;                     // output rows per warp of the 2D FD kernel
   int fd_cols = 4;                      // columns per lane of the 2D FD kernel (FP32)
-  int fd_tile_w = 0;                    // 0: marching FD kernel; 32/64: tile kernel width
+  int fd_tile_w = 0;                    // 0: marching FD kernel; 32/64: tile kernel width; 128: block; 1: wavefront
   int collide_rows = 2;                 // sites per thread of the 2D collide kernel
   long long S = 0, t = 0;
   bool inited = false;
@@ -221,6 +221,14 @@ KParams<C> make_params(const lbm_handle *h, int force_on);
 bool collide2d_tma_eligible(const lbm_handle *h, int variant);
 cudaError_t collide2d_tma(lbm_handle *h, int in, int force_on, int mode, int variant);
 cudaError_t collide2d_tma_configure(int precision);
+
+// FP32 FD update in y-marching form (fd2d_wave.cu): sub = 2 or 4 substeps per
+// launch, NY output rows per segment; FP32 or FP16 storage (phi and u* are
+// FP32), printed advection form, Lx % 4 == 0, 16-byte aligned phi and u*
+bool fd2d_wave_eligible(const lbm_handle *h);
+cudaError_t fd2d_wave(lbm_handle *h, const KParams<float> &p, const float *src, float *dst, int sub,
+                      int NY);
+int fd2d_wave_written_columns(int sub);
 int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
 
 }  // namespace hlbm

@@ -341,7 +341,14 @@ int autotune_2d(lbm_handle *h) {
     bool block_ok = false;
     for (const auto &sh : shapes)
       block_ok |= v[4] == 128 && h->P.precision != LBM_F64 && v[0] == sh[0] && v[1] == sh[1] && v[2] == sh[2];
-    if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok))) && v[0] >= 1 &&
+    // wavefront kernel: 2 or 4 substeps per launch, rows = output rows of a segment
+    const bool wave_ok = v[4] == 1 && fd2d_wave_eligible(h) && (std::min(v[0], h->m) == 2 || std::min(v[0], h->m) == 4);
+    if (nv == 5 && v[4] == 1 && !wave_ok) {
+      return fail(h, LBM_EINVAL,
+                  "HLBM_TUNING wavefront FD kernel (tile 1): sub 2 or 4 (m >= 2), FP32 or FP16 storage, "
+                  "printed advection form, Lx % 4 == 0");
+    }
+    if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok || wave_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
         (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV) ||
          collide2d_tma_eligible(h, v[3]))) {
@@ -393,6 +400,17 @@ int autotune_2d(lbm_handle *h) {
     int tile_w, cols, sub, rows;
   };
   std::vector<FdShape> cands;
+  // wavefront kernel (FP32 phi): 128-column strips marching down segments of
+  // `rows` output rows, 4 or 2 substeps per launch
+  if (fd2d_wave_eligible(h)) {
+    for (int sb : {4, 2}) {
+      if (sb > h->m) continue;
+      for (int ny : {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 1024}) {
+        cands.push_back({1, 4, sb, std::min(ny, h->P.Ly)});
+        if (ny >= h->P.Ly) break;
+      }
+    }
+  }
   // block kernel (FP32): 128-column regions, (substeps, rows per warp)
   if (h->P.precision != LBM_F64) {
     if (h->m >= 4) {

@@ -594,6 +594,79 @@ def test_block_kernel_flux_variant(shape, monkeypatch):
     _fp32_bar(ref, lat, shape)
 
 
+# y-marching wavefront FD kernel (tile 1): substeps per launch 4 or 2, rows =
+# output rows of a segment
+WAVE_SHAPES = ["4,32,4,1,1", "4,7,4,1,1", "2,16,4,1,1", "4,256,4,1,1", "2,5,4,1,1"]
+
+
+@pytest.mark.parametrize("shape", WAVE_SHAPES)
+@pytest.mark.parametrize("size,m", [((72, 45), 5), ((300, 217), 4), ((64, 20), 6), ((412, 130), 8)])
+def test_wave_kernel_shapes(shape, size, m, monkeypatch):
+    """The wavefront FD kernel against the oracle: a lattice narrower than
+    one strip (the strip wraps around it), strips and segments with ragged
+    edges, segments taller than the lattice, and m = 5 / 6 / 8 (a remainder
+    launch of 1 or 2 substeps, or two launches of 4)."""
+    monkeypatch.setenv("HLBM_TUNING", shape)
+    Lx, Ly = size
+    op, lp = _pair(Lx, Ly, m=m, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.drop(2, Lx, Ly, R=min(Lx, Ly) // 4, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, Lx, Ly)
+    u = u + 0.003 * np.sin(np.arange(Lx) / 4.0)[None, None, :]
+    u[1] += 0.002 * np.cos(np.arange(Ly) / 3.0)[:, None]
+    ref, lat = _run_both(op, lp, n, phi, u, 12)
+    _fp32_bar(ref, lat, shape)
+    assert lbm.lbm_tuning(lat.handle)["fd_tile_width"] == 1
+
+
+def test_wave_kernel_cubic_at_half_and_f16(monkeypatch):
+    monkeypatch.setenv("HLBM_TUNING", "4,24,4,1,1")
+    op, lp = _pair(128, 96, m=4, cubic_at_half=1, precision=lbm.LBM_F32DEV, **CFG1)
+    phi = I.drop(2, 128, 96, R=24, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 128, 96)
+    u = u + 0.003 * np.cos(np.arange(96) / 3.0)[None, :, None]
+    ref, lat = _run_both(op, lp, n, phi, u, 15)
+    _fp32_bar(ref, lat, "cubic_at_half")
+    # FP16 deviation storage feeds the same FP32 phi and u* planes
+    monkeypatch.setenv("HLBM_TUNING", "4,24,4,5,1")
+    op, lp = _pair(128, 96, m=4, precision=lbm.LBM_F16DEV, **CFG1)
+    ref, lat = _run_both(op, lp, n, phi, u, 12)
+    dphi, du, _ = _errors(ref, lat)
+    assert dphi <= 1e-3, dphi
+    assert lbm.lbm_tuning(lat.handle)["fd_tile_width"] == 1
+
+
+def test_wave_kernel_matches_block_kernel_spinodal(monkeypatch):
+    """1024^2 spinodal state with a flow, 3 LB steps: the wavefront and the
+    block FD kernels evaluate the same formulas with the same collide kernel;
+    they may round differently (the block kernel's contraction is the
+    compiler's), so they agree to FP32 round-off, not bitwise."""
+    L = 1024
+    phi = I.spinodal(2, L, L, seed=3)
+    n, u = I.rest(2, L, L)
+    u = u + 0.004 * np.sin(np.arange(L) / 7.0)[None, None, :]
+    out = []
+    for shape in ("4,96,2,5,128", "4,64,4,5,1"):
+        monkeypatch.setenv("HLBM_TUNING", shape)
+        lat = lbm.Lattice(lbm.LbmParams(Lx=L, Ly=L, fd_substeps=4, precision=lbm.LBM_F32DEV, **CFG1))
+        lat.init_fields(n, phi, u).step(3)
+        out.append(lat.moments())
+        lat.close()
+    (n0, p0, u0), (n1, p1, u1) = out
+    assert np.max(np.abs(p0 - p1)) <= 2e-7 and np.max(np.abs(u0 - u1)) <= 1e-8
+
+
+@pytest.mark.parametrize("kw", [dict(adv_variant=1), dict(precision=lbm.LBM_F64)])
+def test_wave_kernel_refused(kw, monkeypatch):
+    """The wavefront kernel implements the printed advection form on FP32 phi:
+    the flux form and the FP64 path are refused when it is requested."""
+    monkeypatch.setenv("HLBM_TUNING", "4,32,4,1,1")
+    args = dict(CFG1)
+    args.update(kw)
+    args.setdefault("precision", lbm.LBM_F32DEV)
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(lbm.LbmParams(Lx=128, Ly=64, **args))
+
+
 def test_block_kernel_refused_in_fp64(monkeypatch):
     monkeypatch.setenv("HLBM_TUNING", "4,80,2,1,128")
     with pytest.raises(lbm.LbmError):
