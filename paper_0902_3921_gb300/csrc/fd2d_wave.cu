@@ -11,9 +11,9 @@
 //     advection coefficients of row a (Eqs. 32-35, from u*, v* of rows
 //     a - 1 .. a + 1), phih_1(a), psi_1(a - 1), phi_1(a - 2),
 //     phih_2(a - 3), psi_2(a - 4), phi_2(a - 5);
-//   warp B (substeps 3 and 4, SUB = 4 only), b = t - 8:
+//   warp B (substeps 3 and 4, SUB = 4 only), b = t - 9:
 //     phih_3(b) .. phi_3(b - 2), phih_4(b - 3) .. phi_4(b - 5), reading
-//     phi_2 that warp A handed over in the previous tick and the
+//     phi_2 that warp A handed over before the last barrier and the
 //     coefficients warp A wrote to a shared ring.
 //
 // A stencil input is consumed three rows at a time (r - 1, r, r + 1): each
@@ -21,11 +21,12 @@
 // new row per tick, so nothing is read twice.  Lane l holds the four columns
 // 4l .. 4l + 3 of a row (one float4) and takes its x neighbours from lanes
 // l -/+ 1 by shuffles; columns 0 and 127 lose validity first and are never
-// written.  The coefficients of a row are used by two substeps three ticks
-// apart: a four-entry register FIFO (tick loop unrolled by four) holds them.
+// written.  Warp A writes the coefficients of each row to a 16-row shared
+// ring, from which the later substeps read them (3, 7 and 10 ticks later).
 // Inputs (phi, u, v) are prefetched D rows ahead by cp.async into per-lane
 // rings (a lane reads back only the 16 bytes it copied, so no barrier guards
-// them); one named barrier per tick orders the hand-over between the warps.
+// them); one named barrier per pair of ticks orders the hand-over between
+// the warps.
 //
 // Per site and LB step the kernel reads phi and u* once and writes phi once
 // (16 B), plus the strip's x halo (128 / (128 - 2 HX) of the columns) and the
@@ -45,7 +46,6 @@ namespace {
 constexpr int WV_W = 128;   // computed columns of a strip
 constexpr int WV_IR = 8;    // input ring rows (per lane)
 constexpr int WV_D = 6;     // input prefetch distance in rows (<= WV_IR - 2)
-constexpr int WV_CR = 8;    // coefficient ring rows (warp A -> warp B)
 constexpr unsigned WV_FULL = 0xffffffffu;
 
 template <int SUB>
@@ -56,17 +56,23 @@ struct Wave {
   static constexpr int HY = 3 * SUB;                // rows of reach of SUB substeps
   static constexpr int HX = (3 * SUB + 3) / 4 * 4;  // columns, rounded to whole float4 groups
   static constexpr int TX = WV_W - 2 * HX;          // written columns of a strip
-  // warp A's output row lags its input by 6 rows; warp B's by 13
-  static constexpr int LAG = SUB == 4 ? 13 : 6;
-  // shared memory (floats): phi, u, v rings of warp A; the coefficient ring
+  // warp A's output row lags its input by 6 rows; warp B's by 14 (it works on
+  // row b = t - 9, two ticks behind warp A's phi_2, so that one barrier per
+  // pair of ticks orders the hand-over)
+  static constexpr int LAG = SUB == 4 ? 14 : 6;
+  // coefficient ring rows: written for row a at tick a + 1, read for row a - 3
+  // (warp A) and rows t - 9, t - 12 (warp B); hand-over ring rows
+  static constexpr int CR = SUB == 4 ? 16 : 4;
+  static constexpr int HR = 4;
+  // shared memory (floats): phi, u, v rings of warp A, the coefficient ring
   // (c0, dt u, dt v) and the two-row phi_2 hand-over (SUB = 4)
   static constexpr int OFF_PHI = 0, OFF_U = WV_IR * WV_W, OFF_V = 2 * WV_IR * WV_W;
   static constexpr int OFF_C = 3 * WV_IR * WV_W;
-  static constexpr int OFF_H = OFF_C + (SUB == 4 ? 3 * WV_CR * WV_W : 0);
-  static constexpr int FLOATS = OFF_H + (SUB == 4 ? 2 * WV_W : 0);
+  static constexpr int OFF_H = OFF_C + 3 * CR * WV_W;
+  static constexpr int FLOATS = OFF_H + (SUB == 4 ? HR * WV_W : 0);
   static constexpr size_t smem = sizeof(float) * FLOATS;
-  // ticks for a segment of NY output rows, rounded up to the FIFO period
-  static __host__ __device__ int ticks(int NY) { return (NY + HY + LAG + 3) / 4 * 4; }
+  // ticks for a segment of NY output rows, rounded up to whole pairs
+  static __host__ __device__ int ticks(int NY) { return (NY + HY + LAG + 1) / 2 * 2; }
 };
 
 __device__ __forceinline__ float4 wv_ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -208,21 +214,24 @@ __global__ void __launch_bounds__(Wave<SUB>::NT)
   // an output lane writes its float4 when the columns are inside the strip's
   // written range and the lattice (Lx % 4 == 0: a group never straddles Lx)
   const bool col_ok = c >= G::HX && c < G::HX + G::TX && x0 + c < Lx;
-  float *coef = wv_smem + G::OFF_C;  // [3][WV_CR][128]
-  float *hand = wv_smem + G::OFF_H;  // [2][128]
+  float *coef = wv_smem + G::OFF_C + c;  // [3][CR][128], this lane's columns
+  float *hand = wv_smem + G::OFF_H + c;  // [HR][128]
+  auto ld_coef = [&](int r) {
+    const int sc = (r & (G::CR - 1)) * WV_W;
+    return WvCoef{wv_ld(coef + sc), wv_ld(coef + G::CR * WV_W + sc), wv_ld(coef + 2 * G::CR * WV_W + sc)};
+  };
   pdl_wait();  // u*(t) comes from the collide kernel, phi(t) from the previous FD launch
   pdl_trigger();
   WvSub s1{}, s2{};
-  WvCoef fifo[4];
   if (warp == 0) {
     // ---- warp A: inputs, coefficients, substeps 1 and 2 ----
-    float *rphi = wv_smem + G::OFF_PHI, *ru = wv_smem + G::OFF_U, *rv = wv_smem + G::OFF_V;
+    float *rphi = wv_smem + G::OFF_PHI + c, *ru = wv_smem + G::OFF_U + c, *rv = wv_smem + G::OFF_V + c;
     const int gx = wrapi(x0 + c, Lx);
     int yi = wrapi(ys - G::HY, Ly);  // global row of the next input row to issue
     auto issue = [&](int j) {        // input row j of the segment into ring slot j % 8
       if (j < J) {
         const long long off = (long long)yi * Lx + gx;
-        const int sl = (j & (WV_IR - 1)) * WV_W + c;
+        const int sl = (j & (WV_IR - 1)) * WV_W;
         wv_cp16(rphi + sl, phi_in + off);
         wv_cp16(ru + sl, u + off);
         wv_cp16(rv + sl, u + S + off);
@@ -233,61 +242,54 @@ __global__ void __launch_bounds__(Wave<SUB>::NT)
 #pragma unroll 1
     for (int j = 0; j < WV_D; ++j) issue(j);
     float4 vm = make_float4(0.f, 0.f, 0.f, 0.f), vc = vm;  // v of rows t - 2, t - 1
-    auto tick = [&](auto KK, int t) {
-      constexpr int K = decltype(KK)::value;  // t % 4: the FIFO slot of row t - 1
+    auto tick = [&](int t) {
       issue(t + WV_D);
       wv_wait_d();  // rows <= t have landed (this lane's copies)
-      const int st = (t & (WV_IR - 1)) * WV_W + c, stm = ((t - 1) & (WV_IR - 1)) * WV_W + c;
+      const int st = (t & (WV_IR - 1)) * WV_W, stm = ((t - 1) & (WV_IR - 1)) * WV_W;
       const float4 pn = wv_ld(rphi + st), vn = wv_ld(rv + st), uc = wv_ld(ru + stm);
-      fifo[K] = wv_coef(uc, vm, vc, vn, k.dt);  // row a = t - 1
+      const WvCoef cf = wv_coef(uc, vm, vc, vn, k.dt);  // row a = t - 1
       vm = vc;
       vc = vn;
-      if constexpr (SUB == 4) {
-        const int sc = ((t - 1) & (WV_CR - 1)) * WV_W + c;
-        wv_st(coef + sc, fifo[K].c0);
-        wv_st(coef + WV_CR * WV_W + sc, fifo[K].t1);
-        wv_st(coef + 2 * WV_CR * WV_W + sc, fifo[K].t2);
+      {
+        const int sc = ((t - 1) & (G::CR - 1)) * WV_W;
+        wv_st(coef + sc, cf.c0);
+        wv_st(coef + G::CR * WV_W + sc, cf.t1);
+        wv_st(coef + 2 * G::CR * WV_W + sc, cf.t2);
       }
-      const float4 o1 = wv_substep(s1, pn, fifo[K], k);             // phi_1(a - 2)
-      const float4 o2 = wv_substep(s2, o1, fifo[(K + 1) & 3], k);   // phi_2(a - 5), coef(a - 3)
+      const float4 o1 = wv_substep(s1, pn, cf, k);              // phi_1(a - 2)
+      const float4 o2 = wv_substep(s2, o1, ld_coef(t - 4), k);  // phi_2(a - 5), coef(a - 3)
       if constexpr (SUB == 4) {
-        wv_st(hand + ((t - 6) & 1) * WV_W + c, o2);
+        wv_st(hand + ((t - 6) & (G::HR - 1)) * WV_W, o2);
       } else {
         const int r = t - 6;  // relative input row of the output
         if (r >= G::HY && r < G::HY + NY && ys + r - G::HY < Ly && col_ok)
           wv_st(phi_out + (long long)(ys + r - G::HY) * Lx + (x0 + c), o2);
       }
-      if constexpr (SUB == 4) wv_bar<G::NT>();  // one warp alone needs no barrier
     };
+    // two ticks per iteration: the second tick's early phases overlap the
+    // first's late ones; warp B reads what both wrote after the barrier
 #pragma unroll 1
-    for (int t = 0; t < T; t += 4) {
-      tick(std::integral_constant<int, 0>{}, t);
-      tick(std::integral_constant<int, 1>{}, t + 1);
-      tick(std::integral_constant<int, 2>{}, t + 2);
-      tick(std::integral_constant<int, 3>{}, t + 3);
+    for (int t = 0; t < T; t += 2) {
+      tick(t);
+      tick(t + 1);
+      if constexpr (SUB == 4) wv_bar<G::NT>();
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if constexpr (SUB == 4) {
-    // ---- warp B: substeps 3 and 4 of row b = t - 8 ----
-    auto tick = [&](auto KK, int t) {
-      constexpr int K = decltype(KK)::value;
-      const float4 pn = wv_ld(hand + ((t - 7) & 1) * WV_W + c);  // phi_2 of row b + 1
-      const int sc = ((t - 8) & (WV_CR - 1)) * WV_W + c;
-      fifo[K] = WvCoef{wv_ld(coef + sc), wv_ld(coef + WV_CR * WV_W + sc),
-                       wv_ld(coef + 2 * WV_CR * WV_W + sc)};
-      const float4 o3 = wv_substep(s1, pn, fifo[K], k);            // phi_3(b - 2)
-      const float4 o4 = wv_substep(s2, o3, fifo[(K + 1) & 3], k);  // phi_4(b - 5)
-      const int r = t - 13;
+    // ---- warp B: substeps 3 and 4 of row b = t - 9 ----
+    auto tick = [&](int t) {
+      const float4 pn = wv_ld(hand + ((t - 8) & (G::HR - 1)) * WV_W);  // phi_2 of row b + 1
+      const float4 o3 = wv_substep(s1, pn, ld_coef(t - 9), k);          // phi_3(b - 2)
+      const float4 o4 = wv_substep(s2, o3, ld_coef(t - 12), k);         // phi_4(b - 5)
+      const int r = t - 14;
       if (r >= G::HY && r < G::HY + NY && ys + r - G::HY < Ly && col_ok)
         wv_st(phi_out + (long long)(ys + r - G::HY) * Lx + (x0 + c), o4);
-      wv_bar<G::NT>();
     };
 #pragma unroll 1
-    for (int t = 0; t < T; t += 4) {
-      tick(std::integral_constant<int, 0>{}, t);
-      tick(std::integral_constant<int, 1>{}, t + 1);
-      tick(std::integral_constant<int, 2>{}, t + 2);
-      tick(std::integral_constant<int, 3>{}, t + 3);
+    for (int t = 0; t < T; t += 2) {
+      tick(t);
+      tick(t + 1);
+      wv_bar<G::NT>();
     }
   }
 }
@@ -308,7 +310,34 @@ bool fd2d_wave_eligible(const lbm_handle *h) {
          h->P.Lx % 4 == 0 && h->m >= 2 && al(h->u) && al(h->phi[0]) && al(h->phi[1]) && al(h->phi[2]);
 }
 
-int fd2d_wave_written_columns(int sub) { return sub >= 4 ? Wave<4>::TX : Wave<2>::TX; }
+// CTAs of one wave (resident CTAs per SM x SMs) and strips of the lattice, for
+// a segment height that makes the grid whole waves
+int fd2d_wave_slots(int sub, int *strips, int Lx) {
+  int dev = 0, sms = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  int tx;
+  if (sub == 4) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fd2d_wave_kernel<4>, Wave<4>::NT, Wave<4>::smem);
+    tx = Wave<4>::TX;
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fd2d_wave_kernel<2>, Wave<2>::NT, Wave<2>::smem);
+    tx = Wave<2>::TX;
+  }
+  *strips = (Lx + tx - 1) / tx;
+  return e == cudaSuccess ? nb * sms : 0;
+}
+
+// dynamic shared memory beyond the default 48 KB
+cudaError_t fd2d_wave_configure() {
+  cudaError_t e = cudaFuncSetAttribute(fd2d_wave_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Wave<4>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd2d_wave_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Wave<2>::smem);
+  return e;
+}
 
 // sub = 2 or 4 substeps in one launch; NY = output rows of a segment
 cudaError_t fd2d_wave(lbm_handle *h, const KParams<float> &p, const float *src, float *dst, int sub,

@@ -1355,6 +1355,7 @@ cudaError_t collide2d_launch(lbm_handle *h, int in, int force_on, int mode) {
 cudaError_t collide2d_configure(int precision) {
   cudaError_t e = precision == LBM_F64 ? fd2d_tile_configure<double>() : fd2d_tile_configure<float>();
   if (e == cudaSuccess && precision != LBM_F64) e = fd2d_block_configure();
+  if (e == cudaSuccess && precision != LBM_F64) e = fd2d_wave_configure();
   if (e != cudaSuccess) return e;
   if (precision == LBM_F64) return collide2d_async_configure<double>();
   if (precision == LBM_F32DEV) {

@@ -228,7 +228,8 @@ cudaError_t collide2d_tma_configure(int precision);
 bool fd2d_wave_eligible(const lbm_handle *h);
 cudaError_t fd2d_wave(lbm_handle *h, const KParams<float> &p, const float *src, float *dst, int sub,
                       int NY);
-int fd2d_wave_written_columns(int sub);
+cudaError_t fd2d_wave_configure();
+int fd2d_wave_slots(int sub, int *strips, int Lx);  // CTAs of one wave; strips of Lx
 int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
 
 }  // namespace hlbm

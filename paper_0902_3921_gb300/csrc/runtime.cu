@@ -402,13 +402,22 @@ int autotune_2d(lbm_handle *h) {
   std::vector<FdShape> cands;
   // wavefront kernel (FP32 phi): 128-column strips marching down segments of
   // `rows` output rows, 4 or 2 substeps per launch
+  // (one CTA marches a whole segment, so the segment heights offered are the
+  // ones that make the grid one to eight whole waves of resident CTAs)
   if (fd2d_wave_eligible(h)) {
     for (int sb : {4, 2}) {
       if (sb > h->m) continue;
-      for (int ny : {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 1024}) {
-        cands.push_back({1, 4, sb, std::min(ny, h->P.Ly)});
-        if (ny >= h->P.Ly) break;
+      int strips = 1;
+      const int slots = fd2d_wave_slots(sb, &strips, h->P.Lx);
+      std::vector<int> nys;
+      for (int w = 1; w <= 8 && slots > 0; w++) {
+        const int spp = w * slots / strips;  // segments per strip
+        if (spp < 1) continue;
+        const int ny = (h->P.Ly + spp - 1) / spp;
+        if (ny >= 8 && std::find(nys.begin(), nys.end(), ny) == nys.end()) nys.push_back(ny);
       }
+      if (nys.empty()) nys.push_back(std::min(h->P.Ly, 64));
+      for (int ny : nys) cands.push_back({1, 4, sb, ny});
     }
   }
   // block kernel (FP32): 128-column regions, (substeps, rows per warp)

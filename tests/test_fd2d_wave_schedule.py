@@ -5,10 +5,11 @@ substeps 3-4), run on the CPU against the oracle's FD substeps.
 The model follows the kernel's grid (128-column strips writing their inner
 128 - 2 HX columns, segments of NY output rows reading HY = 3 SUB rows on
 either side), its tick schedule (input row j lands at tick j; warp A works on
-row a = t - 1, warp B on b = t - 8), the per-lane input rings (slot j % 8,
-prefetched 6 rows ahead), the four-entry coefficient FIFO of each warp (slot
-t % 4), the shared coefficient ring (slot r % 8) and the two-slot phi_2
-hand-over.  Shuffles past the strip's edge read NaN, every ring slot starts
+row a = t - 1, warp B on b = t - 9), the per-lane input rings (slot j % 8,
+prefetched 6 rows ahead), the shared coefficient ring (slot r % 16 for four
+substeps, r % 4 for two; warp A writes row t - 1 and reads row t - 4, warp B
+reads rows t - 9 and t - 12) and the four-slot phi_2 hand-over, with one
+barrier after every second tick.  Shuffles past the strip's edge read NaN, every ring slot starts
 as NaN and keeps its last contents (the kernel computes through the fill and
 drain ticks on whatever the slots hold), writes to the shared rings become
 visible at the tick's barrier and may not touch a slot read in the same
@@ -19,19 +20,19 @@ import pytest
 
 import oracle as O
 
-W, IR, D, CR = 128, 8, 6, 8
+W, IR, D = 128, 8, 6
 
 
 def consts(sub):
     hy = 3 * sub
     hx = (3 * sub + 3) // 4 * 4
-    lag = 13 if sub == 4 else 6
+    lag = 14 if sub == 4 else 6
     return hy, hx, W - 2 * hx, lag
 
 
 def ticks(sub, NY):
     hy, _, _, lag = consts(sub)
-    return (NY + hy + lag + 3) // 4 * 4
+    return (NY + hy + lag + 1) // 2 * 2
 
 
 def left(x):
@@ -68,7 +69,7 @@ class Sub:
         return out
 
 
-def wave_model(phi, u, p, sub, NY, cubic_half=False, lag_b=13):
+def wave_model(phi, u, p, sub, NY, cubic_half=False, lag_b=14):
     Ly, Lx = phi.shape
     hy, hx, tx, lag = consts(sub)
     dt = 1.0 / p.m
@@ -84,9 +85,10 @@ def wave_model(phi, u, p, sub, NY, cubic_half=False, lag_b=13):
             J = NY + 2 * hy
             T = ticks(sub, NY)
             rings = {k: [(None, np.full(W, np.nan))] * IR for k in "puv"}
-            coef_ring = [(None, None)] * CR
-            hand = [(None, np.full(W, np.nan))] * 2
-            fifo_a, fifo_b = [(None, None)] * 4, [(None, None)] * 4
+            CR = 16 if sub == 4 else 4
+            coef_ring = [(None, (np.nan,) * 3)] * CR
+            hand = [(None, np.full(W, np.nan))] * 4
+            writes = {}
             sa1, sa2, sb1, sb2 = Sub(), Sub(), Sub(), Sub()
             vm = vc = np.full(W, np.nan)
 
@@ -105,21 +107,23 @@ def wave_model(phi, u, p, sub, NY, cubic_half=False, lag_b=13):
             for j in range(D):
                 issue(j)
             for t in range(T):
-                K = t % 4
                 # ---- warp A ----
                 issue(t + D)
                 pn, vn, uc = rd_in("p", t), rd_in("v", t), rd_in("u", t - 1)
                 cf = coef(uc, vm, vc, vn, dt)
                 vm, vc = vc, vn
-                fifo_a[K] = (t - 1, cf)
+                # warp A's own ring entries are visible to it at once (each lane
+                # reads back the columns it wrote); warp B sees them after the barrier
+                coef_ring[(t - 1) % CR] = (t - 1, cf)
                 o1 = sa1.step(pn, cf, p, dt, cubic_half)
-                tag, cf2 = fifo_a[(K + 1) % 4]
-                assert tag == t - 4 or t < 4, ("warp A FIFO", t, tag)
-                o2 = sa2.step(o1, cf2 if cf2 is not None else (np.nan,) * 3, p, dt, cubic_half)
-                writes = {}
+                tag, cf2 = coef_ring[(t - 4) % CR]
+                assert tag == t - 4 or t < 4, ("coefficient ring, warp A", t, tag)
+                o2 = sa2.step(o1, cf2, p, dt, cubic_half)
+                if t % 2 == 0:
+                    written_c = set()  # slots written since the last barrier
+                written_c.add((t - 1) % CR)
                 if sub == 4:
-                    writes[("c", (t - 1) % CR)] = (t - 1, cf)
-                    writes[("h", (t - 6) % 2)] = (t - 6, o2)
+                    writes[("h", (t - 6) % 4)] = (t - 6, o2)
                 else:
                     r = t - 6
                     if hy <= r < hy + NY and ys + r - hy < Ly:
@@ -129,30 +133,27 @@ def wave_model(phi, u, p, sub, NY, cubic_half=False, lag_b=13):
                             out[y, x0 + cc] = o2[cc]
                 # ---- warp B ----
                 if sub == 4:
-                    reads = {("h", (t - 7) % 2), ("c", (t - 8) % CR)}
-                    assert not (reads & set(writes)), ("ring slot read and written in one tick", t)
-                    htag, pnb = hand[(t - 7) % 2]
-                    assert htag == t - 7 or t < 7, ("hand-over", t, htag)
-                    ctag, cfb = coef_ring[(t - 8) % CR]
-                    assert ctag == t - 8 or t < 9, ("coefficient ring", t, ctag)
-                    cfb = cfb if cfb is not None else (np.nan,) * 3
-                    fifo_b[K] = (t - 8, cfb)
+                    assert not ({(t - 9) % CR, (t - 12) % CR} & written_c), ("coefficient slot race", t)
+                    assert ("h", (t - 8) % 4) not in writes, ("hand-over slot race", t)
+                    htag, pnb = hand[(t - 8) % 4]
+                    assert htag == t - 8 or t < 8, ("hand-over", t, htag)
+                    ctag, cfb = coef_ring[(t - 9) % CR]
+                    assert ctag == t - 9 or t < 10, ("coefficient ring, warp B", t, ctag)
                     o3 = sb1.step(pnb, cfb, p, dt, cubic_half)
-                    tag, cf4 = fifo_b[(K + 1) % 4]
-                    assert tag == t - 11 or t < 4, ("warp B FIFO", t, tag)
-                    o4 = sb2.step(o3, cf4 if cf4 is not None else (np.nan,) * 3, p, dt, cubic_half)
+                    ctag, cf4 = coef_ring[(t - 12) % CR]
+                    assert ctag == t - 12 or t < 13, ("coefficient ring, warp B", t, ctag)
+                    o4 = sb2.step(o3, cf4, p, dt, cubic_half)
                     r = t - lag_b
                     if hy <= r < hy + NY and ys + r - hy < Ly:
                         y = ys + r - hy
                         for cc in np.nonzero(col_ok)[0]:
                             assert np.isnan(out[y, x0 + cc]), ("written twice", y, x0 + cc)
                             out[y, x0 + cc] = o4[cc]
-                # barrier: the tick's writes become visible
-                for (kind, slot), val in writes.items():
-                    if kind == "c":
-                        coef_ring[slot] = val
-                    else:
+                # barrier after every second tick: the hand-over becomes visible
+                if t % 2 == 1:
+                    for (kind, slot), val in writes.items():
                         hand[slot] = val
+                    writes = {}
     return out
 
 
@@ -198,7 +199,7 @@ def test_wave_model_detects_a_wrong_lag():
     u = 0.05 * rng.standard_normal((2,) + shape)
     p = O.Params(Lx=128, Ly=24, m=4)
     ref = oracle_fd(p, phi, u, 4)
-    for lag_b in (12, 14):
+    for lag_b in (13, 15):
         with pytest.raises(AssertionError):
             got = wave_model(phi, u, p, 4, 12, lag_b=lag_b)
             assert not np.any(np.isnan(got))

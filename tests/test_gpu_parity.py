@@ -596,7 +596,7 @@ def test_block_kernel_flux_variant(shape, monkeypatch):
 
 # y-marching wavefront FD kernel (tile 1): substeps per launch 4 or 2, rows =
 # output rows of a segment
-WAVE_SHAPES = ["4,32,4,1,1", "4,7,4,1,1", "2,16,4,1,1", "4,256,4,1,1", "2,5,4,1,1"]
+WAVE_SHAPES = ["4,32,4,1,1", "4,7,4,1,1", "2,16,4,1,1", "4,256,4,1,1", "2,5,4,1,1", "2,200,4,1,1"]
 
 
 @pytest.mark.parametrize("shape", WAVE_SHAPES)
@@ -645,14 +645,17 @@ def test_wave_kernel_matches_block_kernel_spinodal(monkeypatch):
     n, u = I.rest(2, L, L)
     u = u + 0.004 * np.sin(np.arange(L) / 7.0)[None, None, :]
     out = []
-    for shape in ("4,96,2,5,128", "4,64,4,5,1"):
+    for shape in ("4,96,2,5,128", "4,64,4,5,1", "2,64,4,5,1"):
         monkeypatch.setenv("HLBM_TUNING", shape)
         lat = lbm.Lattice(lbm.LbmParams(Lx=L, Ly=L, fd_substeps=4, precision=lbm.LBM_F32DEV, **CFG1))
         lat.init_fields(n, phi, u).step(3)
         out.append(lat.moments())
         lat.close()
-    (n0, p0, u0), (n1, p1, u1) = out
+    (n0, p0, u0), (n1, p1, u1), (n2, p2, u2) = out
     assert np.max(np.abs(p0 - p1)) <= 2e-7 and np.max(np.abs(u0 - u1)) <= 1e-8
+    # four substeps in one launch or two launches of two: the wavefront kernel
+    # evaluates the same explicitly rounded formulas in the same order
+    assert np.array_equal(p1, p2) and np.array_equal(u1, u2)
 
 
 @pytest.mark.parametrize("kw", [dict(adv_variant=1), dict(precision=lbm.LBM_F64)])
