@@ -329,8 +329,11 @@ const char *lbm_net_last_error(const lbm_net *net);
  * process exits.
  *
  *   params  geometry and the a, b, kappa, T, N, Q used by p0; other fields
- *           are ignored.  At most LBM_NOALLOC_MAX_SITES sites: larger
- *           lattices return LBM_EINVAL ("exceed the ... capacity").
+ *           are ignored.  They are checked as lbm_create checks them (sides
+ *           >= 3; a finite and < 0, so that phi0 = sqrt(-a/b); b > 0; kappa
+ *           >= 0; T > 0; N and Q finite), and at most LBM_NOALLOC_MAX_SITES
+ *           sites: anything else returns LBM_EINVAL with a reason before
+ *           any CUDA call ("exceed the ... capacity" for a lattice too big).
  *   fields  DEVICE pointer to (2 + dims) * S doubles, [n | phi | u*_x | u*_y
  *           (| u*_z)], each block row-major [z][y][x] (what lbm_moments
  *           returns, laid end to end).  Read only.
@@ -341,9 +344,11 @@ const char *lbm_net_last_error(const lbm_net *net);
  *   out     host struct, filled on return (out->t = -1).
  * Waits for the stream.  Returns LBM_OK, LBM_ENONFINITE (out filled),
  * LBM_EINVAL or LBM_ECUDA; lbm_noalloc_last_error() describes the failure.
- * The first call on each device looks up the device address of the scratch
- * array with that device current; make that first call before any stream
- * capture.  All calls share the one array and leave the last call's values
+ * The first call in each CUDA context looks up the device address of the
+ * scratch array with that context current (the address belongs to the
+ * context: after cudaDeviceReset, or under another context of the same
+ * device, the next call looks it up again); make that first call in a
+ * context before any stream capture.  All calls share the one array and leave the last call's values
  * in it (each call writes every entry it reads, so nothing is cleared):
  * calls that overlap on the GPU (other streams, other host threads) race. */
 #define LBM_NOALLOC_MAX_BLOCKS 2048

@@ -220,3 +220,48 @@ def test_invalid_networks_are_rejected(lib, channels, layers):
         lbm.Net(channels, layers)
     assert ei.value.code == lbm.LBM_EINVAL
     assert "channels must be 16 or 32" in str(ei.value)
+
+
+NOALLOC_BAD = [
+    (dict(dims=4), "dims"),
+    (dict(Lx=2), "side"),
+    (dict(a=float("nan")), "a must be"),
+    (dict(a=0.05), "a must be"),
+    (dict(b=0.0), "b must be"),
+    (dict(kappa=float("inf")), "kappa"),
+    (dict(kappa=-1.0), "kappa"),
+    (dict(T=0.0), "T must be"),
+    (dict(T=float("nan")), "T must be"),
+    (dict(N=float("nan")), "N and Q"),
+    (dict(Q=float("inf")), "N and Q"),
+    # one site beyond the scratch capacity (4194305 = 838861 x 5)
+    (dict(Lx=838861, Ly=5), "capacity"),
+]
+
+
+@pytest.mark.parametrize("bad,why", NOALLOC_BAD)
+def test_noalloc_refuses_invalid_parameters_before_any_cuda_call(lib, bad, why):
+    """lbm_diagnostics_noalloc checks the fields it reads as lbm_create does,
+    and its site capacity, before touching the GPU (none is needed here)."""
+    kw = dict(Lx=64, Ly=64, a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    kw.update(bad)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_diagnostics_noalloc(lbm.LbmParams(**kw), 1 << 20)
+    assert ei.value.code == lbm.LBM_EINVAL
+    assert why in str(ei.value), str(ei.value)
+
+
+def test_noalloc_capacity_is_exactly_the_declared_maximum(lib):
+    """A lattice of exactly LBM_NOALLOC_MAX_SITES sites passes every check
+    before the CUDA calls (without a GPU the call then fails with ECUDA, not
+    EINVAL); one site more is refused."""
+    src = open(os.path.join(ROOT, "include", "hybrid_lbm.h")).read()
+    assert "#define LBM_NOALLOC_MAX_BLOCKS 2048" in src
+    assert "#define LBM_NOALLOC_MAX_SITES (LBM_NOALLOC_MAX_BLOCKS * 2048)" in src
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the ECUDA branch needs a machine without a GPU")
+    kw = dict(a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_diagnostics_noalloc(lbm.LbmParams(Lx=2048, Ly=2048, **kw), 1 << 20)
+    assert ei.value.code == lbm.LBM_ECUDA

@@ -75,10 +75,36 @@ def test_noalloc_matches_lbm_diagnostics_twice(dims, shape, prec):
     lat.close()
 
 
+def test_noalloc_at_full_capacity():
+    """Exactly LBM_NOALLOC_MAX_SITES sites (2048 x 2048): every block row of
+    the partial sums and the result vector stored right after them are used,
+    where an off-by-one in their offsets would show; compared with
+    lbm_diagnostics on the same state."""
+    import torch
+    from paper_0902_3921_gb300 import build as B
+    B.build()
+    lbm.load_library()
+    L = 2048
+    assert L * L == 2048 * 2048  # LBM_NOALLOC_MAX_SITES
+    p = lbm.LbmParams(Lx=L, Ly=L, precision=lbm.LBM_F32DEV, fd_substeps=4, **CFG1)
+    phi = I.drop(2, L, L, R=300, phi0=1.0, xi=np.sqrt(2.8))
+    n, u = I.rest(2, L, L)
+    u = u + 0.002 * np.sin(np.arange(L) / 9.0)[None, None, :]
+    lat = lbm.Lattice(p)
+    lat.init_fields(n, phi, u).step(10)
+    ref = lat.diagnostics()
+    f = _device_fields(lat)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        rc, got = lbm.lbm_diagnostics_noalloc(p, f.data_ptr(), r_ref=[L / 2.0, L / 2.0, 0.0])
+        assert rc == lbm.LBM_OK
+        _compare(got, ref)
+    lat.close()
+
+
 def test_noalloc_rejects_lattices_beyond_its_scratch():
     lbm.load_library()
-    side = int(np.sqrt(4096 * 2048)) + 1
-    p = lbm.LbmParams(Lx=side, Ly=side, **CFG1)
+    p = lbm.LbmParams(Lx=838861, Ly=5, **CFG1)  # 4194305 sites: the capacity plus one
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_diagnostics_noalloc(p, 1 << 20)
     assert ei.value.code == lbm.LBM_EINVAL
