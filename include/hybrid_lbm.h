@@ -105,7 +105,22 @@ typedef struct lbm_handle lbm_handle;
  * unknown precision/variant), picks m (Sec. II C), allocates device memory and
  * returns a handle in *out (NULL on error; the error text is then available
  * from lbm_last_error(NULL)).  cuda_stream is a cudaStream_t to queue work on,
- * or NULL for a stream owned by the handle.  Does not initialise the fields. */
+ * or NULL for a stream owned by the handle.  Does not initialise the fields.
+ * Testing the error paths (environment, read at each call):
+ *   LBM_FAULT=alloc    lbm_create returns LBM_ENOMEM as if the first device
+ *                      allocation failed, before any CUDA call;
+ *   LBM_FAULT=alloc:K  the K-th device allocation fails (LBM_ENOMEM; the
+ *                      earlier ones are freed);
+ *   LBM_FAULT=h2d      lbm_init_fields fails as if its host-to-device copy
+ *                      had (LBM_ECUDA, latched on the handle);
+ *   HLBM_DEBUG_TMA_WAIT_NS=<ns>  bound of the TMA collide kernels' waits for
+ *                      a tile's copies (default 0.5 s; process-wide, set by
+ *                      each lbm_create).  A short bound makes the wait give
+ *                      up: the kernel lets its issued copies land (that drain
+ *                      keeps the 0.5 s bound), skips the tile, and the
+ *                      handle reports LBM_ETIMEOUT at the next lbm_moments,
+ *                      lbm_diagnostics or lbm_synchronize.  The handle can
+ *                      then only be freed. */
 int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out);
 
 /* Device buffers a caller (for example a PyTorch program) allocates and lends

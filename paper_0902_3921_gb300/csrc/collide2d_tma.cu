@@ -88,6 +88,9 @@ __device__ __forceinline__ void cvt_st(float *d, float v, float) { *d = v; }
 __device__ __forceinline__ void cvt_st(__half *d, float v, float scale) { *d = __float2half_rn(v * scale); }
 
 __device__ int g_collide_tma_err = 0;
+// bound of the waits for a tile's copies (the drain waits of the give-up path
+// keep 0.5 s); the host shortens it only to exercise the give-up path
+__device__ unsigned long long g_collide_tma_wait_ns = 500000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -97,8 +100,11 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Waits for the mbarrier phase `parity` to complete; gives up after limit_ns.
+// Waits for the mbarrier phase `parity` to complete; gives up after limit_ns
+// (at once, without polling, when limit_ns is 0: try_wait itself may block
+// for a while, long enough for the copies to land).
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return false;
   const uint64_t t0 = gtimer();
   while (true) {
     uint32_t done;
@@ -197,9 +203,10 @@ __global__ void __launch_bounds__(256, MINB)
       spn[ry][rx] = p.cs2mT * (1.f + dn[(long long)gy * Lx + gx]);
     }
   }
-  const bool arrived = bar_wait(bar, 0, 500000000ull);
+  const bool arrived = bar_wait(bar, 0, g_collide_tma_wait_ns);
   if (!__syncthreads_and(arrived)) {
-    // the copies did not complete within 0.5 s: report, let them land, leave
+    // the copies did not complete within the wait bound: report, let them land
+    // (that drain keeps the 0.5 s bound), leave
     if (tid == 0) {
       atomicExch(&g_collide_tma_err, 1);
       bar_wait(bar, 0, 500000000ull);
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(256, MINB)
         spn[ry][rx] = p.cs2mT * (1.f + dn[(long long)gy * Lx + gx]);
       }
     }
-    const bool arrived = bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, 500000000ull);
+    const bool arrived = bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, g_collide_tma_wait_ns);
     if (!__syncthreads_and(arrived)) {
       failed = true;
       break;
@@ -740,7 +747,7 @@ __global__ void __launch_bounds__(256, MINB)
   }
   if (tid == 0) {
     if (failed) {
-      // a copy did not complete within 0.5 s: report it and let the copies
+      // a copy did not complete within the wait bound: report it and let the copies
       // still in flight land before the CTA's shared memory is released
       atomicExch(&g_collide_tma_err, 1);
       const int st = k & 1;
@@ -926,6 +933,10 @@ cudaError_t collide2d_tma_configure(int precision) {
     e = cudaFuncSetAttribute(collide2d_tma_pipe_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pipe_smem<true>());
   return e;
+}
+
+int collide2d_tma_set_wait_ns(unsigned long long ns) {
+  return cudaMemcpyToSymbol(g_collide_tma_wait_ns, &ns, sizeof ns) == cudaSuccess ? 0 : -1;
 }
 
 int collide2d_tma_error(bool reset) {

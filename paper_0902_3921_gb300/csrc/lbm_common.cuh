@@ -231,5 +231,6 @@ cudaError_t fd2d_wave(lbm_handle *h, const KParams<float> &p, const float *src, 
 cudaError_t fd2d_wave_configure();
 int fd2d_wave_slots(int sub, int *strips, int Lx);  // CTAs of one wave; strips of Lx
 int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
+int collide2d_tma_set_wait_ns(unsigned long long ns);  // bound of the copy waits (0 on success)
 
 }  // namespace hlbm

@@ -118,7 +118,7 @@ int cuda_fail(lbm_handle *h, cudaError_t e, const char *what) {
 // that gave up (its copies never completed) latches LBM_ETIMEOUT.
 int check_device_waits(lbm_handle *h) {
   if (h->tma_ready && collide2d_tma_error(true) > 0)
-    return fail(h, LBM_ETIMEOUT, "collide kernel: a TMA copy did not complete within 0.5 s");
+    return fail(h, LBM_ETIMEOUT, "collide kernel: a TMA copy did not complete within its wait bound");
   return LBM_OK;
 }
 
@@ -141,6 +141,26 @@ double fd_stiffness(const lbm_params &P) {
   const double lam = 4.0 * P.dims;
   const double aeff = P.a < 0 ? -2.0 * P.a : P.a;
   return P.Gamma * (aeff * lam + P.kappa * lam * lam);
+}
+
+// Host-side fault injection for testing the error paths (LBM_FAULT):
+// "alloc" refuses lbm_create as if the first device allocation failed, before
+// any CUDA call; "alloc:K" fails the K-th allocation (the earlier ones are
+// freed again); "h2d" fails the host-to-device copy of lbm_init_fields.
+// Returns the allocation index to fail (0: before any call, -1: none) for
+// "alloc", and sets *h2d for "h2d".
+int injected_fault(bool *h2d) {
+  *h2d = false;
+  const char *f = std::getenv("LBM_FAULT");
+  if (f == nullptr) return -1;
+  if (std::strcmp(f, "h2d") == 0) {
+    *h2d = true;
+    return -1;
+  }
+  if (std::strcmp(f, "alloc") == 0) return 0;
+  int k = 0;
+  if (std::sscanf(f, "alloc:%d", &k) == 1 && k >= 1) return k;
+  return -1;
 }
 
 int validate(const lbm_params *P, std::string &why) {
@@ -579,6 +599,10 @@ static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_bu
   std::string why;
   int rc = validate(params, why);
   if (rc) return fail(nullptr, rc, why);
+  bool fault_h2d = false;
+  const int fault_alloc = injected_fault(&fault_h2d);
+  if (fault_alloc == 0)
+    return fail(nullptr, LBM_ENOMEM, "injected fault (LBM_FAULT=alloc): device allocation refused");
   lbm_params P = *params;
   if (P.dims == 2) P.Lz = 1;
   if (P.precision == LBM_F16DEV && P.f16_scale_log2 == 0) P.f16_scale_log2 = 10;
@@ -649,8 +673,11 @@ static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_bu
     for (int k = 0; k < 3; k++) h->phi[k] = adopt->phi[k];
     h->u = adopt->u;
   }
+  int nalloc = 0;
   for (auto &a : allocs) {
     if (a.n == 0 || *a.p != nullptr) continue;  // adopted
+    if (++nalloc == fault_alloc)
+      return bail(fail(h, LBM_ENOMEM, "injected fault (LBM_FAULT=alloc:K): device allocation refused"));
     cudaError_t e = cudaMalloc(a.p, a.n);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaMalloc"));
   }
@@ -667,6 +694,14 @@ static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_bu
   } else {
     e = collide2d_configure(P.precision);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "collide shared-memory configuration"));
+    // bound of the TMA collide's copy waits: 0.5 s unless HLBM_DEBUG_TMA_WAIT_NS
+    // shortens it to exercise the give-up path (process-wide, set at each create)
+    if (P.precision != LBM_F64) {
+      unsigned long long wait_ns = 500000000ull;
+      if (const char *w = std::getenv("HLBM_DEBUG_TMA_WAIT_NS")) wait_ns = std::strtoull(w, nullptr, 10);
+      if (collide2d_tma_set_wait_ns(wait_ns) != 0)
+        return bail(fail(h, LBM_ECUDA, "TMA wait bound: cudaMemcpyToSymbol failed"));
+    }
     int rc2 = autotune_2d(h);
     if (rc2) return bail(rc2);
   }
@@ -680,6 +715,9 @@ int lbm_init_fields(lbm_handle *h, const double *n, const double *phi, const dou
   if (rc) return rc;
   if (!n || !phi || !ux || !uy || (h->dims == 3 && !uz))
     return fail(h, LBM_EINVAL, "lbm_init_fields: NULL input array");
+  bool fault_h2d = false;
+  injected_fault(&fault_h2d);
+  if (fault_h2d) return fail(h, LBM_ECUDA, "injected fault (LBM_FAULT=h2d): host-to-device copy failed");
   const size_t bytes = sizeof(double) * (size_t)h->S;
   const double *src[5] = {n, phi, ux, uy, uz};
   for (int k = 0; k < 2 + h->dims; k++)

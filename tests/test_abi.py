@@ -265,3 +265,14 @@ def test_noalloc_capacity_is_exactly_the_declared_maximum(lib):
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_diagnostics_noalloc(lbm.LbmParams(Lx=2048, Ly=2048, **kw), 1 << 20)
     assert ei.value.code == lbm.LBM_ECUDA
+
+
+def test_injected_allocation_fault_is_refused_before_any_cuda_call(lib, monkeypatch):
+    """LBM_FAULT=alloc: lbm_create reports LBM_ENOMEM as if the first device
+    allocation failed, before it touches the GPU (none is needed here)."""
+    monkeypatch.setenv("LBM_FAULT", "alloc")
+    kw = dict(Lx=64, Ly=64, a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Lattice(lbm.LbmParams(**kw))
+    assert ei.value.code == lbm.LBM_ENOMEM
+    assert "injected fault" in str(ei.value)
