@@ -51,7 +51,7 @@ class _Params(ctypes.Structure):
                 ("Gamma", ctypes.c_double), ("N", ctypes.c_double), ("Q", ctypes.c_double),
                 ("m", ctypes.c_int), ("adv_variant", ctypes.c_int),
                 ("cubic_at_half", ctypes.c_int), ("g", ctypes.c_double * 3),
-                ("force_steps", ctypes.c_long)]
+                ("force_steps", ctypes.c_long), ("stencil_fd", ctypes.c_int)]
 
 
 _lib = None
@@ -115,6 +115,7 @@ class Params:
     cubic_at_half: int = 0
     g: tuple = (0.0, 0.0, 0.0)
     force_steps: int = 0
+    stencil_fd: int = 0
 
     @property
     def shape(self):
@@ -138,6 +139,7 @@ class Params:
         p.adv_variant, p.cubic_at_half = self.adv_variant, self.cubic_at_half
         p.g = (ctypes.c_double * 3)(*[float(x) for x in self.g])
         p.force_steps = int(self.force_steps)
+        p.stencil_fd = int(self.stencil_fd)
         return ctypes.byref(p), p
 
 

@@ -49,6 +49,10 @@ typedef struct {
                           phi^{n+1/2} (an option for experiments)             */
   double g[3];         /* body force per unit density, Sec. III (G = n g)     */
   long force_steps;    /* G acts for LB steps t = 0 .. force_steps-1          */
+  int stencil_fd;      /* 0: Eqs. 33 and 36 as printed (central d u, 5-point
+                          Laplacian); 1: the stencil operators of Eqs. 30-31
+                          with (N, Q) in their place, the "more general
+                          stencil" of Sec. II C (after Eq. 36) and Sec. IV    */
 } orc_params;
 
 /* ---- lattices (Sec. II A, Fig. 1; D3Q19 is the 3D generalisation) -------- */
@@ -377,6 +381,17 @@ void orc_advect(const orc_params *p, const double *phi, const double *u,
   long S = orc_sites(p);
   int d = p->dims;
   int Lz = p->dims == 3 ? p->Lz : 1;
+  /* stencil_fd: d_alpha u_alpha by the stencil derivative of Eq. 30 */
+  double *du_st = NULL;
+  if (p->stencil_fd && p->adv_variant == 0) {
+    double *g = malloc(sizeof(double) * 3 * S);
+    du_st = malloc(sizeof(double) * 3 * S);
+    for (int al = 0; al < d; al++) {
+      orc_grad_D(p, u + al * S, g);
+      memcpy(du_st + al * S, g + al * S, sizeof(double) * S);
+    }
+    free(g);
+  }
   for (int z = 0; z < Lz; z++)
     for (int y = 0; y < p->Ly; y++)
       for (int x = 0; x < p->Lx; x++) {
@@ -390,7 +405,8 @@ void orc_advect(const orc_params *p, const double *phi, const double *u,
           long sm = nbr(p, x, y, z, dm[0], dm[1], dm[2]);
           const double *ua = u + al * S;
           if (p->adv_variant == 0) {
-            double du = (ua[sp] - ua[sm]) / 2.0;          /* Eq. 33 */
+            double du = du_st ? du_st[al * S + s]          /* Eq. 30 */
+                              : (ua[sp] - ua[sm]) / 2.0;   /* Eq. 33 */
             double dphi = ua[s] < 0.0 ? phi[sp] - phi[s]  /* Eq. 35 */
                                       : phi[s] - phi[sm]; /* Eq. 34 */
             tend += phi[s] * du + ua[s] * dphi;
@@ -404,13 +420,16 @@ void orc_advect(const orc_params *p, const double *phi, const double *u,
         }
         out[s] = phi[s] - dt * tend;
       }
+  free(du_st);
 }
 
 /*
  * Diffusive half step, Eq. 36:
  *   phi^{n+1} = phi^{n+1/2} + dt Gamma [a lap phi^{n+1/2} + b lap (phi^n)^3
  *                                       - kappa lap(lap phi^{n+1/2})]
- * with the standard Laplacian (Eq. 31 with Q = 1, R = 0).
+ * with the standard Laplacian (Eq. 31 with Q = 1, R = 0), or with lap_D of
+ * Eq. 31 at the stencil's (Q, R) when stencil_fd is set (Sec. II C, the
+ * sentence after Eq. 36: other stencils for this Laplacian are possible).
  */
 void orc_diffuse(const orc_params *p, const double *phi_half,
                  const double *phi_old, double dt, double *out) {
@@ -421,9 +440,10 @@ void orc_diffuse(const orc_params *p, const double *phi_half,
   double *lap_lap = malloc(sizeof(double) * S);
   const double *src = p->cubic_at_half ? phi_half : phi_old;
   for (long s = 0; s < S; s++) cube[s] = src[s] * src[s] * src[s];
-  orc_lap_std(p, phi_half, lap_h);
-  orc_lap_std(p, cube, lap_c);
-  orc_lap_std(p, lap_h, lap_lap);
+  void (*lap)(const orc_params *, const double *, double *) = p->stencil_fd ? orc_lap_D : orc_lap_std;
+  lap(p, phi_half, lap_h);
+  lap(p, cube, lap_c);
+  lap(p, lap_h, lap_lap);
   for (long s = 0; s < S; s++)
     out[s] = phi_half[s] + dt * p->Gamma *
                                (p->a * lap_h[s] + p->b * lap_c[s] -
