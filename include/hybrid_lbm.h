@@ -78,6 +78,16 @@ typedef struct {
   long long force_steps; /* G acts at steps t = 0 .. force_steps-1             */
   int precision;         /* LBM_F64, LBM_F32DEV or LBM_F16DEV                  */
   int f16_scale_log2;    /* FP16 scale exponent s (0 = default 10), 0..14      */
+  int stencil_fd;        /* 0: Eqs. 33 and 36 as printed (central d u, 5-point
+                            Laplacian); 1: the stencil operators of Eqs. 30-31
+                            at this N, Q for d u and the three Laplacians of
+                            Eq. 36 -- the "more general stencil" of Sec. II C
+                            (after Eq. 36) and Sec. IV.  2D, the printed
+                            advection form and Q >= 0 only (EINVAL otherwise);
+                            run by the shared-memory tile FD kernel.  lap_D's
+                            largest eigenvalue is max(8Q, 4) (8 for the
+                            5-point form), which the m of fd_substeps = 0 and
+                            the Euler bound take into account               */
 } lbm_params;
 
 /* FP64 observables (Sec. III) at the handle's current time t. */

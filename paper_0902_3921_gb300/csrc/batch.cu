@@ -500,6 +500,7 @@ int lbm_batch_create(const lbm_params *common, const lbm_instance *inst, int cou
       !std::isfinite(P.a) || !std::isfinite(P.N) || !std::isfinite(P.Q))
     return bfail(nullptr, LBM_EINVAL, "bad common parameters (tau > 1/2, b > 0, kappa, Gamma >= 0)");
   if (P.T != 1.0 / 3.0) return bfail(nullptr, LBM_EINVAL, "batches need T = 1/3");
+  if (P.stencil_fd != 0) return bfail(nullptr, LBM_EINVAL, "batches run Eqs. 33 and 36 as printed (stencil_fd = 0)");
   if (P.adv_variant != LBM_ADV_PAPER && P.adv_variant != LBM_ADV_FLUX)
     return bfail(nullptr, LBM_EINVAL, "unknown adv_variant");
   // FD substeps as for a single lattice (Sec. II C)

@@ -769,7 +769,22 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   // 2. advection coefficients of this thread's sites (registers)
   const bool paper = p.adv_variant == LBM_ADV_PAPER, cubic_half = p.cubic_at_half != 0;
+  const bool stencil = p.stencil_fd != 0;  // Eqs. 30-31 in place of Eq. 33 and the 5-point Laplacian
   const C dt = p.dt, dtG = p.dtG, a = p.a, b = p.b, kappa = p.kappa;
+  // lap of Eq. 36: the 5-point Laplacian, or lap_D of Eq. 31 (stencil_fd)
+  auto lap_at = [&](const C *f, int k) {
+    if (stencil) {
+      const C faces = (f[k - RXW] + f[k + RXW]) + (f[k - 1] + f[k + 1]);
+      const C corners = (f[k - RXW - 1] + f[k - RXW + 1]) + (f[k + RXW - 1] + f[k + RXW + 1]);
+      return p.Q * faces + p.R * corners + p.C0 * f[k];
+    }
+    C l = f[k - RXW];
+    l += f[k - 1];
+    l += C(-4) * f[k];
+    l += f[k + 1];
+    l += f[k + RXW];
+    return l;
+  };
   C c0[NYI][NXI], c1[NYI][NXI], c2[NYI][NXI], c3[NYI][NXI];
 #pragma unroll
   for (int yi = 0; yi < NYI; ++yi)
@@ -782,8 +797,14 @@ __global__ void __launch_bounds__(256)
       const C uc = sa[k], uL = sa[k - 1], uR = sa[k + 1];
       const C vc = sq[k], vm = sq[k - RXW], vp = sq[k + RXW];
       if (paper) {
-        // phih = c0 phi + |dt u| phi_upx + |dt v| phi_upy (Eqs. 32-35)
-        const C div = (uR - uL) / C(2) + (vp - vm) / C(2);
+        // phih = c0 phi + |dt u| phi_upx + |dt v| phi_upy (Eqs. 32-35); with
+        // stencil_fd the divergence by the stencil derivative of Eq. 30
+        C div = (uR - uL) / C(2) + (vp - vm) / C(2);
+        if (stencil) {
+          const C dux = p.N * (uR - uL) + p.M * ((sa[k - RXW + 1] - sa[k - RXW - 1]) + (sa[k + RXW + 1] - sa[k + RXW - 1]));
+          const C dvy = p.N * (vp - vm) + p.M * ((sq[k + RXW + 1] - sq[k - RXW + 1]) + (sq[k + RXW - 1] - sq[k - RXW - 1]));
+          div = dux + dvy;
+        }
         c0[yi][xi] = C(1) - dt * (div + (fabs(uc) + fabs(vc)));
         c1[yi][xi] = dt * uc;
         c2[yi][xi] = dt * vc;
@@ -834,11 +855,7 @@ __global__ void __launch_bounds__(256)
         const int k = ry * RXW + rx;
         const C hk = sa[k];
         const C c = cubic_half ? hk : sp[k];
-        C lap = sa[k - RXW];
-        lap += sa[k - 1];
-        lap += C(-4) * hk;
-        lap += sa[k + 1];
-        lap += sa[k + RXW];
+        const C lap = lap_at(sa, k);
         sq[k] = a * hk + b * (c * c * c) - kappa * lap;
       }
     __syncthreads();
@@ -850,11 +867,7 @@ __global__ void __launch_bounds__(256)
         const int ry = ty + 8 * yi, rx = tx + 32 * xi;
         if (ry < lo || ry >= RY - lo || rx < lo || rx >= RXW - lo) continue;
         const int k = ry * RXW + rx;
-        C lap = sq[k - RXW];
-        lap += sq[k - 1];
-        lap += C(-4) * sq[k];
-        lap += sq[k + 1];
-        lap += sq[k + RXW];
+        const C lap = lap_at(sq, k);
         sp[k] = sa[k] + dtG * lap;
       }
     __syncthreads();

@@ -124,6 +124,7 @@ struct KParams {
   C dt, dtG;                // FD step 1/m and Gamma/m (Sec. II C)
   C scale, inv_scale;       // FP16 storage scale 2^s and its inverse (1 otherwise)
   int adv_variant, cubic_at_half;
+  int stencil_fd;           // 2D FD: stencil d u (Eq. 30) and lap_D (Eq. 31)
 };
 
 // ---- handle -------------------------------------------------------------------

@@ -65,6 +65,7 @@ KParams<C> make_params(const lbm_handle *h, int force_on) {
   }
   p.adv_variant = P.adv_variant;
   p.cubic_at_half = P.cubic_at_half;
+  p.stencil_fd = P.stencil_fd;
   return p;
 }
 template KParams<float> make_params<float>(const lbm_handle *, int);
@@ -137,8 +138,12 @@ size_t compute_bytes(int precision) { return precision == LBM_F64 ? 8 : 4; }
 // Gamma (a_eff lam + kappa lam^2), lam = 4 d the largest eigenvalue of the
 // 5-point (7-point) Laplacian and a_eff = a + 3 b phi0^2 = -2a in the ordered
 // phase (a < 0), a otherwise.
+// Largest eigenvalue lam of -lap over the Brillouin zone: 4 d for the 5/7-point
+// Laplacian; for lap_D of Eq. 31 (stencil_fd, 2D) the symbol 4(Q + R) -
+// 2Q (cos kx + cos ky) - 4R cos kx cos ky is bilinear in the cosines, so its
+// maximum is at a corner: max(8Q, 4).
 double fd_stiffness(const lbm_params &P) {
-  const double lam = 4.0 * P.dims;
+  const double lam = (P.stencil_fd && P.dims == 2) ? std::max(8.0 * P.Q, 4.0) : 4.0 * P.dims;
   const double aeff = P.a < 0 ? -2.0 * P.a : P.a;
   return P.Gamma * (aeff * lam + P.kappa * lam * lam);
 }
@@ -187,6 +192,11 @@ int validate(const lbm_params *P, std::string &why) {
   if (P->f16_scale_log2 < 0 || P->f16_scale_log2 > 14)
     return why = "f16_scale_log2 must be in 0..14", LBM_EINVAL;
   if (std::abs(P->fd_substeps) > 4096) return why = "fd_substeps too large", LBM_EINVAL;
+  if (P->stencil_fd != 0 && P->stencil_fd != 1) return why = "stencil_fd must be 0 or 1", LBM_EINVAL;
+  if (P->stencil_fd && (P->dims != 2 || P->adv_variant != LBM_ADV_PAPER))
+    return why = "stencil_fd is a 2D option of the printed advection form", LBM_EINVAL;
+  if (P->stencil_fd && !(P->Q >= 0.0))
+    return why = "stencil_fd needs Q >= 0 (lap_D is otherwise not negative semi-definite)", LBM_EINVAL;
   return LBM_OK;
 }
 
@@ -330,7 +340,7 @@ bool same_params(const lbm_params &a, const lbm_params &b) {
          a.Gamma == b.Gamma && a.N == b.N && a.Q == b.Q && a.fd_substeps == b.fd_substeps &&
          a.adv_variant == b.adv_variant && a.cubic_at_half == b.cubic_at_half &&
          a.g[0] == b.g[0] && a.g[1] == b.g[1] && a.g[2] == b.g[2] &&
-         a.force_steps == b.force_steps && a.precision == b.precision &&
+         a.force_steps == b.force_steps && a.precision == b.precision && a.stencil_fd == b.stencil_fd &&
          a.f16_scale_log2 == b.f16_scale_log2;
 }
 
@@ -368,6 +378,8 @@ int autotune_2d(lbm_handle *h) {
                   "HLBM_TUNING wavefront FD kernel (tile 1): sub 2 or 4 (m >= 2), FP32 or FP16 storage, "
                   "printed advection form, Lx % 4 == 0");
     }
+    if (h->P.stencil_fd && !(nv == 5 && (v[4] == 32 || v[4] == 64)))
+      return fail(h, LBM_EINVAL, "HLBM_TUNING: stencil_fd runs on the tile FD kernel (tile 32 or 64)");
     if ((nv == 4 || (nv == 5 && (v[4] == 0 || v[4] == 32 || v[4] == 64 || block_ok || wave_ok))) && v[0] >= 1 &&
         v[0] <= 4 && v[1] >= 1 && (v[2] == 2 || v[2] == 4) &&
         (v[3] == 2 || v[3] == 4 || (v[3] <= 1 && v[3] >= 0 && h->P.precision != LBM_F16DEV) ||
@@ -420,11 +432,12 @@ int autotune_2d(lbm_handle *h) {
     int tile_w, cols, sub, rows;
   };
   std::vector<FdShape> cands;
+  const bool stencil = h->P.stencil_fd != 0;  // only the tile kernel evaluates the stencil operators
   // wavefront kernel (FP32 phi): 128-column strips marching down segments of
   // `rows` output rows, 4 or 2 substeps per launch
   // (one CTA marches a whole segment, so the segment heights offered are the
   // ones that make the grid one to eight whole waves of resident CTAs)
-  if (fd2d_wave_eligible(h)) {
+  if (fd2d_wave_eligible(h) && !stencil) {
     for (int sb : {4, 2}) {
       if (sb > h->m) continue;
       int strips = 1;
@@ -441,7 +454,7 @@ int autotune_2d(lbm_handle *h) {
     }
   }
   // block kernel (FP32): 128-column regions, (substeps, rows per warp)
-  if (h->P.precision != LBM_F64) {
+  if (h->P.precision != LBM_F64 && !stencil) {
     if (h->m >= 4) {
       cands.push_back({128, 2, 4, 80});
       cands.push_back({128, 2, 4, 96});
@@ -462,6 +475,7 @@ int autotune_2d(lbm_handle *h) {
   const int subs[3] = {std::min(h->m, 4), std::min(h->m, 2), 1};
   const int rows[5] = {8, 16, 32, 64, 128};
   for (int cols : {4, 2}) {
+    if (stencil) break;
     if (cols == 4 && h->P.precision == LBM_F64) continue;
     for (int si = 0; si < 3; si++) {
       if (si > 0 && subs[si] == subs[si - 1]) continue;
@@ -867,7 +881,7 @@ int lbm_save(lbm_handle *h, const char *path) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof hd);
   std::memcpy(hd.magic, "HLBMCKP", 8);
-  hd.version = 1;
+  hd.version = 2;  // 2: lbm_params carries stencil_fd
   hd.t = h->t;
   hd.payload = (long long)buf.size();
   hd.P = h->P;
@@ -891,8 +905,8 @@ int lbm_load(lbm_handle *h, const char *path) {
   std::vector<unsigned char> buf;
   const char *why = nullptr;
   if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "HLBMCKP", 8) != 0 ||
-      hd.version != 1)
-    why = "not a version-1 checkpoint";
+      hd.version != 2)
+    why = "not a version-2 checkpoint";
   else if (hd.payload != (long long)(h->hbytes + h->phibytes) || !same_params(hd.P, h->P))
     why = "written by a handle with other parameters";
   if (!why) {

@@ -53,7 +53,7 @@ class c_lbm_params(ctypes.Structure):
                 ("fd_substeps", ctypes.c_int), ("adv_variant", ctypes.c_int),
                 ("cubic_at_half", ctypes.c_int), ("g", ctypes.c_double * 3),
                 ("force_steps", ctypes.c_longlong), ("precision", ctypes.c_int),
-                ("f16_scale_log2", ctypes.c_int)]
+                ("f16_scale_log2", ctypes.c_int), ("stencil_fd", ctypes.c_int)]
 
 
 class c_lbm_diag(ctypes.Structure):
@@ -207,6 +207,7 @@ class LbmParams:
     force_steps: int = 0
     precision: int = LBM_F32DEV
     f16_scale_log2: int = 0
+    stencil_fd: int = 0
 
     def to_c(self) -> c_lbm_params:
         c = c_lbm_params()

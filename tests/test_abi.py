@@ -276,3 +276,15 @@ def test_injected_allocation_fault_is_refused_before_any_cuda_call(lib, monkeypa
         lbm.Lattice(lbm.LbmParams(**kw))
     assert ei.value.code == lbm.LBM_ENOMEM
     assert "injected fault" in str(ei.value)
+
+
+@pytest.mark.parametrize("bad", [dict(stencil_fd=2), dict(stencil_fd=1, dims=3, Lz=8, N=1 / 6, Q=1 / 3),
+                                 dict(stencil_fd=1, adv_variant=1), dict(stencil_fd=1, Q=-0.5)])
+def test_stencil_fd_refusals_before_any_cuda_call(lib, bad):
+    """stencil_fd is 0 or 1, 2D only, and only with the printed advection form
+    (the paper defines no stencil for the upwind fluxes)."""
+    kw = dict(Lx=64, Ly=64, a=-0.1, b=0.1, kappa=0.14, tau=1.0, Gamma=0.5, N=0.3, Q=2.5)
+    kw.update(bad)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Lattice(lbm.LbmParams(**kw))
+    assert ei.value.code == lbm.LBM_EINVAL and "stencil_fd" in str(ei.value)

@@ -428,52 +428,49 @@ def test_handle_on_torch_buffers(precision):
     assert torch.isfinite(bufs["populations"][0]).all()  # still usable after the handle is freed
 
 
-def _table1():
-    rows = []
-    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table1_spurious_velocities.txt")):
-        if line.strip() and not line.startswith("#"):
-            rows.append(tuple(float(v) for v in line.split()))
-    return rows
+@pytest.mark.parametrize("shape", ["1,32,4,0,32", "1,32,4,2,64", "2,32,4,4,64"])
+@pytest.mark.parametrize("precision", [lbm.LBM_F64, lbm.LBM_F32DEV])
+def test_stencil_fd_against_oracle(shape, precision, monkeypatch):
+    """stencil_fd = 1 (the stencil operators of Eqs. 30-31 in Eqs. 33 and 36,
+    Sec. II C after Eq. 36 and Sec. IV) on the tile FD kernel, against the
+    oracle with the same option: FP64 at 1e-11, FP32 at the FP32 bar; a
+    lattice smaller than a tile and an odd m (a remainder launch).  lap_D with
+    Q = 2.5 has the largest eigenvalue 8Q = 20 (8 for the 5-point form), so
+    Eq. 36 needs m = 21 here for dt x stiffness <= 1.5."""
+    monkeypatch.setenv("HLBM_TUNING", shape)
+    kw = dict(CFG1, stencil_fd=1)
+    op, lp = _pair(70, 45, m=21, precision=precision, **kw)
+    phi = I.drop(2, 70, 45, R=12, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 70, 45)
+    u = u + 0.003 * np.sin(np.arange(70) / 4.0)[None, None, :]
+    u[1] += 0.002 * np.cos(np.arange(45) / 3.0)[:, None]
+    ref, lat = _run_both(op, lp, n, phi, u, 25)
+    if precision == lbm.LBM_F64:
+        dphi, du, dn = _errors(ref, lat)
+        assert dphi <= 1e-11 and du <= 1e-12 and dn <= 1e-11, (shape, dphi, du, dn)
+    else:
+        _fp32_bar(ref, lat, shape)
 
 
-def _drop128_umax(tau, N, Q, steps):
-    L = 128
-    p = lbm.LbmParams(Lx=L, Ly=L, a=-1e-3, b=1e-3, kappa=3e-3, tau=tau, Gamma=5.0, N=N, Q=Q,
-                      precision=lbm.LBM_F64)
-    phi = I.drop(2, L, L, R=32, phi0=1.0, xi=np.sqrt(2 * 3e-3 / 1e-3))
-    n, u = I.rest(2, L, L)
-    lat = lbm.Lattice(p).init_fields(n, phi, u)
-    lat.step(steps)
-    umax = lat.diagnostics()["u_max"] * np.sqrt(3.0)
-    lat.close()
-    return umax
-
-
-def test_table1_spurious_velocities():
-    """Sec. III, Table I (tests/golden/table1_spurious_velocities.txt): the
-    equilibrated drop's maximum spurious velocity for the paper's optimal
-    (N, Q) at each tau.  The paper states neither the run length nor the
-    initial profile; after 40 000 steps from a tanh profile the FP64 path
-    gives the printed values within a factor of 1.7 over two decades (within
-    6-37 % at 200 000 steps), decreasing with tau as printed.
-
-    With the SC stencils (N = 1/2, Q = 1) the force's Laplacian is the
-    5-point one that Eq. 36 uses (Sec. II C), so the discrete system has an
-    exact stationary drop with u* = 0: mu_D is uniform once the diffusion has
-    converged and -phi d_D mu_D vanishes.  The SC velocity therefore decays
-    far below the OC value instead of exceeding it ten-fold as Fig. 4 shows;
-    the test pins the property of the scheme as printed."""
-    rows = _table1()
-    got = []
-    for tau, N, Q, paper in rows:
-        umax = _drop128_umax(tau, N, Q, 40000)
-        print(f"Table I: tau {tau} N {N} Q {Q}: |u*_max|/c_s = {umax:.3e} (paper {paper:.3e})")
-        assert paper / 1.7 <= umax <= paper * 1.7, (tau, umax, paper)
-        got.append(umax)
-    assert all(a > b for a, b in zip(got[:5], got[1:5]))  # tau = 0.6 .. 5: decreasing
-    sc = _drop128_umax(1.0, 0.5, 1.0, 40000)
-    print(f"SC stencils at tau 1: |u*_max|/c_s = {sc:.3e}")
-    assert sc < 0.02 * got[2]
+def test_stencil_fd_autotuned_and_differs_from_printed():
+    """An autotuned stencil_fd handle runs the tile kernel and matches the
+    oracle; with OC stencils its result differs from the printed scheme's."""
+    kw = dict(CFG1, stencil_fd=1)
+    op, lp = _pair(96, 64, m=21, precision=lbm.LBM_F64, **kw)
+    phi = I.drop(2, 96, 64, R=16, phi0=O.phi0_of(op), xi=O.xi_of(op))
+    n, u = I.rest(2, 96, 64)
+    ref, lat = _run_both(op, lp, n, phi, u, 40)
+    dphi, du, _ = _errors(ref, lat)
+    assert dphi <= 1e-11 and du <= 1e-12
+    assert lbm.lbm_tuning(lat.handle)["fd_tile_width"] in (32, 64)
+    # the automatic m follows lap_D's spectrum: stiffness 30 -> m = 20
+    auto = lbm.Lattice(lbm.LbmParams(Lx=96, Ly=64, precision=lbm.LBM_F64, **kw))
+    assert lbm.lbm_fd_substeps(auto.handle) == 20
+    auto.close()
+    op0 = O.Params(**{**op.__dict__, "stencil_fd": 0})
+    ref0 = O.State.create(op0, n, phi, u)
+    ref0.run(40)
+    assert np.max(np.abs(ref0.phi - ref.phi)) > 1e-9
 
 
 def test_checkpoint_roundtrip_bitwise(tmp_path):
