@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                           "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -89,10 +89,18 @@ def lib():
             fn.restype = None
         _lib.orc_nq.argtypes = [ctypes.c_int]
         _lib.orc_nq.restype = ctypes.c_int
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
+        _lib.orc_set_threads.restype = ctypes.c_int
         _lib.orc_lattice.argtypes = [ctypes.c_int, np.ctypeslib.ndpointer(dtype=np.int32),
                                      dp]
         _lib.orc_lattice.restype = None
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's site loops (0: all cores); returns the count.
+    Any count gives the same bits (no reduction crosses sites)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 @dataclass

@@ -13,7 +13,10 @@
  * in the paper's order and notation.  No blocking, no fusion, no
  * reordering: each operator is applied to a whole field before the next one
  * starts.  All arithmetic is IEEE double, round-to-nearest; the build uses
- * -ffp-contract=off so x86-64 and AArch64 give the same bits.
+ * -ffp-contract=off so x86-64 and AArch64 give the same bits.  The site loops
+ * carry OpenMP pragmas: every site's value is computed by the same
+ * operations whichever thread runs it (no reduction crosses sites), so any
+ * thread count gives the same bits as one thread (orc_set_threads).
  *
  * Conventions (the paper is silent on them; the readings are listed in the
  * design notes of the repository):
@@ -34,6 +37,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int dims;            /* 2 (D2Q9) or 3 (D3Q19)                               */
@@ -78,6 +84,19 @@ static const double W3Q19[19] = {
 static const double CS2 = 1.0 / 3.0; /* c_s^2 = c^2/3, Sec. II A */
 
 int orc_nq(int dims) { return dims == 3 ? 19 : 9; }
+
+/* Threads of the site loops (n <= 0: all cores); returns the count in use.
+ * The result of every function is the same for any count. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n <= 0) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return n;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 static const int *orc_e(int dims, int i) {
   return dims == 3 ? E3Q19[i] : E2Q9[i];
@@ -156,6 +175,7 @@ static void apply_stencil(const orc_params *p, const double *w,
                           const double *field, double *out) {
   int Lz = p->dims == 3 ? p->Lz : 1;
   int zlo = p->dims == 3 ? -1 : 0, zhi = p->dims == 3 ? 1 : 0;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < Lz; z++)
     for (int y = 0; y < p->Ly; y++)
       for (int x = 0; x < p->Lx; x++) {
@@ -200,6 +220,7 @@ void orc_mu(const orc_params *p, const double *phi, double *mu) {
   long S = orc_sites(p);
   double *lap = malloc(sizeof(double) * S);
   orc_lap_D(p, phi, lap);
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++)
     mu[s] = p->a * phi[s] + p->b * phi[s] * phi[s] * phi[s] -
             p->kappa * lap[s];
@@ -278,6 +299,7 @@ void orc_forcing_term(int dims, double tau, const double *u, const double *F,
 void orc_density(const orc_params *p, const double *f, double *n) {
   long S = orc_sites(p);
   int q = orc_nq(p->dims);
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++) {
     double acc = 0.0;
     for (int i = 0; i < q; i++) acc += f[i * S + s];
@@ -291,6 +313,7 @@ void orc_moments(const orc_params *p, const double *f, const double *F,
   long S = orc_sites(p);
   int q = orc_nq(p->dims), d = p->dims;
   orc_density(p, f, n);
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++)
     for (int al = 0; al < d; al++) {
       double j = 0.0;
@@ -309,8 +332,9 @@ void orc_init(const orc_params *p, const double *n, const double *phi,
   int q = orc_nq(p->dims), d = p->dims;
   double *F = malloc(sizeof(double) * S * d);
   orc_force(p, phi, n, 0, F);
-  double us[3] = {0, 0, 0}, feq[19];
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++) {
+    double us[3] = {0, 0, 0}, feq[19];
     for (int al = 0; al < d; al++)
       us[al] = u[al * S + s] - F[al * S + s] / (2.0 * n[s]);
     orc_feq(d, n[s], us, feq);
@@ -337,8 +361,9 @@ void orc_lb_step(const orc_params *p, double *f, const double *phi, long t,
   orc_density(p, f, n);
   orc_force(p, phi, n, t, F);
   orc_moments(p, f, F, n, u);
-  double us[3] = {0, 0, 0}, Fs[3] = {0, 0, 0}, feq[19], Fi[19];
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++) {
+    double us[3] = {0, 0, 0}, Fs[3] = {0, 0, 0}, feq[19], Fi[19];
     for (int al = 0; al < d; al++) {
       us[al] = u[al * S + s];
       Fs[al] = F[al * S + s];
@@ -352,6 +377,7 @@ void orc_lb_step(const orc_params *p, double *f, const double *phi, long t,
   /* streaming: the left-hand side of Eq. 17, periodic */
   for (int i = 0; i < q; i++) {
     const int *e = orc_e(d, i);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < Lz; z++)
       for (int y = 0; y < p->Ly; y++)
         for (int x = 0; x < p->Lx; x++)
@@ -392,6 +418,7 @@ void orc_advect(const orc_params *p, const double *phi, const double *u,
     }
     free(g);
   }
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < Lz; z++)
     for (int y = 0; y < p->Ly; y++)
       for (int x = 0; x < p->Lx; x++) {
@@ -439,11 +466,13 @@ void orc_diffuse(const orc_params *p, const double *phi_half,
   double *lap_c = malloc(sizeof(double) * S);
   double *lap_lap = malloc(sizeof(double) * S);
   const double *src = p->cubic_at_half ? phi_half : phi_old;
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++) cube[s] = src[s] * src[s] * src[s];
   void (*lap)(const orc_params *, const double *, double *) = p->stencil_fd ? orc_lap_D : orc_lap_std;
   lap(p, phi_half, lap_h);
   lap(p, cube, lap_c);
   lap(p, lap_h, lap_lap);
+#pragma omp parallel for schedule(static)
   for (long s = 0; s < S; s++)
     out[s] = phi_half[s] + dt * p->Gamma *
                                (p->a * lap_h[s] + p->b * lap_c[s] -
