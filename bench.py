@@ -157,27 +157,69 @@ def make_inputs(seed, side=None):
     return n, phi, u
 
 
-def cpu_oracle_mlups(steps=1, seed=0):
-    """The FP64 oracle as it stands, single thread, `steps` LB steps of the
-    1024^2 workload.  Returns (MLUPS, seconds)."""
+def cpu_identity():
+    """This host's logical CPU count and model name (lscpu, else /proc/cpuinfo)."""
+    import platform
+    import subprocess
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def cpu_oracle_mlups(steps=1, seed=0, threads=1):
+    """The FP64 oracle as it stands, `steps` LB steps of the 1024^2 workload
+    on `threads` threads (0: all cores; its OpenMP site loops give the same
+    bits for any count).  Returns (MLUPS, seconds, threads used)."""
     import oracle as O
     O.build()
+    used = O.set_threads(threads)
     op = O.Params(Lx=L, Ly=L, m=M_SUB, **CFG)
     n, phi, u = make_inputs(seed)
     st = O.State.create(op, n, phi, u)
     t0 = time.perf_counter()
     st.run(steps)
     dt = time.perf_counter() - t0
-    return L * L * steps / dt / 1e6, dt
+    O.set_threads(0)
+    return L * L * steps / dt / 1e6, dt, used
+
+
+def cpu_baseline_line(single_steps):
+    """The oracle on one thread and on all host cores (about 10-20 s of CPU
+    work on the 16-core host of the GPU machine): the all-core figure is the
+    baseline, the single-thread one is reported beside it."""
+    m1, dt1, _ = cpu_oracle_mlups(single_steps, threads=1)
+    steps_all = 4 * single_steps
+    mn, dtn, used = cpu_oracle_mlups(steps_all, threads=0)
+    return {"value": mn, "unit": "MLUPS", "cores": used, "kind": "oracle",
+            "sample": f"{steps_all} LB steps of the 1024x1024 workload on {used} threads ({dtn:.1f} s)",
+            "single_thread": {"value": m1, "unit": "MLUPS", "cores": 1,
+                              "sample": f"{single_steps} LB steps of the same workload ({dt1:.1f} s)"},
+            "host": cpu_identity()}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cores = 1
     times = []
+    cores = 1
     for k in range(args.warmup + args.steps):
-        mlups, dt = cpu_oracle_mlups(1, seed=k)
+        mlups, dt, cores = cpu_oracle_mlups(1, seed=k, threads=0)
         if k >= args.warmup:
             times.append(dt)
     total = sum(times)
@@ -188,9 +230,11 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": [L, L],
                        "lb_steps_per_timed_step": 1,
-                       "note": "FP64 CPU oracle, single thread, one LB step per timed step"},
+                       "note": f"FP64 CPU oracle on {cores} threads (OpenMP site loops), one LB step "
+                               "per timed step"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} LB steps of the 1024x1024 workload"},
+                             "sample": f"{args.steps} LB steps of the 1024x1024 workload",
+                             "host": cpu_identity()},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -299,6 +343,25 @@ def run_ours(args, rank, world, local):
                "launches_per_lb_step": fd_launches_per_step,
                "avg_launch_us": fd_avg_s * 1e6, "peak_kind": "derived (unit counts x clock)",
                "share_of_step": fd_ms / (coll_ms + fd_ms)}
+    # the same kernels inside the graph-timed step: their event times above
+    # are taken on eager launches (each bracketed by events, no programmatic
+    # overlap), which sum to more than the graph step; the in-step figures
+    # share the graph step's time in the proportion of the event times
+    graph_lb_us = ms_max / (args.steps * LB_PER_STEP) * 1000.0
+    eager_lb_us = (coll_ms + fd_ms) / 2000.0 * 1000.0
+    share_c = coll_ms / (coll_ms + fd_ms)
+    c_in = share_c * graph_lb_us
+    f_in = (1.0 - share_c) * graph_lb_us / fd_launches_per_step
+    roof_collide.update({"in_step_us": c_in,
+                         "frac_in_step": COLLIDE_BYTES_PER_SITE * S / (c_in * 1e-6) / 1e9 / peak})
+    roof_fd.update({"in_step_us": f_in,
+                    "frac_in_step": fd_flops_launch / (f_in * 1e-6) / 1e12 / FP32_PEAK_TFLOPS})
+    kernel_times = {"graph_lb_step_us": graph_lb_us, "eager_lb_step_us": eager_lb_us,
+                    "graph_over_eager": graph_lb_us / eager_lb_us,
+                    "collide_us_per_lb_step_eager": coll_ms / 2000.0 * 1000.0,
+                    "fd_us_per_lb_step_eager": fd_ms / 2000.0 * 1000.0,
+                    "note": "avg_launch_us: CUDA events around eager launches; in_step_us: the graph-timed "
+                            "step split in the proportion of those times (they add up to the step)"}
     dominant, other = (roof_fd, roof_collide) if fd_ms > coll_ms else (roof_collide, roof_fd)
 
     # end to end through the C ABI with host buffers: H2D of the inputs from
@@ -330,11 +393,7 @@ def run_ours(args, rank, world, local):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            steps_cpu = args.cpu_sample_steps
-            mlups, dt = cpu_oracle_mlups(steps_cpu)
-            cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                   "sample": f"{steps_cpu} LB steps of the 1024x1024 workload "
-                             f"({dt:.1f} s, single thread)"}
+            cpu = cpu_baseline_line(args.cpu_sample_steps)
         sub = max(1, tuning["fd_substeps_per_launch"])
         fd_launches = (M_SUB + sub - 1) // sub
         gpu_launches = args.steps * LB_PER_STEP * (1 + fd_launches)
@@ -358,15 +417,34 @@ def run_ours(args, rank, world, local):
                     "lb_steps_per_step": LB_PER_STEP},
             "gpu_launches": gpu_launches,
             "clocks": clocks.summary(),
+            "kernel_times": kernel_times,
         }
         if side == L and not args.no_large:
             line["large_lattice"] = large_lattice(args.large_side, stream)
             line["f16_storage"] = {"1024": f16_storage(side, 2000, stream),
                                    str(args.large_side): f16_storage(args.large_side, 200, stream)}
+        if side == L and not args.no_forms:
+            line["forms"] = other_forms(local, rank, stream)
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def other_forms(local, rank, stream):
+    """Short, bounded runs of the other forms of the path, on the same GPU:
+    the 512-instance batch (200 LB steps), the 256^3 D3Q19 drop (FP32 and
+    FP16 deviations, 3 x 10 LB steps) and the learned surrogate (forward pass
+    on 2048^2, and the trained network's speedup at fixed error from
+    t = 2000 to 16000)."""
+    out = {"batched": batched_form(200, local, rank, stream),
+           "drop3d": drop3d_form(D3_SIDE, 3, 2, local, stream)}
+    fwd, net, x0, x1 = surrogate_forward(400, 3, local, rank, stream)
+    net.close()
+    del x0, x1
+    fwd["fixed_error"] = surrogate_fixed_error(SURR_SIDE)
+    out["surrogate"] = fwd
+    return out
 
 
 # bytes per site and LB step the method must carry between steps (FP32
@@ -475,6 +553,68 @@ def large_lattice(side, stream):
             "fd_avg_launch_us": fms / fn * 1000.0, "fd_launches_per_lb_step": fn / 100.0}
 
 
+def batched_form(steps, local, rank, stream):
+    """512 independent drops (sides 32..256, half pushed by g_x = 1e-5 for the
+    first 2000 of 6000 steps) advanced by one persistent launch per LB step
+    (captured in a CUDA graph), FP32 deviations, `steps` LB steps timed after
+    as many warm-up steps; compared with the plain kernels on one square
+    lattice of (about) the same number of sites, timed the same way."""
+    import torch
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    desc = I.batch_instances(512, seed=rank)
+    insts = [(d["side"], d["side"], (1e-5 if d["forced"] else 0.0, 0.0),
+              2000 if d["forced"] else 0) for d in desc]
+    common = lbm.LbmParams(precision=lbm.LBM_F32DEV, fd_substeps=M_SUB, **CFG)
+    b = lbm.Batch(common, insts, stream=stream.cuda_stream)
+    xi = (2 * CFG["kappa"] / -CFG["a"]) ** 0.5
+    for k, d in enumerate(desc):
+        phi = I.drop(2, d["side"], d["side"], R=d["R"], phi0=1.0, xi=xi)
+        n, u = I.rest(2, d["side"], d["side"])
+        b.init_fields(k, n, phi, u)
+    sites = b.shape()["sites"]
+    b.step(steps)  # warm-up, captures the graph
+    b.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+            b.step(steps)
+            t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    value = sites * steps / (ms / 1000.0) / 1e6
+    shape = b.shape()
+    b.close()
+    # the plain kernels on one lattice with the same number of sites
+    side = int(round(sites ** 0.5 / 16.0)) * 16
+    lat = lbm.Lattice(lbm.LbmParams(Lx=side, Ly=side, fd_substeps=M_SUB, precision=lbm.LBM_F32DEV, **CFG),
+                      stream=stream.cuda_stream)
+    n, u = I.rest(2, side, side)
+    lat.init_fields(n, I.spinodal(2, side, side, seed=rank), u)
+    del n, u
+    with torch.cuda.stream(stream):
+        lat.step(steps)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        lat.step(steps)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    plain = side * side * steps / (t0.elapsed_time(t1) / 1000.0) / 1e6
+    lat.close()
+    peak, kind = measured_peak()
+    return {"value": value, "unit": "MLUPS", "instances": 512, "sites": sites, "lb_steps_timed": steps,
+            "ms": ms, "shape": shape, "launches_per_lb_step": 1,
+            "step_roofline": {"bound": "hbm", "achieved": value * STEP_BYTES_PER_SITE / 1e3, "peak": peak,
+                              "unit": "GB/s", "frac": value * STEP_BYTES_PER_SITE / 1e3 / peak,
+                              "bytes_per_site": STEP_BYTES_PER_SITE, "peak_kind": kind},
+            "plain_equal_sites": {"lattice": [side, side], "value": plain, "unit": "MLUPS"},
+            "vs_plain_equal_sites": value / plain, "clocks": clocks.summary()}
+
+
 def run_batched(args, rank, world, local):
     """512 independent drops (sides 32..256, half pushed by g_x = 1e-5 for the
     first 2000 of 6000 steps) in one persistent launch per call, against 512
@@ -567,26 +707,25 @@ D3_COLLIDE_BYTES = {"f32": 2 * 19 * 4 + 4, "f16": 2 * 19 * 2 + 4}
 # minimum; the three-pass kernels also write and re-read phih and psi)
 D3_FD_BYTES = 4 + 4 + 12
 D3_M = 8
+# whole-step algorithmic bytes per site: populations read and written, phi
+# read and written (FP32: 19 x 4 x 2 + 8; FP16 deviations: 19 x 2 x 2 + 8)
+D3_STEP_BYTES = {"f32": 160, "f16": 84}
 
 
-def run_drop3d(args, rank, world, local):
-    """D3Q19 drop on a 256^3 periodic lattice (R = 48, centred), FP32 and FP16
-    deviations, m = 8 FD substeps; one timed step = lbm_step(10)."""
+def drop3d_form(side, steps, warmup, local, stream):
+    """D3Q19 drop on a side^3 periodic lattice (R = 48 side/256, centred), FP32
+    and FP16 deviations, m = 8 FD substeps; one timed step = lbm_step(10).
+    Returns {"f32": ..., "f16": ...} with MLUPS, rooflines and clocks."""
     import torch
-    from paper_0902_3921_gb300 import build as B
     from paper_0902_3921_gb300 import inputs as I
     from paper_0902_3921_gb300 import lbm
 
-    torch.cuda.set_device(local)
-    B.build()
-    lbm.load_library()
-    S3 = args.side3d
+    S3 = side
     S = S3 ** 3
     xi = (2 * D3_CFG["kappa"] / -D3_CFG["a"]) ** 0.5
     phi0 = (-D3_CFG["a"] / D3_CFG["b"]) ** 0.5
     phi = I.drop(3, S3, S3, S3, R=48 * S3 / 256, phi0=phi0, xi=xi)
     n, u = I.rest(3, S3, S3, S3)
-    stream = torch.cuda.Stream()
     out = {}
     peak, peak_kind = measured_peak()
     for name, prec in (("f32", lbm.LBM_F32DEV), ("f16", lbm.LBM_F16DEV)):
@@ -594,7 +733,7 @@ def run_drop3d(args, rank, world, local):
                           stream=stream.cuda_stream)
         lat.init_fields(n, phi, u)
         with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 lat.step(D3_LB_PER_STEP)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -602,11 +741,11 @@ def run_drop3d(args, rank, world, local):
         with ClockSampler(local) as clocks:
             with torch.cuda.stream(stream):
                 t0.record(stream)
-                for _ in range(args.steps):
+                for _ in range(steps):
                     lat.step(D3_LB_PER_STEP)
                 t1.record(stream)
             torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1) / args.steps
+        ms = t0.elapsed_time(t1) / steps
         value = S * D3_LB_PER_STEP / (ms / 1000.0) / 1e6
         lbm.lbm_set_kernel_timing(lat.handle, True)
         lbm.lbm_kernel_times(lat.handle, reset=True)
@@ -634,9 +773,34 @@ def run_drop3d(args, rank, world, local):
                   "note": f"avg_launch_us covers all FD launches of one LB step ({fn} launches)",
                   "peak_kind": peak_kind, "share_of_step": fms / (cms + fms)}
         dom, oth = (roof_c, roof_f) if cms >= fms else (roof_f, roof_c)
-        out[name] = {"value": value, "ms_per_step": ms, "roofline": dom, "roofline_other_kernel": oth,
+        step_bytes = D3_STEP_BYTES[name]
+        out[name] = {"lattice": [S3, S3, S3], "value": value, "unit": "MLUPS", "ms_per_step": ms,
+                     "lb_steps_per_timed_step": D3_LB_PER_STEP, "timed_steps": steps,
+                     "step_roofline": {"bound": "hbm", "achieved": value * step_bytes / 1e3, "peak": peak,
+                                       "unit": "GB/s", "frac": value * step_bytes / 1e3 / peak,
+                                       "bytes_per_site": step_bytes, "peak_kind": peak_kind},
+                     "roofline": dom, "roofline_other_kernel": oth,
                      "clocks": clocks.summary(), "launches_per_step": (cn + fn)}
         lat.close()
+    return out
+
+
+def run_drop3d(args, rank, world, local):
+    """D3Q19 drop on a 256^3 periodic lattice (R = 48, centred), FP32 and FP16
+    deviations, m = 8 FD substeps; one timed step = lbm_step(10)."""
+    import torch
+    from paper_0902_3921_gb300 import build as B
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    B.build()
+    lbm.load_library()
+    S3 = args.side3d
+    stream = torch.cuda.Stream()
+    out = drop3d_form(S3, args.steps, args.warmup, local, stream)
+    xi = (2 * D3_CFG["kappa"] / -D3_CFG["a"]) ** 0.5
+    phi0 = (-D3_CFG["a"] / D3_CFG["b"]) ** 0.5
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         import oracle as O
@@ -695,37 +859,31 @@ def cpu_surrogate_forward(side=64, reps=1):
     return side * side * reps / dt, dt
 
 
-def run_surrogate(args, rank, world, local):
+def surrogate_forward(steps, warmup, local, rank, stream):
     """The learned surrogate's step, x_{t+50} = x_t + Net(x_t), on the 2048^2
     inference lattice: six periodic 3x3 convolutions (4 -> 32 -> ... -> 32 ->
     4), BF16 weights and activations, FP32 accumulation on the tcgen05 tensor
     cores.  Weights are random (throughput does not depend on their values).
     value = lattice updates per second the forward pass stands in for
-    (2048^2 sites x 50 LB steps per pass); the plain scheme is timed on the
-    same lattice beside it."""
+    (2048^2 sites x 50 LB steps per pass).  Returns (result dict, net, x0,
+    x1); the caller closes the net."""
     import torch
-    from paper_0902_3921_gb300 import build as B
-    from paper_0902_3921_gb300 import inputs as I
     from paper_0902_3921_gb300 import lbm
 
-    torch.cuda.set_device(local)
-    B.build()
-    lbm.load_library()
     S = SURR_SIDE
     P = S * S
-    stream = torch.cuda.Stream()
     net = lbm.Net(32, 6, seed=1)
     net.set_normalisation([0.0, 0.0, 0.0, 0.0], [0.6, 2e-3, 2e-3, 3e-3], [0.05, 1e-3, 1e-3, 1e-3])
     g = torch.Generator(device="cuda").manual_seed(rank)
     x0 = (0.5 * torch.randn(P * 4, device="cuda", generator=g)).contiguous()
     x1 = torch.empty_like(x0)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             net.forward(x0.data_ptr(), 1, S, S, x1.data_ptr(), stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    steps = max(args.steps, 400)  # about 0.3 s, long enough for the clock samples
+    steps = max(steps, 400)  # about 0.3 s, long enough for the clock samples
     with ClockSampler(local) as clocks:
         with torch.cuda.stream(stream):
             t0.record(stream)
@@ -735,7 +893,7 @@ def run_surrogate(args, rank, world, local):
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     value = P * SURR_WINDOW / (ms / 1000.0) / 1e6
-    layer_ms = net.layer_times(x0.data_ptr(), 1, S, S, reps=max(3, args.steps // 2),
+    layer_ms = net.layer_times(x0.data_ptr(), 1, S, S, reps=max(3, steps // 20),
                                stream=stream.cuda_stream)
     dom = max(range(1, 5), key=lambda l: layer_ms[l])  # a 32 -> 32 layer
     conv_s = layer_ms[dom] / 1000.0
@@ -748,6 +906,39 @@ def run_surrogate(args, rank, world, local):
             bf16_peak = json.load(f).get("bf16_tflops")
     except OSError:
         pass
+    res = {"value": value, "unit": "MLUPS-equivalent", "ms_per_forward": ms, "forwards_timed": steps,
+           "lattice": [S, S], "window_lb_steps": SURR_WINDOW,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved / hbm_peak,
+                        "traffic": NCU_TRAFFIC_CONV_2048 if S == 2048 else None,
+                        "kernel": f"conv_tc layer {dom} (32 -> 32, tcgen05)",
+                        "bytes_per_px": CONV_BYTES_PER_PX, "avg_launch_us": layer_ms[dom] * 1000.0,
+                        "peak_kind": hbm_kind,
+                        "tensor": {"achieved": tensor_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                   "frac": (tensor_tflops / bf16_peak) if bf16_peak else None}},
+           "layer_us": [v * 1000.0 for v in layer_ms], "clocks": clocks.summary()}
+    return res, net, x0, x1
+
+
+def run_surrogate(args, rank, world, local):
+    """The surrogate workload: the forward pass (surrogate_forward), end to end
+    from pinned host memory, the plain scheme timed on the same lattice beside
+    it, and the trained network's speedup at fixed error."""
+    import torch
+    from paper_0902_3921_gb300 import build as B
+    from paper_0902_3921_gb300 import inputs as I
+    from paper_0902_3921_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    B.build()
+    lbm.load_library()
+    S = SURR_SIDE
+    P = S * S
+    stream = torch.cuda.Stream()
+    fwd, net, x0, x1 = surrogate_forward(args.steps, args.warmup, local, rank, stream)
+    value, ms, steps, layer_ms = fwd["value"], fwd["ms_per_forward"], fwd["forwards_timed"], fwd["layer_us"]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
     # e2e: pinned host state in, prediction out, every step
     hx0 = torch.empty(P * 4, dtype=torch.float32, pin_memory=True)
     hx0.copy_(x0.cpu())
@@ -796,15 +987,8 @@ def run_surrogate(args, rank, world, local):
             "config": {"workload": "surrogate-2048x2048-6x3x3conv-32ch", "pixels": P,
                        "window_lb_steps": SURR_WINDOW, "layers": 6, "channels": 32,
                        "l2": "activations (256 MiB per 32-channel layer) exceed L2"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak,
-                         "traffic": NCU_TRAFFIC_CONV_2048 if S == 2048 else None,
-                         "kernel": f"conv_tc layer {dom} (32 -> 32, tcgen05)",
-                         "bytes_per_px": CONV_BYTES_PER_PX, "avg_launch_us": layer_ms[dom] * 1000.0,
-                         "peak_kind": hbm_kind,
-                         "tensor": {"achieved": tensor_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                                    "frac": (tensor_tflops / bf16_peak) if bf16_peak else None}},
-            "layer_us": [v * 1000.0 for v in layer_ms],
+            "roofline": fwd["roofline"],
+            "layer_us": layer_ms,
             "plain_scheme": {"value": plain, "unit": "MLUPS", "lattice": [S, S]},
             "speedup_vs_plain_per_window": value / plain,
             "fixed_error": fixed,
@@ -812,7 +996,7 @@ def run_surrogate(args, rank, world, local):
             "e2e": {"value": P * SURR_WINDOW / (ms_e2e / 1000.0) / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": P * 16, "d2h_bytes_per_step": P * 16},
             "gpu_launches": 8 * steps,
-            "clocks": clocks.summary()}), flush=True)
+            "clocks": fwd["clocks"]}), flush=True)
 
 
 SURR_WEIGHTS = os.path.join(ROOT, "paper_0902_3921_gb300", "weights", "surrogate_32ch6_spinodal.npz")
@@ -857,6 +1041,8 @@ def main():
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (the workload is 1024; other sides are for profiling)")
     ap.add_argument("--no-large", action="store_true", help="skip the 4096^2 (--large-side) line")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched, 3D and surrogate sub-results of the default line")
     ap.add_argument("--large-side", type=int, default=4096)
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no kernel timing, e2e or CPU baseline)")
