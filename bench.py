@@ -447,6 +447,9 @@ def other_forms(local, rank, stream):
     return out
 
 
+# algorithmic bytes of one FD launch per site: phi read and written, u* read
+FD_BYTES_PER_SITE_LAUNCH = 16
+
 # bytes per site and LB step the method must carry between steps (FP32
 # deviations): populations read and written (9 x 4 x 2) and phi (4 x 2)
 STEP_BYTES_PER_SITE = 80
@@ -550,7 +553,14 @@ def large_lattice(side, stream):
                         "traffic": (NCU_TRAFFIC_COLLIDE_2048[1] * S / 2048 ** 2
                                     if tuning["collide_sites_per_thread"] == NCU_TRAFFIC_COLLIDE_2048[0] else None),
                         "traffic_note": "ncu capture on 2048^2 scaled by the site count"},
-            "fd_avg_launch_us": fms / fn * 1000.0, "fd_launches_per_lb_step": fn / 100.0}
+            "fd_avg_launch_us": fms / fn * 1000.0, "fd_launches_per_lb_step": fn / 100.0,
+            # each FD launch reads phi and u* and writes phi: 16 B/site
+            "fd": {"bound": "hbm", "achieved": FD_BYTES_PER_SITE_LAUNCH * S / (fms / fn / 1000.0) / 1e9,
+                   "peak": peak, "unit": "GB/s",
+                   "frac": FD_BYTES_PER_SITE_LAUNCH * S / (fms / fn / 1000.0) / 1e9 / peak,
+                   "avg_launch_us": fms / fn * 1000.0, "bytes_per_site": FD_BYTES_PER_SITE_LAUNCH,
+                   "kernel": f"fd2d (tile {tuning['fd_tile_width']}: 1 = y-marching wavefront)",
+                   "peak_kind": peak_kind}}
 
 
 def batched_form(steps, local, rank, stream):
