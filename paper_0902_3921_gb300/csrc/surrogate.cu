@@ -198,6 +198,136 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], unsigned addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned &r0, unsigned &r1, unsigned addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
+}
+
+// The same partial weight and bias gradients on the tensor cores.  Per pixel
+// tile (TILE_H rows of TILE_W = 16 pixels) and per tile row r, the 16 pixels
+// are one K step of
+//   C[co][(tap, ci)] += sum_k dz[k, co] x[k + tap, ci]
+// by mma.sync m16n8k16 (BF16 operands, FP32 accumulation): A = dz^T (16
+// output channels x 16 pixels), B = the input shifted by the tap (16 pixels x
+// 8 input channels).  Both are staged in shared memory as 16-byte rows of 8
+// channels of one pixel ([chunk][row][x], as in global memory) and read with
+// ldmatrix.trans, which turns the pixel-major rows into the row-major A and
+// column-major B fragments.  Warp w owns the N tiles w, w + 8, ... of the
+// 9 CINP / 8 (tap, 8 channels) tiles; warp 0 also multiplies A by a tile of
+// ones, whose columns are the bias gradient sum_k dz[k, co].  COUTP = 8 fills
+// the upper half of the 16-row A tile with a copy and drops those rows.
+template <int CINP, int COUTP, int DZS>
+__global__ void __launch_bounds__(256)
+    conv_wgrad_mma_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int N, int H, int W,
+                          float *__restrict__ partial) {
+  constexpr int RH = TILE_H + 2, RW = TILE_W + 2;
+  constexpr int CJ = CINP / 8, DJ = COUTP / 8;
+  constexpr int MT = (COUTP + 15) / 16;  // 16-row tiles of output channels
+  constexpr int NT = 9 * CJ;             // 8-column tiles of (tap, input channel)
+  constexpr int NTW = (NT + 7) / 8;      // N tiles per warp
+  static_assert(TILE_W == 16, "one K step of 16 pixels per tile row");
+  __shared__ __align__(16) uint4 sx[CJ * RH * RW];
+  __shared__ __align__(16) uint4 sd[DJ * TILE_H * TILE_W];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float acc[MT][NTW][4], accb[MT][4];
+#pragma unroll
+  for (int mi = 0; mi < MT; ++mi) {
+#pragma unroll
+    for (int t = 0; t < NTW; ++t) acc[mi][t][0] = acc[mi][t][1] = acc[mi][t][2] = acc[mi][t][3] = 0.f;
+    accb[mi][0] = accb[mi][1] = accb[mi][2] = accb[mi][3] = 0.f;
+  }
+  const unsigned ONES = 0x3F803F80u;  // two BF16 ones
+  const unsigned sx_base = static_cast<unsigned>(__cvta_generic_to_shared(sx));
+  const unsigned sd_base = static_cast<unsigned>(__cvta_generic_to_shared(sd));
+  const int tiles_x = W / TILE_W, tiles_y = H / TILE_H;
+  const long long ntiles = (long long)tiles_x * tiles_y * N;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int n = (int)(tile / ((long long)tiles_x * tiles_y));
+    const int rem = (int)(tile - (long long)n * tiles_x * tiles_y);
+    const int y0 = (rem / tiles_x) * TILE_H, x0 = (rem % tiles_x) * TILE_W;
+    const long long img = (long long)n * H * W;
+    __syncthreads();
+    for (int k = tid; k < CJ * RH * RW; k += 256) {
+      const int j = k / (RH * RW), q = k - j * (RH * RW);
+      const int r = q / RW, cc = q - r * RW;
+      int gy = y0 + r - 1, gx = x0 + cc - 1;
+      gy = gy < 0 ? gy + H : (gy >= H ? gy - H : gy);
+      gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
+      sx[k] = *reinterpret_cast<const uint4 *>(x + conv_act_index(img / W + gy, j, gx, W, CJ));
+    }
+    for (int k = tid; k < DJ * TILE_H * TILE_W; k += 256) {
+      const int j = k / (TILE_H * TILE_W), q = k - j * (TILE_H * TILE_W);
+      const int r = q / TILE_W, cc = q - r * TILE_W;
+      sd[k] = *reinterpret_cast<const uint4 *>(dz + conv_act_index(img / W + y0 + r, j, x0 + cc, W, DZS / 8));
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < TILE_H; ++r) {
+      unsigned a[MT][4];
+#pragma unroll
+      for (int mi = 0; mi < MT; ++mi) {
+        // lanes 8b .. 8b + 7 address the rows of 8 x 8 block b: blocks 0 / 1
+        // are output channels 0-7 / 8-15 of pixels 0-7, blocks 2 / 3 of 8-15
+        const int blk = lane >> 3;
+        const int chunk = min(2 * mi + (blk & 1), DJ - 1);
+        const int kk = (blk >> 1) * 8 + (lane & 7);
+        ldsm_x4_t(a[mi], sd_base + 16u * (unsigned)((chunk * TILE_H + r) * TILE_W + kk));
+      }
+#pragma unroll
+      for (int t = 0; t < NTW; ++t) {
+        const int nt = warp + 8 * t;
+        if (nt < NT) {
+          const int tap = nt / CJ, j = nt - tap * CJ;
+          // lanes 0-7: pixels 0-7 (block 0), lanes 8-15: pixels 8-15 (block 1)
+          const int kk = lane & 15;
+          unsigned b0, b1;
+          ldsm_x2_t(b0, b1, sx_base + 16u * (unsigned)((j * RH + r + tap / 3) * RW + kk + tap % 3));
+#pragma unroll
+          for (int mi = 0; mi < MT; ++mi) mma_bf16(acc[mi][t], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b0, b1);
+        }
+      }
+      if (warp == 0) {
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi) mma_bf16(accb[mi], a[mi][0], a[mi][1], a[mi][2], a[mi][3], ONES, ONES);
+      }
+    }
+  }
+  // C fragment: rows g and g + 8, columns 2q and 2q + 1
+  float *out = partial + (size_t)blockIdx.x * (COUTP * 9 * CINP + COUTP);
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int mi = 0; mi < MT; ++mi) {
+#pragma unroll
+    for (int t = 0; t < NTW; ++t) {
+      const int nt = warp + 8 * t;
+      if (nt >= NT) continue;
+      const int tap = nt / CJ, j = nt - tap * CJ;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int co = 16 * mi + g + 8 * h;
+        if (co < COUTP) {
+          float *o = out + (co * 9 + tap) * CINP + 8 * j + 2 * q;
+          o[0] = acc[mi][t][2 * h];
+          o[1] = acc[mi][t][2 * h + 1];
+        }
+      }
+    }
+    if (warp == 0 && q == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int co = 16 * mi + g + 8 * h;
+        if (co < COUTP) out[COUTP * 9 * CINP + co] = accb[mi][2 * h];
+      }
+    }
+  }
+}
+
 // Sums the per-CTA partials in a fixed order into the padded weight (KS
 // stride) and bias gradients.
 __global__ void wgrad_reduce_kernel(const float *__restrict__ partial, int nparts, int cinp,
@@ -532,11 +662,21 @@ cudaError_t conv_any(int cinp, int coutp, int epi, const bf16 *in, const bf16 *w
   return cudaErrorInvalidValue;
 }
 
+// HLBM_WGRAD_PATH=simt asks for the FP32 SIMT weight-gradient kernel (the
+// tensor-core one is the default)
+bool wgrad_simt() {
+  const char *e = std::getenv("HLBM_WGRAD_PATH");  // read at each call (tests compare both paths)
+  return e != nullptr && std::strcmp(e, "simt") == 0;
+}
+
 cudaError_t wgrad_any(int cinp, int coutp, int dzs, const bf16 *x, const bf16 *dz, int N, int H,
                       int W, float *partial, int ctas, cudaStream_t s) {
 #define CASE(CI, CO, DS)                                                               \
   if (cinp == CI && coutp == CO && dzs == DS) {                                        \
-    conv_wgrad_kernel<CI, CO, DS><<<ctas, 256, 0, s>>>(x, dz, N, H, W, partial);       \
+    if (wgrad_simt())                                                                  \
+      conv_wgrad_kernel<CI, CO, DS><<<ctas, 256, 0, s>>>(x, dz, N, H, W, partial);     \
+    else                                                                               \
+      conv_wgrad_mma_kernel<CI, CO, DS><<<ctas, 256, 0, s>>>(x, dz, N, H, W, partial); \
     return cudaGetLastError();                                                         \
   }
   CASE(16, 32, 32) CASE(32, 32, 32) CASE(32, 8, 16) CASE(16, 16, 16) CASE(16, 8, 16)

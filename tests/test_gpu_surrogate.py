@@ -199,6 +199,28 @@ def test_gradients_and_loss_match_reference():
     net.close()
 
 
+@pytest.mark.parametrize("C,L,shape", [(32, 6, (2, 16, 32)), (16, 3, (1, 24, 48)), (32, 3, (1, 8, 128))])
+def test_tensor_core_weight_gradients_match_simt(C, L, shape, monkeypatch):
+    """The weight and bias gradients of every layer shape (16 -> 32, 32 -> 32,
+    32 -> 8, 16 -> 16, 16 -> 8) from the mma.sync kernel against the FP32
+    SIMT kernel on the same BF16 activations: the same products summed in
+    another order (FP32 accumulation in both), so they agree to 1e-4."""
+    net, _ = _random_net(C, L, seed=21)
+    net.set_normalisation(*NORM)
+    x0, x1 = _inputs(*shape, 22)
+    d0 = torch.from_numpy(x0.astype(np.float32)).cuda()
+    d1 = torch.from_numpy(x1.astype(np.float32)).cuda()
+    grads = {}
+    for path in ("simt", "mma"):
+        monkeypatch.setenv("HLBM_WGRAD_PATH", path)
+        net.train_step(d0.data_ptr(), d1.data_ptr(), *shape, lr=0.0, update=False)
+        grads[path] = _flat_to_params(net.get_grads().astype(np.float64), C, L)
+    for li, ((gw, gb), (sw, sb)) in enumerate(zip(grads["mma"], grads["simt"])):
+        assert np.linalg.norm(gw - sw) <= 1e-4 * np.linalg.norm(sw), li
+        assert np.linalg.norm(gb - sb) <= 1e-4 * max(np.linalg.norm(sb), 1e-30), li
+    net.close()
+
+
 def test_adam_step_matches_reference():
     C, L = 16, 3
     net, _ = _random_net(C, L, seed=7)
