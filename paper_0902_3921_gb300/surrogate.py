@@ -30,7 +30,7 @@ def _params(side):
 
 def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=2000, lr=1e-3,
           channels=32, layers=6, seed0=0, log=None, reservoir=0, batch=0, updates=1, lr_final=None,
-          pushforward=0.0, pushforward_from=1):
+          pushforward=0.0, pushforward_from=1, init=None, t_start_hi=None):
     """Trains a network on pairs (x_t, x_{t+window}) that the plain scheme
     produces.  reservoir = 0: every window's pairs of the current lattices are
     one training batch.  reservoir > 0: the pairs stream into a device
@@ -41,10 +41,19 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
     pushforward > 0 (reservoir only, from generation pushforward_from on):
     that fraction of the windows also adds the pair (Net(x_{t-window}),
     x_{t+window}), whose input is the network's own prediction of x_t, so the
-    network learns to correct the errors it makes when applied repeatedly."""
+    network learns to correct the errors it makes when applied repeatedly.
+    init: an .npz written by --save to start from (its normalisation is kept).
+    t_start_hi: each generation starts at a time drawn uniformly from
+    [t_start, t_start_hi] (a multiple of the window), so later stages of the
+    coarsening enter the data."""
     import torch
     stream = torch.cuda.Stream()
     net = lbm.Net(channels, layers, seed=seed0 + 12345)
+    if init is not None:
+        z = np.load(init)
+        net.set_params(z["params"])
+        nrm = z["normalisation"]
+        net.set_normalisation(nrm[0], nrm[1], nrm[2])
     x0 = torch.empty((lattices, side, side, 4), dtype=torch.float32, device="cuda")
     x1 = torch.empty_like(x0)
     if reservoir:
@@ -68,19 +77,22 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
         return lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * step / max(total - 1, 1)))
 
     for gen in range(generations):
+        ts = t_start
+        if t_start_hi is not None:
+            ts = int(rng.integers(t_start // window, t_start_hi // window + 1)) * window
         lats = []
         for k in range(lattices):
             lat = lbm.Lattice(_params(side), stream=stream.cuda_stream)
             n, u = I.rest(2, side, side)
             lat.init_fields(n, I.spinodal(2, side, side, seed=seed0 + gen * lattices + k), u)
-            lat.step(t_start)
+            lat.step(ts)
             lats.append(lat)
         for it in range(iters):
             for k, lat in enumerate(lats):
                 lbm.lbm_surrogate_state(lat.handle, x0[k].data_ptr())
                 lat.step(window)
                 lbm.lbm_surrogate_state(lat.handle, x1[k].data_ptr())
-            if gen == 0 and it == 0:
+            if gen == 0 and it == 0 and init is None:
                 stream.synchronize()
                 a = x0.cpu().numpy().reshape(-1, 4)
                 d = (x1 - x0).cpu().numpy().reshape(-1, 4)
@@ -127,7 +139,14 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
 
 
 def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 16000),
-             window=50, mass_tol=2e-3, phi_clamp=0.0, relax=0, log=None):
+             window=50, mass_tol=2e-3, phi_clamp=0.0, relax=0, log=None, late_net=None, late_from=None,
+             control=False):
+    """late_net (optional) replaces net for the windows from t = late_from on.
+    control: a third lattice, the plain scheme re-initialised from its own n,
+    phi, u* at t_start (populations rebuilt at equilibrium, the reconstruction
+    every accepted surrogate window makes) and then advanced by the plain
+    scheme: how far two plain trajectories one such perturbation apart drift,
+    the floor under which no surrogate error can be judged."""
     import torch
     stream = torch.cuda.Stream()
     n, u = I.rest(2, side, side)
@@ -136,6 +155,11 @@ def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 1
     surr = lbm.Lattice(_params(side), stream=stream.cuda_stream).init_fields(n, phi0, u)
     plain.step(t_start)
     surr.step(t_start)
+    ctrl = None
+    if control:
+        cn, cphi, cu = plain.moments()
+        ctrl = lbm.Lattice(_params(side), stream=stream.cuda_stream).init_fields(cn, cphi, cu)
+        del cn, cphi, cu
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     rows, t = [], t_start
     tp_total = ts_total = 0.0
@@ -147,10 +171,13 @@ def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 1
             plain.step(dt)
             ev[1].record(stream)
         stream.synchronize()
+        if ctrl is not None:
+            ctrl.step(dt)
+        use = late_net if (late_net is not None and late_from is not None and t >= late_from) else net
         with torch.cuda.stream(stream):
             ev[2].record(stream)
             nwin = dt // (window + relax)
-            fb = lbm.lbm_surrogate_advance(surr.handle, net, nwin, window, mass_tol, True,
+            fb = lbm.lbm_surrogate_advance(surr.handle, use, nwin, window, mass_tol, True,
                                            phi_clamp, relax_steps=relax)
             if dt - nwin * (window + relax):
                 surr.step(dt - nwin * (window + relax))
@@ -169,14 +196,31 @@ def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 1
                "sum_phi_plain": float(pp.sum()), "sum_phi_surrogate": float(ps.sum()),
                "sum_phi_start": float(phi0.sum()), "fallbacks": fb, "windows": dt // (window + relax),
                "ms_plain": tp, "ms_surrogate": ts}
+        if ctrl is not None:
+            _, pc, _ = ctrl.moments()
+            _, Sc = OB.structure_factor(pc)
+            row["L_control"] = OB.domain_size(pc)
+            row["S_rel_l2_control"] = float(np.linalg.norm(Sc - Sp) / np.linalg.norm(Sp))
         rows.append(row)
         if log:
             log(json.dumps(row))
         t = tc
     plain.close()
     surr.close()
+    if ctrl is not None:
+        ctrl.close()
     return {"side": side, "checkpoints": rows, "speedup": tp_total / ts_total,
             "fallbacks": fb_total, "ms_plain": tp_total, "ms_surrogate": ts_total}
+
+
+def load_net(path, channels=32, layers=6):
+    """A network with the parameters and normalisation written by --save."""
+    z = np.load(path)
+    net = lbm.Net(channels, layers, seed=0)
+    net.set_params(z["params"])
+    nrm = z["normalisation"]
+    net.set_normalisation(nrm[0], nrm[1], nrm[2])
+    return net
 
 
 def main():
@@ -201,25 +245,36 @@ def main():
                     help="fraction of windows that add (Net(x_{t-w}), x_{t+w}) pairs")
     ap.add_argument("--pushforward-from", type=int, default=1, help="first generation with them")
     ap.add_argument("--save", default=None, help="write the trained parameters (.npz)")
+    ap.add_argument("--init", default=None, help="start training from these parameters (.npz)")
+    ap.add_argument("--t-start", type=int, default=2000, help="LB step of the first training window")
+    ap.add_argument("--t-start-hi", type=int, default=None,
+                    help="draw each generation's first window uniformly from [t-start, t-start-hi]")
+    ap.add_argument("--seed0", type=int, default=0, help="first training seed")
+    ap.add_argument("--late", default=None, help="parameters (.npz) used from --late-from on")
+    ap.add_argument("--late-from", type=int, default=16000)
+    ap.add_argument("--control", action="store_true",
+                    help="also run the plain scheme re-initialised from its own moments at the start")
     ap.add_argument("--load", default=None, help="evaluate parameters written by --save")
     args = ap.parse_args()
     if args.load:
-        z = np.load(args.load)
-        net = lbm.Net(32, 6, seed=0)
-        net.set_params(z["params"])
-        nrm = z["normalisation"]
-        net.set_normalisation(nrm[0], nrm[1], nrm[2])
+        net = load_net(args.load)
         hist = {"loaded": args.load}
     else:
         net, hist = train(args.side, args.lattices, args.generations, args.iters, window=args.window,
                           lr=args.lr, log=lambda m: print(m, flush=True), reservoir=args.reservoir,
                           batch=args.batch, updates=args.updates, lr_final=args.lr_final,
-                          pushforward=args.pushforward, pushforward_from=args.pushforward_from)
+                          pushforward=args.pushforward, pushforward_from=args.pushforward_from,
+                          init=args.init, t_start=args.t_start, t_start_hi=args.t_start_hi,
+                          seed0=args.seed0)
     if args.save:
         np.savez(args.save, params=net.get_params(), normalisation=np.asarray(net.normalisation()))
+    late = None
+    if args.late:
+        late = load_net(args.late)
     res = evaluate(net, args.eval_side, checkpoints=tuple(int(c) for c in args.checkpoints.split(",")),
                    window=args.window, mass_tol=args.mass_tol, phi_clamp=args.phi_clamp,
-                   relax=args.relax, log=lambda m: print(m, flush=True))
+                   relax=args.relax, log=lambda m: print(m, flush=True), late_net=late,
+                   late_from=args.late_from if late is not None else None, control=args.control)
     print(json.dumps({"training": hist, "evaluation": res, "window": args.window, "relax": args.relax}),
           flush=True)
 

@@ -417,3 +417,24 @@ def test_committed_network_gains_at_fixed_error():
         assert abs(r["L_surrogate"] - r["L_plain"]) <= 0.06 * r["L_plain"], r
         assert r["S_rel_l2"] <= 0.3, r
         assert abs(r["sum_phi_surrogate"] - r["sum_phi_plain"]) <= 0.02 * 2048 * 2048, r
+
+
+def test_evaluation_control_and_staged_networks():
+    """evaluate(control=True): the plain scheme re-initialised from its own n,
+    phi, u* at the start (populations rebuilt at equilibrium, as an accepted
+    window does) follows the plain run (at tau = 1 the post-collision
+    populations are the equilibrium plus the forcing term, so the moments fix
+    the state); with a late network the windows after late_from use it."""
+    from paper_0902_3921_gb300 import surrogate as SG
+    import os
+    wdir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_0902_3921_gb300", "weights")
+    net = SG.load_net(os.path.join(wdir, "surrogate_32ch6_spinodal.npz"))
+    late = SG.load_net(os.path.join(wdir, "surrogate_32ch6_spinodal_late.npz"))
+    res = SG.evaluate(net, side=256, checkpoints=(2500, 3000), late_net=late, late_from=2500, control=True)
+    for r in res["checkpoints"]:
+        assert abs(r["L_control"] - r["L_plain"]) <= 1e-3 * r["L_plain"]
+        assert r["S_rel_l2_control"] <= 1e-3
+        assert r["windows"] == 10 and 0 <= r["fallbacks"] <= 10
+    net.close()
+    late.close()
