@@ -565,10 +565,13 @@ def large_lattice(side, stream):
 
 def batched_form(steps, local, rank, stream):
     """512 independent drops (sides 32..256, half pushed by g_x = 1e-5 for the
-    first 2000 of 6000 steps) advanced by one persistent launch per LB step
-    (captured in a CUDA graph), FP32 deviations, `steps` LB steps timed after
-    as many warm-up steps; compared with the plain kernels on one square
-    lattice of (about) the same number of sites, timed the same way."""
+    first 2000 of 6000 steps) advanced together, FP32 deviations, `steps` LB
+    steps timed after as many warm-up steps, on the path the library chose at
+    creation (the persistent kernel, one launch per LB step, or the tiled path,
+    the collide over the tiles of all instances and m/2 wavefront FD launches
+    over their strips; either captured in a CUDA graph); compared with the
+    plain kernels on one square lattice of (about) the same number of sites,
+    timed the same way."""
     import torch
     from paper_0902_3921_gb300 import inputs as I
     from paper_0902_3921_gb300 import lbm
@@ -617,7 +620,8 @@ def batched_form(steps, local, rank, stream):
     lat.close()
     peak, kind = measured_peak()
     return {"value": value, "unit": "MLUPS", "instances": 512, "sites": sites, "lb_steps_timed": steps,
-            "ms": ms, "shape": shape, "launches_per_lb_step": 1,
+            "ms": ms, "shape": shape, "path": "tiled" if shape["threads"] == 0 else "persistent",
+            "launches_per_lb_step": 2 + M_SUB // 2 if shape["threads"] == 0 else 1,
             "step_roofline": {"bound": "hbm", "achieved": value * STEP_BYTES_PER_SITE / 1e3, "peak": peak,
                               "unit": "GB/s", "frac": value * STEP_BYTES_PER_SITE / 1e3 / peak,
                               "bytes_per_site": STEP_BYTES_PER_SITE, "peak_kind": kind},

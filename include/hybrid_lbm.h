@@ -235,12 +235,24 @@ int lbm_load(lbm_handle *h, const char *path);
  * Many independent periodic 2D (D2Q9) lattices of uneven size, all with the
  * common parameters of `common` (T = 1/3, FP64 or FP32-deviation storage)
  * and each with its own size and body force G = n g while t < force_steps
- * (Sec. III), advanced together by ONE persistent kernel launch per
- * lbm_batch_step call (captured in a CUDA graph).  Each instance is owned by
- * one CTA, so no CTA ever waits for another.  The CTA shape (threads x CTAs
- * per SM) is timed at creation on a zeroed state and the fastest kept
- * (HLBM_BATCH_SHAPE="threads,ctas_per_sm" fixes it; HLBM_TUNE_VERBOSE=1 prints
- * the candidates).  Every instance starts at rest (phi = 0, n = 1, u = 0). */
+ * (Sec. III), advanced together by one of two paths chosen at creation:
+ *   persistent: ONE kernel launch per lbm_batch_step call, each instance
+ *     owned by one CTA, so no CTA ever waits for another; its CTA shape
+ *     (threads x CTAs per SM) is timed on a zeroed state and the fastest kept
+ *     (HLBM_BATCH_SHAPE="threads,ctas_per_sm" fixes it);
+ *   tiled (FP32 deviations, printed advection form, even m, every Lx a
+ *     multiple of 4): per LB step the collide over the 32 x 16 tiles of all
+ *     instances -- a persistent TMA-staged kernel, through one set of tensor
+ *     maps per instance shape, for the instances at least 64 on a side
+ *     (HLBM_BATCH_NO_TMA=1 sends them to the tile kernel too), the tile
+ *     kernel for the rest -- and m / 2 launches of the two-substep wavefront
+ *     FD kernel over their 128-column strips.
+ * Where the tiled path is eligible both are timed and the faster kept
+ * (HLBM_BATCH_PATH=tiled|persistent fixes the choice; HLBM_TUNE_VERBOSE=1
+ * prints the timings).  Either is captured in a CUDA graph per call.  Every
+ * instance starts at rest (phi = 0, n = 1, u = 0).  Instances are stored
+ * grouped by shape; the instance index k of the calls below is the index in
+ * the array given to lbm_batch_create. */
 typedef struct {
   int Lx, Ly;            /* periodic lattice of this instance, each >= 3        */
   double g[2];           /* body force per unit density                         */
@@ -258,12 +270,16 @@ int lbm_batch_create(const lbm_params *common, const lbm_instance *inst, int cou
  * that should not start at rest before the first lbm_batch_step. */
 int lbm_batch_init_fields(lbm_batch *b, int k, const double *n, const double *phi,
                           const double *ux, const double *uy);
-/* Advances every instance by nsteps LB steps (one persistent launch). */
+/* Advances every instance by nsteps LB steps on the chosen path.  On the
+ * tiled path, a TMA copy that never completes ends the collide after its
+ * bounded wait and latches LBM_ETIMEOUT at the next lbm_batch_synchronize or
+ * lbm_batch_moments. */
 int lbm_batch_step(lbm_batch *b, long long nsteps);
 /* n, phi, u* of instance k at the current t into host arrays (NULL skips). */
 int lbm_batch_moments(lbm_batch *b, int k, double *n, double *phi, double *ux, double *uy);
 int lbm_batch_set_graphs(lbm_batch *b, int enable);
-/* Threads per CTA, CTAs and total sites of the batch (any pointer may be NULL). */
+/* Threads per CTA, CTAs and total sites of the batch (any pointer may be
+ * NULL); the tiled path reports 0 threads and its number of collide tiles. */
 int lbm_batch_shape(const lbm_batch *b, int *threads, int *ctas, long long *sites);
 int lbm_batch_synchronize(lbm_batch *b);
 void lbm_batch_free(lbm_batch *b);

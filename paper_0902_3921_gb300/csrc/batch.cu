@@ -10,9 +10,23 @@
 //   collide: F = -phi d_D mu + n g, pull streaming, n, u*, BGK + Guo F_i
 //                                                  (Eqs. 12, 15, 17, 18, 28, 29)
 //   m FD substeps: phih (Eqs. 32-35), psi, new phi (Eq. 36)
-// Per-site arrays of all instances are packed end to end (offset off_k), one
-// plane per population: h[i * ST + off_k + y * Lx + x].  The instance's
-// neighbours stay in L1/L2 while the CTA works on it.
+// Per-site arrays of all instances are packed end to end (offset off_k; the
+// instances grouped by shape), one plane per population:
+// h[i * ST + off_k + y * Lx + x].  The instance's neighbours stay in L1/L2
+// while the CTA works on it.
+//
+// Tiled path (FP32 deviations, printed advection form, even m, Lx % 4 == 0):
+// the step is instead the collide over a table of (instance, 32 x 16 tile)
+// items -- the persistent TMA-staged kernel, through one set of tensor maps
+// per instance shape, for the instances at least 64 on a side, the tile
+// kernel for the rest -- and m / 2 launches of the two-substep wavefront FD
+// kernel over a table of (instance, strip, segment of at most 64 rows) items,
+// per LB step, captured in a CUDA graph: every population and phi value is
+// read and written once per step as on a single lattice.  The launches are
+// plain (no programmatic dependent launch: an early-scheduled grid would hold
+// the SM slots that the previous grid's later CTAs need).  The autotuner
+// times both paths on the zeroed state and keeps the faster
+// (HLBM_BATCH_PATH=tiled or persistent fixes the choice).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -332,6 +346,17 @@ struct lbm_batch {
   cudaGraphExec_t graph = nullptr;
   long long graph_steps = -1, graph_t0 = -1;
   bool use_graphs = true;
+  // tiled path
+  bool tiled = false;
+  TiledInst *d_tinst = nullptr;
+  int4 *d_citems = nullptr, *d_fitems = nullptr, *d_titems = nullptr;
+  int ncitems = 0, nfitems = 0, ntitems = 0;  // collide tiles (tile kernel), FD items, collide tiles (TMA)
+  struct TmaChunk {                           // one launch of the TMA collide
+    int begin = 0, n = 0, shapes = 0;          // its items in d_titems, shape slots used
+    TmaShapeMaps maps[2];                      // per buffer parity
+  };
+  std::vector<TmaChunk> tchunks;
+  float persistent_ms = -1.f;  // the persistent kernel's time per LB step at its tuned shape
 };
 
 namespace {
@@ -388,7 +413,68 @@ BatchArgs<C> batch_args(const lbm_batch *b) {
   return A;
 }
 
+// Kernel constants of the tiled path (FP32, D2Q9, T = 1/3; the body force comes
+// from the instance table).
+KParams<float> tiled_params(const lbm_batch *b) {
+  const lbm_params &P = b->P;
+  KParams<float> p{};
+  p.Lx = p.Ly = p.Lz = 1;
+  p.a = (float)P.a;
+  p.b = (float)P.b;
+  p.kappa = (float)P.kappa;
+  p.tau_inv = (float)(1.0 / P.tau);
+  p.pref = (float)(1.0 - 1.0 / (2.0 * P.tau));
+  p.N = (float)P.N;
+  p.Q = (float)P.Q;
+  p.M = (float)((1.0 - 2.0 * P.N) / 4.0);
+  p.R = (float)((1.0 - P.Q) / 2.0);
+  p.C0 = (float)(-4.0 * (P.Q + (1.0 - P.Q) / 2.0));
+  p.cs2mT = 0.f;
+  p.dt = (float)(1.0 / b->m);
+  p.dtG = (float)(P.Gamma / b->m);
+  p.scale = p.inv_scale = 1.f;
+  p.adv_variant = P.adv_variant;
+  p.cubic_at_half = P.cubic_at_half;
+  p.stencil_fd = 0;
+  return p;
+}
+
+// One LB step per iteration: the collide of every tile (TMA launches, then the
+// tile kernel), then m / 2 two-substep FD launches (phi(t) -> phi[2] ->
+// phi[out] ... ending in phi[out]).
+cudaError_t launch_tiled(lbm_batch *b, long long t0, int nsteps) {
+  const KParams<float> p = tiled_params(b);
+  float *h[2] = {static_cast<float *>(b->h[0]), static_cast<float *>(b->h[1])};
+  float *ph[3] = {static_cast<float *>(b->phi[0]), static_cast<float *>(b->phi[1]),
+                  static_cast<float *>(b->phi[2])};
+  float *u = static_cast<float *>(b->u);
+  const int launches = b->m / 2;
+  for (int s = 0; s < nsteps; ++s) {
+    const long long t = t0 + s;
+    const int in = (int)(t & 1), out = 1 - in;
+    cudaError_t e = cudaSuccess;
+    for (const auto &c : b->tchunks) {
+      if (e != cudaSuccess) break;
+      e = collide2d_tma_batch(c.maps[in], h[in], h[out], ph[in], u, b->ST, b->d_tinst, b->d_titems + c.begin, c.n,
+                              p, t, b->stream, false);
+    }
+    if (e == cudaSuccess && b->ncitems > 0)
+      e = collide2d_batch(h[in], h[out], ph[in], u, b->ST, b->d_tinst, b->d_citems, b->ncitems, p, t,
+                          b->stream);
+    if (e != cudaSuccess) return e;
+    const float *src = ph[in];
+    for (int j = 0; j < launches; ++j) {
+      float *dst = ((launches - 1 - j) % 2 == 0) ? ph[out] : ph[2];
+      e = fd2d_wave_batch(src, u, dst, b->ST, b->d_tinst, b->d_fitems, b->nfitems, p, b->stream, false);
+      if (e != cudaSuccess) return e;
+      src = dst;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_batch(lbm_batch *b, long long t0, int nsteps) {
+  if (b->tiled) return launch_tiled(b, t0, nsteps);
   dim3 block(32, b->threads / 32);
   if (b->P.precision == LBM_F64)
     batch_kernel<double><<<b->ctas, block, 0, b->stream>>>(batch_args<double>(b), t0, nsteps);
@@ -470,7 +556,122 @@ int tune_batch(lbm_batch *b, int steps) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->threads = bt;
+  b->persistent_ms = best / steps;
   return upload_assignment(b, bc);
+}
+
+bool tiled_eligible(const lbm_batch *b) {
+  if (b->P.precision != LBM_F32DEV || b->P.adv_variant != LBM_ADV_PAPER || b->m % 2 != 0) return false;
+  for (const DevInst &d : b->inst)
+    if (d.Lx % 4 != 0) return false;
+  return true;
+}
+
+// The item tables of the tiled path: 32 x 16 collide tiles (TMA chunks of
+// shape slots for the instances at least collide2d_tma_batch_min_side() on a
+// side, a slot per run of equal shapes in storage order of up to 0xffff
+// instances; the tile kernel for the rest, or for every instance without the
+// driver's tensor-map encoder or with HLBM_BATCH_NO_TMA set) and FD strips
+// split into segments of at most 64 rows.
+int build_tiles(lbm_batch *b) {
+  std::vector<TiledInst> ti;
+  std::vector<int4> ci, fi, tmi;
+  const int TX = fd2d_wave_batch_strip_columns();
+  for (const DevInst &d : b->inst)
+    ti.push_back(TiledInst{d.Lx, d.Ly, d.off, (float)d.gx, (float)d.gy, d.force_steps});
+  const bool tma = !std::getenv("HLBM_BATCH_NO_TMA");
+  const int tma_min = collide2d_tma_batch_min_side();
+  std::vector<int> ord(b->count);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int p, int q) { return b->inst[p].off < b->inst[q].off; });
+  struct Shape {
+    int chunk, slot, Lx, Ly, n;
+    long long off0;
+  };
+  std::vector<Shape> shapes;
+  b->tchunks.clear();
+  for (int k : ord) {
+    const DevInst &d = b->inst[k];
+    if (tma && d.Lx >= tma_min && d.Ly >= tma_min) {
+      if (shapes.empty() || shapes.back().Lx != d.Lx || shapes.back().Ly != d.Ly || shapes.back().n == 0xffff ||
+          shapes.back().off0 + (long long)shapes.back().n * d.Lx * d.Ly != d.off) {
+        if (b->tchunks.empty() || b->tchunks.back().shapes == TMA_BATCH_SHAPES) {
+          b->tchunks.emplace_back();
+          b->tchunks.back().begin = (int)tmi.size();
+        }
+        shapes.push_back(Shape{(int)b->tchunks.size() - 1, b->tchunks.back().shapes++, d.Lx, d.Ly, 0, d.off});
+      }
+      Shape &sh = shapes.back();
+      const int j = sh.n++;
+      for (int y0 = 0; y0 < d.Ly; y0 += BATCH_TILE_ROWS)
+        for (int x0 = 0; x0 < d.Lx; x0 += 32) tmi.push_back(make_int4(k, x0, y0, (sh.slot << 16) | j));
+    } else {
+      for (int y0 = 0; y0 < d.Ly; y0 += BATCH_TILE_ROWS)
+        for (int x0 = 0; x0 < d.Lx; x0 += 32) ci.push_back(make_int4(k, x0, y0, 0));
+    }
+  }
+  for (size_t c = 0; c < b->tchunks.size(); ++c)
+    b->tchunks[c].n = (c + 1 < b->tchunks.size() ? b->tchunks[c + 1].begin : (int)tmi.size()) - b->tchunks[c].begin;
+  for (const Shape &sh : shapes) {
+    bool ok = true;
+    for (int par = 0; par < 2 && ok; ++par)
+      ok = collide2d_tma_batch_shape(&b->tchunks[sh.chunk].maps[par], sh.slot, static_cast<float *>(b->h[par]),
+                                     static_cast<float *>(b->phi[par]), b->ST, sh.Lx, sh.Ly, sh.off0, sh.n);
+    if (!ok) {  // no encoder, or a shape it refuses: the tile kernel for every instance
+      for (const int4 &it : tmi) ci.push_back(make_int4(it.x, it.y, it.z, 0));
+      tmi.clear();
+      b->tchunks.clear();
+      break;
+    }
+  }
+  for (int k = 0; k < b->count; ++k) {
+    const DevInst &d = b->inst[k];
+    const int strips = (d.Lx + TX - 1) / TX;
+    const int nseg = std::max(1, (d.Ly + 63) / 64), ny = (d.Ly + nseg - 1) / nseg;
+    for (int sx = 0; sx < strips; ++sx)
+      for (int ys = 0; ys < d.Ly; ys += ny) fi.push_back(make_int4(k, sx, ys, std::min(ny, d.Ly - ys)));
+  }
+  auto upload = [&](auto **dst, const auto &v) -> int {
+    if (v.empty()) return LBM_OK;
+    using T = typename std::decay<decltype(v)>::type::value_type;
+    BCK(b, cudaMalloc(dst, sizeof(T) * v.size()), "cudaMalloc");
+    BCK(b, cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "host-to-device copy");
+    return LBM_OK;
+  };
+  int rc = upload(&b->d_tinst, ti);
+  if (!rc) rc = upload(&b->d_citems, ci);
+  if (!rc) rc = upload(&b->d_titems, tmi);
+  if (!rc) rc = upload(&b->d_fitems, fi);
+  b->ncitems = (int)ci.size();
+  b->ntitems = (int)tmi.size();
+  b->nfitems = (int)fi.size();
+  return rc;
+}
+
+// Times `steps` LB steps of the current path (after one warm-up call), ms per step.
+int time_path(lbm_batch *b, int steps, float *ms_per_step) {
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0), "cudaEventCreate");
+  BCK(b, cudaEventCreate(&e1), "cudaEventCreate");
+  float ms = 0.f;
+  BCK(b, launch_batch(b, 0, steps), "batch step");
+  BCK(b, cudaEventRecord(e0, b->stream), "cudaEventRecord");
+  BCK(b, launch_batch(b, 0, steps), "batch step");
+  BCK(b, cudaEventRecord(e1, b->stream), "cudaEventRecord");
+  BCK(b, cudaEventSynchronize(e1), "cudaEventSynchronize");
+  BCK(b, cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_step = ms / steps;
+  return LBM_OK;
+}
+
+// After a synchronisation: a bounded wait of the TMA collide that gave up
+// (its copies never completed) latches LBM_ETIMEOUT.
+int check_waits(lbm_batch *b) {
+  if (b->ntitems > 0 && collide2d_tma_error(true) > 0)
+    return bfail(b, LBM_ETIMEOUT, "batched collide kernel: a TMA copy did not complete within its wait bound");
+  return LBM_OK;
 }
 
 int zero_state(lbm_batch *b) {
@@ -514,7 +715,6 @@ int lbm_batch_create(const lbm_params *common, const lbm_instance *inst, int cou
   b->P = P;
   b->count = count;
   b->m = m;
-  long long ST = 0;
   for (int k = 0; k < count; k++) {
     const lbm_instance &q = inst[k];
     if (q.Lx < 3 || q.Ly < 3 || (long long)q.Lx * q.Ly > (1LL << 30) || q.force_steps < 0 ||
@@ -525,13 +725,24 @@ int lbm_batch_create(const lbm_params *common, const lbm_instance *inst, int cou
     DevInst d;
     d.Lx = q.Lx;
     d.Ly = q.Ly;
-    d.off = ST;
+    d.off = 0;
     d.gx = q.g[0];
     d.gy = q.g[1];
     d.force_steps = q.force_steps;
     b->inst.push_back(d);
-    ST += (long long)q.Lx * q.Ly;
     b->maxS = std::max(b->maxS, (long long)q.Lx * q.Ly);
+  }
+  // storage order: the instances grouped by shape (Lx, Ly), so that those of
+  // one shape are equally spaced, as the tiled path's per-shape tensor maps need
+  std::vector<int> ord(count);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) {
+    return std::make_pair(b->inst[p].Lx, b->inst[p].Ly) < std::make_pair(b->inst[q].Lx, b->inst[q].Ly);
+  });
+  long long ST = 0;
+  for (int k : ord) {
+    b->inst[k].off = ST;
+    ST += (long long)b->inst[k].Lx * b->inst[k].Ly;
   }
   b->ST = ST;
   auto bail = [&](int code) {
@@ -584,6 +795,28 @@ int lbm_batch_create(const lbm_params *common, const lbm_instance *inst, int cou
     }
   }
   if (!rc) rc = zero_state(b);
+  // the tiled path where eligible, if it is faster (or asked for)
+  const char *path = std::getenv("HLBM_BATCH_PATH");
+  if (!rc && path && std::strcmp(path, "tiled") != 0 && std::strcmp(path, "persistent") != 0)
+    rc = bfail(b, LBM_EINVAL, "HLBM_BATCH_PATH must be 'tiled' or 'persistent'");
+  if (!rc && tiled_eligible(b) && !(path && std::strcmp(path, "persistent") == 0)) {
+    if (b->persistent_ms <= 0.f) rc = time_path(b, 2, &b->persistent_ms);  // a fixed CTA shape
+    if (!rc && (fd2d_wave_configure() != cudaSuccess || collide2d_tma_configure(LBM_F32DEV) != cudaSuccess))
+      rc = bfail(b, LBM_ECUDA, "tiled path: shared-memory attributes");
+    if (!rc) rc = build_tiles(b);
+    if (!rc) {
+      b->tiled = true;
+      float tiled_ms = 0.f;
+      rc = time_path(b, 2, &tiled_ms);
+      if (!rc) rc = check_waits(b);
+      if (std::getenv("HLBM_TUNE_VERBOSE"))
+        std::fprintf(stderr, "hlbm tune batch tiled: %.1f us/step (persistent %.1f)\n", tiled_ms * 1000.f,
+                     b->persistent_ms * 1000.f);
+      const bool forced = path && std::strcmp(path, "tiled") == 0;
+      if (!rc && !forced && b->persistent_ms < tiled_ms) b->tiled = false;
+    }
+    if (!rc) rc = zero_state(b);
+  }
   if (rc) return bail(rc);
   *out = b;
   return LBM_OK;
@@ -669,7 +902,7 @@ int lbm_batch_moments(lbm_batch *b, int k, double *n, double *phi, double *ux, d
                              b->stream),
           "device-to-host copy");
   BCK(b, cudaStreamSynchronize(b->stream), "lbm_batch_moments");
-  return LBM_OK;
+  return check_waits(b);
 }
 
 int lbm_batch_set_graphs(lbm_batch *b, int enable) {
@@ -680,8 +913,8 @@ int lbm_batch_set_graphs(lbm_batch *b, int enable) {
 
 int lbm_batch_shape(const lbm_batch *b, int *threads, int *ctas, long long *sites) {
   if (!b) return LBM_EINVAL;
-  if (threads) *threads = b->threads;
-  if (ctas) *ctas = b->ctas;
+  if (threads) *threads = b->tiled ? 0 : b->threads;
+  if (ctas) *ctas = b->tiled ? b->ncitems + b->ntitems : b->ctas;
   if (sites) *sites = b->ST;
   return LBM_OK;
 }
@@ -690,6 +923,7 @@ int lbm_batch_synchronize(lbm_batch *b) {
   if (!b) return LBM_EINVAL;
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) bfail(b, LBM_ECUDA, std::string("lbm_batch_synchronize: ") + cudaGetErrorString(e));
+  if (!b->err) check_waits(b);
   return b->err;
 }
 
@@ -698,7 +932,8 @@ void lbm_batch_free(lbm_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   void *ptrs[] = {b->h[0], b->h[1], b->phi[0], b->phi[1], b->phi[2], b->u, b->mu,
-                  b->fa,   b->fq,   b->staging, b->d_inst, b->d_order, b->d_first};
+                  b->fa,   b->fq,   b->staging, b->d_inst, b->d_order, b->d_first,
+                  b->d_tinst, b->d_citems, b->d_fitems, b->d_titems};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

@@ -481,6 +481,258 @@ constexpr size_t pipe_smem() {
   return 128 + P_OFF_PN + (TGEN ? 4 * MUW * PMUH : 0);
 }
 
+// The cells of an edge tile that its copies leave as zeros (the copies do not
+// wrap around the periodic lattice): phi outside the lattice in the 36 x 20
+// box, and the populations pulled across the lattice's edges.  Each thread
+// loads its share (at most 3 + 2 cells) into registers before the copies are
+// waited for, so that these loads overlap them; pipe_fix_store writes them
+// into the stage once the copies have landed.  The float offsets in the stage
+// (< 2^16) are packed two to a word, 0xffff for none.
+struct PipeFix {
+  float v[5];
+  unsigned dst[3];
+  __device__ __forceinline__ void set(int s, int off) {
+    dst[s >> 1] = (s & 1) ? (dst[s >> 1] & 0xffffu) | ((unsigned)off << 16)
+                          : (dst[s >> 1] & 0xffff0000u) | (unsigned)off;
+  }
+  __device__ __forceinline__ unsigned get(int s) const { return (s & 1) ? dst[s >> 1] >> 16 : dst[s >> 1] & 0xffffu; }
+};
+static_assert(PPOP_FLOATS + PHW * PPHH < 0xffff, "stage offsets fit 16 bits");
+__device__ __forceinline__ void pipe_fix_load(PipeFix &f, const float *__restrict__ hin,
+                                              const float *__restrict__ phi, const int Lx, const int Ly,
+                                              const long long Sz, const int x0, const int y0) {
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) f.dst[s] = 0xffffffffu;
+  // box column rxr and row ryb are the first beyond the lattice (Lx, Ly >= 64,
+  // so one conditional wrap suffices below)
+  const int rxr = Lx - x0 + 2, ryb = Ly - y0 + 2;
+  const int wl = x0 == 0 ? 2 : 0, wr = max(0, TT + 4 - rxr), ht = y0 == 0 ? 2 : 0, hb = max(0, PPHH - ryb);
+  if (wl + wr + ht + hb == 0) return;
+  // phi outside the lattice: the column strips (all PPHH rows), then the row
+  // strips between them
+  const int ncol = PPHH * (wl + wr), wc = TT + 4 - wl - wr, ntot = ncol + (ht + hb) * wc;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int q = tid + 256 * s;
+    if (q >= ntot) continue;
+    int rx, ry;
+    if (q < ncol) {
+      const int c = q / PPHH;
+      ry = q - c * PPHH;
+      rx = c < wl ? c : rxr + (c - wl);
+    } else {
+      const int q2 = q - ncol, r = q2 / wc;
+      rx = wl + (q2 - r * wc);
+      ry = r < ht ? r : ryb + (r - ht);
+    }
+    f.set(s, PPOP_FLOATS + ry * PHW + rx + 2);
+    f.v[s] = phi[(long long)wrap1(y0 - 2 + ry, Ly) * Lx + wrap1(x0 - 2 + rx, Lx)];
+  }
+  // populations whose pull buf_i(r - e_i) crosses an edge of the lattice
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int q = tid + 256 * s;
+    if (q >= 8 * (PY + TT)) continue;
+    const int i = 1 + q / (PY + TT), j = q % (PY + TT);
+    const int ex = q9_ex(i), ey = q9_ey(i);
+    int xs, ys;
+    if (j < PY) {
+      if (ex == 0) continue;
+      xs = ex > 0 ? 0 : Lx - 1;
+      ys = y0 + j;
+    } else {
+      if (ey == 0) continue;
+      ys = ey > 0 ? 0 : Ly - 1;
+      xs = x0 + j - PY;
+    }
+    if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + PY || ys >= Ly) continue;
+    const int sx = wrap1(xs - ex, Lx), sy = wrap1(ys - ey, Ly);
+    f.set(3 + s, pplane_off(i) + (ys - y0) * plane_w(i) + (xs - x0) + col_off(i));
+    f.v[3 + s] = hin[i * Sz + (long long)sy * Lx + sx];
+  }
+}
+__device__ __forceinline__ void pipe_fix_store(const PipeFix &f, float *pops) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s)
+    if (f.get(s) != 0xffffu) pops[f.get(s)] = f.v[s];
+}
+
+// One 32 x 16 tile of the pipelined kernels once its copies have landed in the
+// stage at `pops`: the periodic images the copies left as zeros (from `fix`),
+// mu on the tile + 1, the force and the packed collision of each thread's two
+// rows (Lx x Ly lattice whose planes are Sz values apart; gx, gy the body
+// force per unit density).
+template <bool TGEN>
+__device__ __forceinline__ void pipe_tile(float *pops, float (*smu)[MUW], float (*spn)[MUW], const PipeFix &fix,
+                                          const float *__restrict__ hin, float *__restrict__ hout,
+                                          const float *__restrict__ phi, float *__restrict__ uout,
+                                          const KParams<float> &p, const int Lx, const int Ly,
+                                          const long long Sz, const int x0, const int y0, const float gx,
+                                          const float gy) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ly0 = 2 * ty, x = x0 + tx;
+  float(*sphi)[PHW] = reinterpret_cast<float(*)[PHW]>(pops + PPOP_FLOATS);
+  const float om = p.tau_inv, keep = 1.f - p.tau_inv;
+  const float A0 = om * float(q9_w(0)), B0 = p.pref * float(q9_w(0));
+  const float A1 = om * float(q9_w(1)), B1 = p.pref * float(q9_w(1));
+  const float A2 = om * float(q9_w(5)), B2 = p.pref * float(q9_w(5));
+  pipe_fix_store(fix, pops);  // the periodic images loaded before the copies were waited for
+  __syncthreads();
+  // mu on the tile + 1: this thread's two rows, then the frame
+  {
+    // site row ly is phi row ly + 2 and mu row ly + 1
+    float w[3][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) w[a + 1][j] = sphi[ly0 + 1 + a][tx + 3 + j];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        w[0][j] = w[1][j];
+        w[1][j] = w[2][j];
+        w[2][j] = sphi[ly0 + 3 + r][tx + 3 + j];
+      }
+      smu[ly0 + 1 + r][tx + 1] = mu_at(p, w);
+    }
+    if (tid < 2 * MUW + 2 * PY) {
+      int my, mx;
+      if (tid < MUW) {
+        my = 0;
+        mx = tid;
+      } else if (tid < 2 * MUW) {
+        my = PMUH - 1;
+        mx = tid - MUW;
+      } else {
+        const int q = tid - 2 * MUW;
+        my = 1 + (q >> 1);
+        mx = (q & 1) ? MUW - 1 : 0;
+      }
+      float v[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2) v[a][b2] = sphi[my + a][mx + b2 + 2];
+      smu[my][mx] = mu_at(p, v);
+    }
+  }
+  __syncthreads();
+  // force (Eqs. 28, 30) of the two rows, then the packed collision
+  float2 Fx, Fy;
+  {
+    float m[4][3];  // mu rows ly0 .. ly0 + 3 (tile + 1 coordinates), columns tx .. tx + 2
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) m[a][j] = smu[ly0 + a][tx + j];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      float gmx = -p.M * m[r][0];
+      gmx += p.M * m[r][2];
+      gmx += -p.N * m[r + 1][0];
+      gmx += p.N * m[r + 1][2];
+      gmx += -p.M * m[r + 2][0];
+      gmx += p.M * m[r + 2][2];
+      float gmy = -p.M * m[r][0];
+      gmy += -p.N * m[r][1];
+      gmy += -p.M * m[r][2];
+      gmy += p.M * m[r + 2][0];
+      gmy += p.N * m[r + 2][1];
+      gmy += p.M * m[r + 2][2];
+      const float ph = sphi[ly0 + r + 2][tx + 4];
+      float fx = -ph * gmx, fy = -ph * gmy;
+      if constexpr (TGEN) {
+        const int mx = tx + 1, my = ly0 + r + 1;
+        float px = -p.M * spn[my - 1][mx - 1];
+        px += p.M * spn[my - 1][mx + 1];
+        px += -p.N * spn[my][mx - 1];
+        px += p.N * spn[my][mx + 1];
+        px += -p.M * spn[my + 1][mx - 1];
+        px += p.M * spn[my + 1][mx + 1];
+        float py = -p.M * spn[my - 1][mx - 1];
+        py += -p.N * spn[my - 1][mx];
+        py += -p.M * spn[my - 1][mx + 1];
+        py += p.M * spn[my + 1][mx - 1];
+        py += p.N * spn[my + 1][mx];
+        py += p.M * spn[my + 1][mx + 1];
+        fx += px;
+        fy += py;
+      }
+      if (r == 0) {
+        Fx.x = fx;
+        Fy.x = fy;
+      } else {
+        Fx.y = fx;
+        Fy.y = fy;
+      }
+    }
+  }
+  const int ya = y0 + ly0;
+  if (x < Lx && ya < Ly) {
+    const bool row_b = ya + 1 < Ly;
+    auto pop = [&](int i, int ly) { return pops[pplane_off(i) + ly * plane_w(i) + tx + col_off(i)]; };
+    float2 h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = make_float2(pop(i, ly0), pop(i, ly0 + 1));
+    float2 dens = h[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) dens = add2(dens, h[i]);
+    const float2 jx = add2(add2(sub2(h[1], h[3]), sub2(h[5], h[7])), sub2(h[8], h[6]));
+    const float2 jy = add2(add2(sub2(h[2], h[4]), sub2(h[5], h[7])), sub2(h[6], h[8]));
+    const float2 n = add2(s2(1.f), dens);
+    Fx = fma2(n, s2(gx), Fx);
+    Fy = fma2(n, s2(gy), Fy);
+    const float2 inv_n = make_float2(1.f / n.x, 1.f / n.y);
+    const float2 ux = mul2(fma2(s2(0.5f), Fx, jx), inv_n);
+    const float2 uy = mul2(fma2(s2(0.5f), Fy, jy), inv_n);
+    const float2 usq = fma2(ux, ux, mul2(uy, uy));
+    const float2 uF = fma2(ux, Fx, mul2(uy, Fy));
+    const float2 base2 = fma2(n, mul2(usq, s2(-1.5f)), dens);
+    const float2 n45 = mul2(n, s2(4.5f)), m3uF = mul2(uF, s2(-3.f));
+    const float2 An3_1 = mul2(n, s2(3.f * A1)), An3_2 = mul2(n, s2(3.f * A2));
+    float2 o[9];
+    o[0] = fma2(s2(keep), h[0], fma2(s2(A0), base2, mul2(s2(-3.f * B0), uF)));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = q < 2 ? q + 1 : q + 3, ib = i + 2;
+      const float A = q < 2 ? A1 : A2, B = q < 2 ? B1 : B2;
+      const float2 An3 = q < 2 ? An3_1 : An3_2;
+      float2 eu, eF;
+      if (q == 0) {
+        eu = ux;
+        eF = Fx;
+      } else if (q == 1) {
+        eu = uy;
+        eF = Fy;
+      } else if (q == 2) {
+        eu = add2(ux, uy);
+        eF = add2(Fx, Fy);
+      } else {
+        eu = sub2(uy, ux);
+        eF = sub2(Fy, Fx);
+      }
+      const float2 se = fma2(mul2(n45, eu), eu, base2);
+      const float2 fe = fma2(mul2(eu, s2(9.f)), eF, m3uF);
+      const float2 E = fma2(s2(A), se, mul2(s2(B), fe));
+      const float2 O = fma2(eu, An3, mul2(s2(3.f * B), eF));
+      o[i] = add2(fma2(s2(keep), h[i], E), O);
+      o[ib] = sub2(fma2(s2(keep), h[ib], E), O);
+    }
+    const long long sa = (long long)ya * Lx + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) hout[i * Sz + sa] = o[i].x;
+    uout[sa] = ux.x;
+    uout[Sz + sa] = uy.x;
+    if (row_b) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) hout[i * Sz + sa + Lx] = o[i].y;
+      uout[sa + Lx] = ux.y;
+      uout[Sz + sa + Lx] = uy.y;
+    }
+  }
+}
 template <bool TGEN, int MINB>
 __global__ void __launch_bounds__(256, MINB)
     collide2d_tma_pipe_kernel(const __grid_constant__ CUtensorMap map_p32,
@@ -498,8 +750,7 @@ __global__ void __launch_bounds__(256, MINB)
   const int Lx = p.Lx, Ly = p.Ly;
   const long long Sz = (long long)Lx * Ly;
   const int ntx = (Lx + TT - 1) / TT, ntiles = ntx * ((Ly + PY - 1) / PY);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int ly0 = 2 * ty;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
@@ -529,10 +780,6 @@ __global__ void __launch_bounds__(256, MINB)
     if (t0 < ntiles) issue(t0, 0);
   }
   __syncthreads();
-  const float om = p.tau_inv, keep = 1.f - p.tau_inv;
-  const float A0 = om * float(q9_w(0)), B0 = p.pref * float(q9_w(0));
-  const float A1 = om * float(q9_w(1)), B1 = p.pref * float(q9_w(1));
-  const float A2 = om * float(q9_w(5)), B2 = p.pref * float(q9_w(5));
   int k = 0;
   bool failed = false;
   while (true) {
@@ -546,9 +793,8 @@ __global__ void __launch_bounds__(256, MINB)
       stile[st ^ 1] = tn;
       if (tn < ntiles) issue(tn, st ^ 1);
     }
-    const int x0 = (tile % ntx) * TT, y0 = (tile / ntx) * PY, x = x0 + tx;
+    const int x0 = (tile % ntx) * TT, y0 = (tile / ntx) * PY;
     float *pops = reinterpret_cast<float *>(base + P_OFF_STAGE + st * PSTAGE);
-    float(*sphi)[PHW] = reinterpret_cast<float(*)[PHW]>(pops + PPOP_FLOATS);
     if constexpr (TGEN) {
       for (int q = tid; q < MUW * PMUH; q += 256) {
         const int ry = q / MUW, rx = q - ry * MUW;
@@ -556,192 +802,14 @@ __global__ void __launch_bounds__(256, MINB)
         spn[ry][rx] = p.cs2mT * (1.f + dn[(long long)gy * Lx + gx]);
       }
     }
+    PipeFix fix;
+    pipe_fix_load(fix, hin, phi, Lx, Ly, Sz, x0, y0);
     const bool arrived = bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, g_collide_tma_wait_ns);
     if (!__syncthreads_and(arrived)) {
       failed = true;
       break;
     }
-    // periodic images of the cells the copies left as zeros (edge tiles)
-    if (x0 == 0 || y0 == 0 || x0 + TT + 2 > Lx || y0 + PY + 2 > Ly) {
-      for (int q = tid; q < (TT + 4) * PPHH; q += 256) {
-        const int ry = q / (TT + 4), rx = q - ry * (TT + 4);
-        const int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-        if (gx < 0 || gx >= Lx || gy < 0 || gy >= Ly)
-          sphi[ry][rx + 2] = phi[(long long)wrapi(gy, Ly) * Lx + wrapi(gx, Lx)];
-      }
-      for (int q = tid; q < 8 * (PY + TT); q += 256) {
-        const int i = 1 + q / (PY + TT), j = q % (PY + TT);
-        const int ex = q9_ex(i), ey = q9_ey(i);
-        int xs, ys;
-        if (j < PY) {
-          if (ex == 0) continue;
-          xs = ex > 0 ? 0 : Lx - 1;
-          ys = y0 + j;
-        } else {
-          if (ey == 0) continue;
-          ys = ey > 0 ? 0 : Ly - 1;
-          xs = x0 + j - PY;
-        }
-        if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + PY || ys >= Ly) continue;
-        const int sx = wrapi(xs - ex, Lx), sy = wrapi(ys - ey, Ly);
-        pops[pplane_off(i) + (ys - y0) * plane_w(i) + (xs - x0) + col_off(i)] =
-            hin[i * Sz + (long long)sy * Lx + sx];
-      }
-    }
-    __syncthreads();
-    // mu on the tile + 1: this thread's two rows, then the frame
-    {
-      // site row ly is phi row ly + 2 and mu row ly + 1
-      float w[3][3];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) w[a + 1][j] = sphi[ly0 + 1 + a][tx + 3 + j];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          w[0][j] = w[1][j];
-          w[1][j] = w[2][j];
-          w[2][j] = sphi[ly0 + 3 + r][tx + 3 + j];
-        }
-        smu[ly0 + 1 + r][tx + 1] = mu_at(p, w);
-      }
-      if (tid < 2 * MUW + 2 * PY) {
-        int my, mx;
-        if (tid < MUW) {
-          my = 0;
-          mx = tid;
-        } else if (tid < 2 * MUW) {
-          my = PMUH - 1;
-          mx = tid - MUW;
-        } else {
-          const int q = tid - 2 * MUW;
-          my = 1 + (q >> 1);
-          mx = (q & 1) ? MUW - 1 : 0;
-        }
-        float v[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b2 = 0; b2 < 3; ++b2) v[a][b2] = sphi[my + a][mx + b2 + 2];
-        smu[my][mx] = mu_at(p, v);
-      }
-    }
-    __syncthreads();
-    // force (Eqs. 28, 30) of the two rows, then the packed collision
-    float2 Fx, Fy;
-    {
-      float m[4][3];  // mu rows ly0 .. ly0 + 3 (tile + 1 coordinates), columns tx .. tx + 2
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) m[a][j] = smu[ly0 + a][tx + j];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        float gmx = -p.M * m[r][0];
-        gmx += p.M * m[r][2];
-        gmx += -p.N * m[r + 1][0];
-        gmx += p.N * m[r + 1][2];
-        gmx += -p.M * m[r + 2][0];
-        gmx += p.M * m[r + 2][2];
-        float gmy = -p.M * m[r][0];
-        gmy += -p.N * m[r][1];
-        gmy += -p.M * m[r][2];
-        gmy += p.M * m[r + 2][0];
-        gmy += p.N * m[r + 2][1];
-        gmy += p.M * m[r + 2][2];
-        const float ph = sphi[ly0 + r + 2][tx + 4];
-        float fx = -ph * gmx, fy = -ph * gmy;
-        if constexpr (TGEN) {
-          const int mx = tx + 1, my = ly0 + r + 1;
-          float px = -p.M * spn[my - 1][mx - 1];
-          px += p.M * spn[my - 1][mx + 1];
-          px += -p.N * spn[my][mx - 1];
-          px += p.N * spn[my][mx + 1];
-          px += -p.M * spn[my + 1][mx - 1];
-          px += p.M * spn[my + 1][mx + 1];
-          float py = -p.M * spn[my - 1][mx - 1];
-          py += -p.N * spn[my - 1][mx];
-          py += -p.M * spn[my - 1][mx + 1];
-          py += p.M * spn[my + 1][mx - 1];
-          py += p.N * spn[my + 1][mx];
-          py += p.M * spn[my + 1][mx + 1];
-          fx += px;
-          fy += py;
-        }
-        if (r == 0) {
-          Fx.x = fx;
-          Fy.x = fy;
-        } else {
-          Fx.y = fx;
-          Fy.y = fy;
-        }
-      }
-    }
-    const int ya = y0 + ly0;
-    if (x < Lx && ya < Ly) {
-      const bool row_b = ya + 1 < Ly;
-      auto pop = [&](int i, int ly) { return pops[pplane_off(i) + ly * plane_w(i) + tx + col_off(i)]; };
-      float2 h[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) h[i] = make_float2(pop(i, ly0), pop(i, ly0 + 1));
-      float2 dens = h[0];
-#pragma unroll
-      for (int i = 1; i < 9; ++i) dens = add2(dens, h[i]);
-      const float2 jx = add2(add2(sub2(h[1], h[3]), sub2(h[5], h[7])), sub2(h[8], h[6]));
-      const float2 jy = add2(add2(sub2(h[2], h[4]), sub2(h[5], h[7])), sub2(h[6], h[8]));
-      const float2 n = add2(s2(1.f), dens);
-      Fx = fma2(n, s2(p.gx), Fx);
-      Fy = fma2(n, s2(p.gy), Fy);
-      const float2 inv_n = make_float2(1.f / n.x, 1.f / n.y);
-      const float2 ux = mul2(fma2(s2(0.5f), Fx, jx), inv_n);
-      const float2 uy = mul2(fma2(s2(0.5f), Fy, jy), inv_n);
-      const float2 usq = fma2(ux, ux, mul2(uy, uy));
-      const float2 uF = fma2(ux, Fx, mul2(uy, Fy));
-      const float2 base2 = fma2(n, mul2(usq, s2(-1.5f)), dens);
-      const float2 n45 = mul2(n, s2(4.5f)), m3uF = mul2(uF, s2(-3.f));
-      const float2 An3_1 = mul2(n, s2(3.f * A1)), An3_2 = mul2(n, s2(3.f * A2));
-      float2 o[9];
-      o[0] = fma2(s2(keep), h[0], fma2(s2(A0), base2, mul2(s2(-3.f * B0), uF)));
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = q < 2 ? q + 1 : q + 3, ib = i + 2;
-        const float A = q < 2 ? A1 : A2, B = q < 2 ? B1 : B2;
-        const float2 An3 = q < 2 ? An3_1 : An3_2;
-        float2 eu, eF;
-        if (q == 0) {
-          eu = ux;
-          eF = Fx;
-        } else if (q == 1) {
-          eu = uy;
-          eF = Fy;
-        } else if (q == 2) {
-          eu = add2(ux, uy);
-          eF = add2(Fx, Fy);
-        } else {
-          eu = sub2(uy, ux);
-          eF = sub2(Fy, Fx);
-        }
-        const float2 se = fma2(mul2(n45, eu), eu, base2);
-        const float2 fe = fma2(mul2(eu, s2(9.f)), eF, m3uF);
-        const float2 E = fma2(s2(A), se, mul2(s2(B), fe));
-        const float2 O = fma2(eu, An3, mul2(s2(3.f * B), eF));
-        o[i] = add2(fma2(s2(keep), h[i], E), O);
-        o[ib] = sub2(fma2(s2(keep), h[ib], E), O);
-      }
-      const long long sa = (long long)ya * Lx + x;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) hout[i * Sz + sa] = o[i].x;
-      uout[sa] = ux.x;
-      uout[Sz + sa] = uy.x;
-      if (row_b) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) hout[i * Sz + sa + Lx] = o[i].y;
-        uout[sa + Lx] = ux.y;
-        uout[Sz + sa + Lx] = uy.y;
-      }
-    }
+    pipe_tile<TGEN>(pops, smu, spn, fix, hin, hout, phi, uout, p, Lx, Ly, Sz, x0, y0, p.gx, p.gy);
     __syncthreads();  // stage st, smu and spn are free again; the next tile's slot is visible
     ++k;
   }
@@ -765,6 +833,103 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                       uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
+
+// The pipelined kernel over the 32 x 16 tiles of many independent lattices
+// packed end to end (one plane per population over all of them, ST sites):
+// tile k is items[k] = (instance, x0, y0, shape slot << 16 | index j within
+// the shape), copied through the slot's tensor maps in the kernel parameter
+// (populations at (x, y, j, plane), phi at (x, y, j)); the instance's body
+// force is on while t < force_steps.  T = 1/3.  Instances are at least
+// TMA_MIN_SIDE on a side.  Static schedule: CTA c takes items c, c + G,
+// c + 2G, ... (G CTAs, G <= nitems), and thread 0 loads the item after next
+// one tile ahead, so that no claim or dependent load stands between a tile
+// and the copies of the next.
+__global__ void __launch_bounds__(256, 4)
+    collide2d_tma_batch_kernel(const __grid_constant__ TmaShapeMaps maps, const float *__restrict__ hin,
+                               float *__restrict__ hout, const float *__restrict__ phi,
+                               float *__restrict__ uout, long long ST, const TiledInst *__restrict__ inst,
+                               const int4 *__restrict__ items, int nitems, KParams<float> p, long long t) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *base = smem_raw + ((128u - (su32(smem_raw) & 127u)) & 127u);
+  const uint32_t bar0 = su32(base);
+  float(*smu)[MUW] = reinterpret_cast<float(*)[MUW]>(base + P_OFF_MU);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int G = gridDim.x;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();  // phi(t) and the populations come from earlier kernels
+  pdl_trigger();
+  // thread 0: the ten copies of item `it` into stage st, completing on its mbarrier
+  auto issue = [&](const int4 it, int st) {
+    const int slot = it.w >> 16, j = it.w & 0xffff;
+    const CUtensorMap *m = reinterpret_cast<const CUtensorMap *>(&maps.map[slot][0][0]);
+    unsigned char *sb = base + P_OFF_STAGE + st * PSTAGE;
+    const uint32_t bar = bar0 + 8 * st;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic accesses first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)PSTAGE)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      tma_4d(su32(sb + 4 * pplane_off(i)), plane_w(i) == TT ? m : m + 1, it.y + box_dx(i), it.z - q9_ey(i), j, i,
+             bar);
+    tma_3d(su32(sb + 4 * PPOP_FLOATS), m + 2, it.y - 4, it.z - 2, j, bar);
+  };
+  int4 nxt = make_int4(0, 0, 0, 0);  // thread 0: the item after the one in flight
+  if (tid == 0) {
+    issue(items[blockIdx.x], 0);
+    if (blockIdx.x + G < nitems) nxt = items[blockIdx.x + G];
+  }
+  int k = 0, tile = blockIdx.x;
+  bool failed = false;
+  for (; tile < nitems; tile += G, ++k) {
+    const int st = k & 1;
+    // the copies of the next item go into the other stage (free since the end
+    // of the previous iteration)
+    if (tid == 0 && tile + G < nitems) {
+      issue(nxt, st ^ 1);
+      if (tile + 2 * G < nitems) nxt = items[tile + 2 * G];
+    }
+    const int4 it = items[tile];
+    const int slot = it.w >> 16, j = it.w & 0xffff;
+    const int Lx = maps.Lx[slot], Ly = maps.Ly[slot];
+    const long long off = maps.off0[slot] + (long long)j * Lx * Ly;
+    float *pops = reinterpret_cast<float *>(base + P_OFF_STAGE + st * PSTAGE);
+    PipeFix fix;
+    pipe_fix_load(fix, hin + off, phi + off, Lx, Ly, ST, it.y, it.z);
+    const bool arrived = bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, g_collide_tma_wait_ns);
+    if (!__syncthreads_and(arrived)) {
+      failed = true;
+      break;
+    }
+    const TiledInst &I = inst[it.x];
+    const bool on = t < I.force_steps;
+    pipe_tile<false>(pops, smu, nullptr, fix, hin + off, hout + off, phi + off, uout + off, p, Lx, Ly, ST, it.y,
+                     it.z, on ? I.gx : 0.f, on ? I.gy : 0.f);
+    __syncthreads();  // stage st and smu are free again
+  }
+  if (tid == 0 && failed) {
+    // a copy did not complete within the wait bound: report it and let the copies
+    // still in flight land before the CTA's shared memory is released
+    atomicExch(&g_collide_tma_err, 1);
+    const int st = k & 1;
+    bar_wait(bar0 + 8 * st, (uint32_t)(k >> 1) & 1u, 500000000ull);
+    if (tile + G < nitems) bar_wait(bar0 + 8 * (st ^ 1), (uint32_t)((k + 1) >> 1) & 1u, 500000000ull);
+  }
+}
+
 // ---- host side -------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -785,7 +950,7 @@ bool encode(CUtensorMap *map, CUtensorMapDataType type, void *ptr, int rank, con
             const cuuint64_t *strides, const cuuint32_t *box) {
   auto fn = encode_fn();
   if (fn == nullptr) return false;
-  const cuuint32_t ones[3] = {1, 1, 1};
+  const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
   return fn(map, type, rank, ptr, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -932,6 +1097,9 @@ cudaError_t collide2d_tma_configure(int precision) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(collide2d_tma_pipe_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pipe_smem<true>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(collide2d_tma_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pipe_smem<false>());
   return e;
 }
 
@@ -947,6 +1115,47 @@ int collide2d_tma_error(bool reset) {
     cudaMemcpyToSymbol(g_collide_tma_err, &zero, sizeof zero);
   }
   return v;
+}
+
+
+int collide2d_tma_batch_min_side() { return TMA_MIN_SIDE; }
+
+bool collide2d_tma_batch_shape(TmaShapeMaps *m, int slot, float *h, float *phi, long long ST, int Lx, int Ly,
+                               long long off0, int n) {
+  static_assert(sizeof(CUtensorMap) == 128 && alignof(TmaShapeMaps) >= 64, "tensor map size and alignment");
+  if (slot < 0 || slot >= TMA_BATCH_SHAPES || n < 1 || n > 0xffff || Lx < TMA_MIN_SIDE || Ly < TMA_MIN_SIDE ||
+      Lx % 4 != 0 || off0 % 4 != 0 || ST % 4 != 0)
+    return false;
+  CUtensorMap *mk = reinterpret_cast<CUtensorMap *>(&m->map[slot][0][0]);
+  const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t S = (cuuint64_t)Lx * Ly;
+  const cuuint64_t pd[4] = {(cuuint64_t)Lx, (cuuint64_t)Ly, (cuuint64_t)n, 9};
+  const cuuint64_t ps[3] = {4 * (cuuint64_t)Lx, 4 * S, 4 * (cuuint64_t)ST};
+  const cuuint64_t fd[3] = {(cuuint64_t)Lx, (cuuint64_t)Ly, (cuuint64_t)n}, fs[2] = {4 * (cuuint64_t)Lx, 4 * S};
+  const cuuint32_t q32[4] = {TT, PY, 1, 1}, q36[4] = {TT + 4, PY, 1, 1}, qphi[3] = {PHW, PPHH, 1};
+  if (!encode(&mk[0], f32, h + off0, 4, pd, ps, q32) || !encode(&mk[1], f32, h + off0, 4, pd, ps, q36) ||
+      !encode(&mk[2], f32, phi + off0, 3, fd, fs, qphi))
+    return false;
+  m->Lx[slot] = Lx;
+  m->Ly[slot] = Ly;
+  m->off0[slot] = off0;
+  return true;
+}
+
+cudaError_t collide2d_tma_batch(const TmaShapeMaps &maps, const float *hin, float *hout, const float *phi,
+                                float *u, long long ST, const TiledInst *inst, const int4 *items, int nitems,
+                                const KParams<float> &p, long long t, cudaStream_t s, bool pdl) {
+  static const int resident = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, collide2d_tma_batch_kernel, 256, pipe_smem<false>());
+    return std::max(1, sms * std::max(per, 1));
+  }();
+  if (nitems <= 0) return cudaSuccess;
+  const int grid = std::min(nitems, resident);
+  return launch_ex(pdl, collide2d_tma_batch_kernel, dim3(grid), dim3(32, 256 / 32), pipe_smem<false>(), s, maps,
+                   hin, hout, phi, u, ST, inst, items, nitems, p, t);
 }
 
 }  // namespace hlbm

@@ -197,18 +197,18 @@ __device__ __forceinline__ float4 wv_substep(WvSub &st, const float4 &pn, const 
   return out;
 }
 
+// One strip segment of an Lx x Ly lattice whose u* planes are S values apart:
+// lanes cover columns x0 .. x0 + 127 (x0 a multiple of 4, wrapped around the
+// lattice as often as needed), output rows ys .. ys + NY - 1 (wrapped reads).
 template <int SUB>
-__global__ void __launch_bounds__(Wave<SUB>::NT)
-    fd2d_wave_kernel(const float *__restrict__ phi_in, const float *__restrict__ u,
-                     float *__restrict__ phi_out, KParams<float> p, int NY) {
+__device__ __forceinline__ void fd2d_wave_strip(const float *__restrict__ phi_in, const float *__restrict__ u,
+                                                float *__restrict__ phi_out, const KParams<float> &p,
+                                                const int Lx, const int Ly, const long long S, const int x0,
+                                                const int ys, const int NY) {
   using G = Wave<SUB>;
   extern __shared__ __align__(16) float wv_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = 4 * lane;
-  const int Lx = p.Lx, Ly = p.Ly;
-  const long long S = (long long)Lx * Ly;
-  const int x0 = blockIdx.x * G::TX - G::HX;  // a multiple of 4
-  const int ys = blockIdx.y * NY;             // first output row of the segment
-  const int J = NY + 2 * G::HY;               // input rows of the segment
+  const int J = NY + 2 * G::HY;  // input rows of the segment
   const int T = G::ticks(NY);
   const WvConst k{p.dt, p.dtG, p.a, p.b, p.kappa, p.cubic_at_half != 0};
   // an output lane writes its float4 when the columns are inside the strip's
@@ -295,6 +295,28 @@ __global__ void __launch_bounds__(Wave<SUB>::NT)
 }
 
 template <int SUB>
+__global__ void __launch_bounds__(Wave<SUB>::NT)
+    fd2d_wave_kernel(const float *__restrict__ phi_in, const float *__restrict__ u,
+                     float *__restrict__ phi_out, KParams<float> p, int NY) {
+  fd2d_wave_strip<SUB>(phi_in, u, phi_out, p, p.Lx, p.Ly, (long long)p.Lx * p.Ly,
+                       blockIdx.x * Wave<SUB>::TX - Wave<SUB>::HX, blockIdx.y * NY, NY);
+}
+
+// The same update for many independent lattices packed end to end (one plane
+// per field over all of them, u*_y ST values after u*_x): CTA b takes the
+// item items[b] = (instance, strip, first output row, output rows).
+template <int SUB>
+__global__ void __launch_bounds__(Wave<SUB>::NT)
+    fd2d_wave_batch_kernel(const float *__restrict__ phi_in, const float *__restrict__ u,
+                           float *__restrict__ phi_out, long long ST, const TiledInst *__restrict__ inst,
+                           const int4 *__restrict__ items, KParams<float> p) {
+  const int4 it = items[blockIdx.x];
+  const TiledInst I = inst[it.x];
+  fd2d_wave_strip<SUB>(phi_in + I.off, u + I.off, phi_out + I.off, p, I.Lx, I.Ly, ST,
+                       it.y * Wave<SUB>::TX - Wave<SUB>::HX, it.z, it.w);
+}
+
+template <int SUB>
 cudaError_t fd2d_wave_one(lbm_handle *h, const KParams<float> &p, const float *src, float *dst, int NY) {
   using G = Wave<SUB>;
   dim3 grid((p.Lx + G::TX - 1) / G::TX, (p.Ly + NY - 1) / NY);
@@ -336,7 +358,19 @@ cudaError_t fd2d_wave_configure() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fd2d_wave_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Wave<2>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fd2d_wave_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Wave<2>::smem);
   return e;
+}
+
+int fd2d_wave_batch_strip_columns() { return Wave<2>::TX; }
+
+cudaError_t fd2d_wave_batch(const float *phi_in, const float *u, float *phi_out, long long ST,
+                            const TiledInst *inst, const int4 *items, int nitems, const KParams<float> &p,
+                            cudaStream_t s, bool pdl) {
+  return launch_ex(pdl, fd2d_wave_batch_kernel<2>, dim3(nitems), dim3(Wave<2>::NT), Wave<2>::smem, s, phi_in, u,
+                   phi_out, ST, inst, items, p);
 }
 
 // sub = 2 or 4 substeps in one launch; NY = output rows of a segment

@@ -25,23 +25,22 @@ namespace {
 constexpr int C2_TX = 32;  // tile width (one warp along x)
 constexpr int C2_BY = 8;   // block of 32 x 8 threads, RY rows each (tile height 8 RY)
 
-// Wraps x in [-L, 2L) into [0, L).
-__device__ __forceinline__ int wrap1(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
-
+// One 32 x 8 RY tile with origin (x0, y0) of an Lx x Ly periodic lattice whose
+// population and velocity planes are Sz values apart (Lx Ly for one lattice,
+// the total site count for a batch); gx, gy the body force per unit density.
 template <typename S, typename C, bool TGEN, int MODE, int RY>
-__global__ void __launch_bounds__(256, 2)
-    collide2d_kernel(const S *__restrict__ hin, S *__restrict__ hout, const C *__restrict__ phi,
-                     const C *__restrict__ dn, C *__restrict__ uout, double *__restrict__ stg,
-                     KParams<C> p) {
+__device__ __forceinline__ void collide2d_tile(const S *__restrict__ hin, S *__restrict__ hout,
+                                               const C *__restrict__ phi, const C *__restrict__ dn,
+                                               C *__restrict__ uout, double *__restrict__ stg,
+                                               const KParams<C> &p, const int Lx, const int Ly,
+                                               const long long Sz, const int x0, const int y0, const C gx,
+                                               const C gy) {
   constexpr int C2_TY = C2_BY * RY;              // tile height
   constexpr int PX = C2_TX + 4, PY = C2_TY + 4;  // phi tile + halo 2
   constexpr int MX = C2_TX + 2, MY = C2_TY + 2;  // mu tile + halo 1
   __shared__ C sphi[PY][PX];
   __shared__ C smu[MY][MX];
   __shared__ C spn[TGEN ? MY : 1][TGEN ? MX : 1];
-  const int Lx = p.Lx, Ly = p.Ly;
-  const long long Sz = (long long)Lx * Ly;
-  const int x0 = blockIdx.x * C2_TX, y0 = blockIdx.y * C2_TY;
   const int tx = threadIdx.x, tid = threadIdx.y * 32 + threadIdx.x;
 
   // 1. issue the pull loads f_i(r, t) = buf_i(r - e_i) of this thread's sites
@@ -154,8 +153,8 @@ __global__ void __launch_bounds__(256, 2)
     const C jx = ((h[1] - h[3]) + (h[5] - h[7])) + (h[8] - h[6]);
     const C jy = ((h[2] - h[4]) + (h[5] - h[7])) + (h[6] - h[8]);
     const C n = C(1) + dens;
-    Fx += n * p.gx;
-    Fy += n * p.gy;
+    Fx += n * gx;
+    Fy += n * gy;
     // u* (Eq. 18)
     const C ux = (jx + C(0.5) * Fx) / n;
     const C uy = (jy + C(0.5) * Fy) / n;
@@ -197,6 +196,32 @@ __global__ void __launch_bounds__(256, 2)
     uout[s] = ux;
     uout[Sz + s] = uy;
   }
+}
+
+template <typename S, typename C, bool TGEN, int MODE, int RY>
+__global__ void __launch_bounds__(256, 2)
+    collide2d_kernel(const S *__restrict__ hin, S *__restrict__ hout, const C *__restrict__ phi,
+                     const C *__restrict__ dn, C *__restrict__ uout, double *__restrict__ stg,
+                     KParams<C> p) {
+  collide2d_tile<S, C, TGEN, MODE, RY>(hin, hout, phi, dn, uout, stg, p, p.Lx, p.Ly, (long long)p.Lx * p.Ly,
+                                       blockIdx.x * C2_TX, blockIdx.y * (C2_BY * RY), p.gx, p.gy);
+}
+
+// The same tile step for many independent lattices packed end to end (one
+// plane per population over all of them, ST sites): CTA b takes the 32 x 16
+// tile items[b] = (instance, x0, y0) and the instance's size, offset and body
+// force (on while t < force_steps).  FP32 deviations, T = 1/3.
+__global__ void __launch_bounds__(256, 2)
+    collide2d_batch_kernel(const float *__restrict__ hin, float *__restrict__ hout,
+                           const float *__restrict__ phi, float *__restrict__ u, long long ST,
+                           const TiledInst *__restrict__ inst, const int4 *__restrict__ items,
+                           KParams<float> p, long long t) {
+  const int4 it = items[blockIdx.x];
+  const TiledInst I = inst[it.x];
+  const bool on = t < I.force_steps;
+  collide2d_tile<float, float, false, COLLIDE_STEP, BATCH_TILE_ROWS / C2_BY>(
+      hin + I.off, hout + I.off, phi + I.off, nullptr, u + I.off, nullptr, p, I.Lx, I.Ly, ST, it.y, it.z,
+      on ? I.gx : 0.f, on ? I.gy : 0.f);
 }
 
 // ---- collide with asynchronous staging (FP32 / FP64 populations) ----------------
@@ -1404,6 +1429,13 @@ cudaError_t density2d_launch(lbm_handle *h, int in) {
           static_cast<const __half *>(h->h[in]), static_cast<float *>(h->dn), p);
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t collide2d_batch(const float *hin, float *hout, const float *phi, float *u, long long ST,
+                            const TiledInst *inst, const int4 *items, int nitems, const KParams<float> &p,
+                            long long t, cudaStream_t s) {
+  collide2d_batch_kernel<<<nitems, dim3(32, C2_BY), 0, s>>>(hin, hout, phi, u, ST, inst, items, p, t);
   return cudaGetLastError();
 }
 

@@ -25,9 +25,11 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 
 bool pdl_enabled();  // HLBM_PDL=0 turns it off (read once)
 
+// launch_pdl, or a plain launch when pdl is false (the kernel's PDL calls are
+// then no-ops)
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                       cudaStream_t stream, Args... args) {
+cudaError_t launch_ex(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t stream, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -37,8 +39,13 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cfg.numAttrs = pdl && pdl_enabled() ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args... args) {
+  return launch_ex(true, kernel, grid, block, smem, stream, args...);
 }
 
 
@@ -111,6 +118,8 @@ __device__ __forceinline__ int wrapi(int x, int L) {
   x %= L;
   return x < 0 ? x + L : x;
 }
+// Wraps x in [-L, 2L) into [0, L).
+__device__ __forceinline__ int wrap1(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
 
 // ---- kernel parameter block (host computes it in FP64, kernels read type C) -------
 template <typename C>
@@ -231,6 +240,47 @@ cudaError_t fd2d_wave(lbm_handle *h, const KParams<float> &p, const float *src, 
                       int NY);
 cudaError_t fd2d_wave_configure();
 int fd2d_wave_slots(int sub, int *strips, int Lx);  // CTAs of one wave; strips of Lx
+// Batches of independent 2D lattices advanced tile by tile (the tiled path
+// of batch.cu): the instance table, the collide over 32 x 16 tiles (items
+// (instance, x0, y0, _)) by the tile kernel (kernels_2d.cu) or the pipelined
+// TMA kernel (collide2d_tma.cu), and the two-substep wavefront FD over
+// 128-column strips (fd2d_wave.cu, items (instance, strip, first output row,
+// output rows)).
+struct TiledInst {
+  int Lx, Ly;
+  long long off;  // first site of the instance in the packed planes
+  float gx, gy;   // body force per unit density while t < force_steps
+  long long force_steps;
+};
+constexpr int BATCH_TILE_ROWS = 16;
+cudaError_t collide2d_batch(const float *hin, float *hout, const float *phi, float *u, long long ST,
+                            const TiledInst *inst, const int4 *items, int nitems, const KParams<float> &p,
+                            long long t, cudaStream_t s);
+int fd2d_wave_batch_strip_columns();  // output columns of a strip
+cudaError_t fd2d_wave_batch(const float *phi_in, const float *u, float *phi_out, long long ST,
+                            const TiledInst *inst, const int4 *items, int nitems, const KParams<float> &p,
+                            cudaStream_t s, bool pdl);
+// The TMA collide takes instances at least collide2d_tma_batch_min_side() on
+// a side.  The instances of one shape (Lx, Ly) are stored n apart by Lx Ly
+// sites from off0 on, so that one set of three tensor maps covers them all
+// (populations as an Lx x Ly x n x 9 tensor, phi as Lx x Ly x n); a launch
+// takes the maps of up to TMA_BATCH_SHAPES shapes as a kernel parameter, and
+// its items carry (shape slot << 16 | index within the shape) in w.
+constexpr int TMA_BATCH_SHAPES = 24;
+struct TmaShapeMaps {
+  alignas(64) unsigned char map[TMA_BATCH_SHAPES][3][128];  // CUtensorMap: p32, p36, phi
+  int Lx[TMA_BATCH_SHAPES], Ly[TMA_BATCH_SHAPES];
+  long long off0[TMA_BATCH_SHAPES];
+};
+int collide2d_tma_batch_min_side();
+// fills slot `slot` of `m` for the planes h, phi of one buffer parity (false
+// if the driver's encoder is missing or refuses the shape)
+bool collide2d_tma_batch_shape(TmaShapeMaps *m, int slot, float *h, float *phi, long long ST, int Lx, int Ly,
+                               long long off0, int n);
+cudaError_t collide2d_tma_batch(const TmaShapeMaps &maps, const float *hin, float *hout, const float *phi,
+                                float *u, long long ST, const TiledInst *inst, const int4 *items, int nitems,
+                                const KParams<float> &p, long long t, cudaStream_t s, bool pdl);
+
 int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
 int collide2d_tma_set_wait_ns(unsigned long long ns);  // bound of the copy waits (0 on success)
 

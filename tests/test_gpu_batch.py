@@ -1,5 +1,7 @@
-"""GPU parity of the batched persistent engine (independent lattices of
-uneven size in one launch) against the FP64 oracle, instance by instance."""
+"""GPU parity of the batched engine (independent lattices of uneven size
+advanced together: the persistent kernel, or the tiled path of TMA-staged and
+tile-kernel collides and wavefront FD launches) against the FP64 oracle,
+instance by instance."""
 import numpy as np
 import pytest
 
@@ -110,6 +112,100 @@ def test_batch_config_fp32_sampled_instances():
         umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
         assert np.max(np.abs(gphi - rphi)) <= 1e-5, k
         assert np.max(np.abs(gu - ru)) <= 1e-3 * umax, k
+    b.close()
+
+
+TILED_INSTS = [(12, 20, (0.0, 0.0), 0), (32, 48, (1e-5, 0.0), 12), (100, 36, (0.0, -2e-5), 40),
+               (116, 130, (2e-5, 1e-5), 5), (256, 80, (0.0, 0.0), 0), (48, 3, (1e-5, 0.0), 100),
+               (64, 64, (0.0, 1e-5), 30)]
+
+
+@pytest.mark.parametrize("graphs,tma", [(True, True), (False, True), (True, False)])
+def test_tiled_batch_matches_oracle_fp32(graphs, tma, monkeypatch):
+    """The tiled path against the oracle at the FP32 bar: the TMA collide
+    for the instances at least 64 on a side and the tile kernel for the rest
+    (or the tile kernel for all), two-substep wavefront FD launches; an
+    instance narrower than one strip (12 wide: the strip wraps around it),
+    ragged tiles, strips and segments, a 3-row instance, and body forces
+    switching off inside a call."""
+    monkeypatch.setenv("HLBM_BATCH_PATH", "tiled")
+    if not tma:
+        monkeypatch.setenv("HLBM_BATCH_NO_TMA", "1")
+    common = lbm.LbmParams(precision=lbm.LBM_F32DEV, fd_substeps=4, **CFG1)
+    b = lbm.Batch(common, TILED_INSTS)
+    b.set_graphs(graphs)
+    assert b.shape()["threads"] == 0  # the tiled path
+    fields = []
+    for k, (Lx, Ly, g, fs) in enumerate(TILED_INSTS):
+        f = _instance_fields(Lx, Ly, R=max(2, min(Lx, Ly) / 4), seed=30 + k)
+        fields.append(f)
+        b.init_fields(k, *f)
+    b.step(9).step(21)
+    for k, (Lx, Ly, g, fs) in enumerate(TILED_INSTS):
+        rn, rphi, ru = _oracle_run(Lx, Ly, g, fs, fields[k], 30)
+        gn, gphi, gu = b.moments(k)
+        umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+        assert np.max(np.abs(gphi - rphi)) <= 1e-5, k
+        assert np.max(np.abs(gu - ru)) <= 1e-3 * umax, k
+        assert np.max(np.abs(gn - rn)) <= 1e-5, k
+    b.close()
+
+
+def test_tiled_batch_many_shapes_fp32(monkeypatch):
+    """The TMA collide's per-shape tensor maps: 26 distinct shapes (more than
+    one launch's 24 slots) and repeated shapes (instances at j > 0 of a
+    shape, listed apart from one another), each instance against the oracle."""
+    monkeypatch.setenv("HLBM_BATCH_PATH", "tiled")
+    shapes = [(64 + 4 * (a % 7), 64 + 4 * (a // 7)) for a in range(26)]
+    insts = [(Lx, Ly, (1e-5 if k % 3 == 0 else 0.0, 0.0), 4 if k % 3 == 0 else 0)
+             for k, (Lx, Ly) in enumerate(shapes + [shapes[0], shapes[25], shapes[0], shapes[7]])]
+    common = lbm.LbmParams(precision=lbm.LBM_F32DEV, fd_substeps=4, **CFG1)
+    b = lbm.Batch(common, insts)
+    assert b.shape()["threads"] == 0
+    fields = []
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        f = _instance_fields(Lx, Ly, R=12.0, seed=60 + k)
+        fields.append(f)
+        b.init_fields(k, *f)
+    b.step(8)
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        rn, rphi, ru = _oracle_run(Lx, Ly, g, fs, fields[k], 8)
+        gn, gphi, gu = b.moments(k)
+        umax = float(np.max(np.sqrt(np.sum(ru * ru, axis=0))))
+        assert np.max(np.abs(gphi - rphi)) <= 1e-5, k
+        assert np.max(np.abs(gu - ru)) <= 1e-3 * umax, k
+    b.close()
+
+
+@pytest.mark.parametrize("kw", [dict(fd_substeps=5), dict(adv_variant=1)])
+def test_tiled_batch_falls_back_when_not_eligible(kw, monkeypatch):
+    """Odd m or the flux form: the persistent kernel runs even when the tiled
+    path is asked for."""
+    monkeypatch.setenv("HLBM_BATCH_PATH", "tiled")
+    args = dict(CFG1, precision=lbm.LBM_F32DEV, fd_substeps=4)
+    args.update(kw)
+    b = lbm.Batch(lbm.LbmParams(**args), [(32, 32, (0.0, 0.0), 0)])
+    assert b.shape()["threads"] > 0
+    b.close()
+
+
+def test_persistent_path_forced_fp32(monkeypatch):
+    """HLBM_BATCH_PATH=persistent keeps the persistent kernel on an eligible
+    batch, which still meets the FP32 bar."""
+    monkeypatch.setenv("HLBM_BATCH_PATH", "persistent")
+    insts = TILED_INSTS[:4]
+    b = lbm.Batch(lbm.LbmParams(precision=lbm.LBM_F32DEV, fd_substeps=4, **CFG1), insts)
+    assert b.shape()["threads"] > 0
+    fields = []
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        f = _instance_fields(Lx, Ly, R=max(2, min(Lx, Ly) / 4), seed=90 + k)
+        fields.append(f)
+        b.init_fields(k, *f)
+    b.step(20)
+    for k, (Lx, Ly, g, fs) in enumerate(insts):
+        rn, rphi, ru = _oracle_run(Lx, Ly, g, fs, fields[k], 20)
+        gn, gphi, gu = b.moments(k)
+        assert np.max(np.abs(gphi - rphi)) <= 1e-5, k
     b.close()
 
 

@@ -57,3 +57,80 @@ def test_phi_box_covers_the_halo():
     lo, hi = -4, -4 + PHW - 1
     assert lo <= -2 and hi >= TT + 1
     assert -2 + PHH - 1 == TT + 1
+
+
+# ---- the edge fixups of the pipelined kernels (32 x 16 tiles) ---------------------------
+PY, PPHH = 16, 20
+
+
+def phi_fix_cells(Lx, Ly, x0, y0):
+    """The phi box cells (rx, ry) of tile (x0, y0) that pipe_fix_load loads,
+    in its order: the column strips (all PPHH rows), then the row strips
+    between them."""
+    rxr, ryb = Lx - x0 + 2, Ly - y0 + 2
+    wl, wr = (2 if x0 == 0 else 0), max(0, TT + 4 - rxr)
+    ht, hb = (2 if y0 == 0 else 0), max(0, PPHH - ryb)
+    if wl + wr + ht + hb == 0:
+        return []
+    ncol, wc = PPHH * (wl + wr), TT + 4 - wl - wr
+    ntot = ncol + (ht + hb) * wc
+    assert ntot <= 3 * 256  # three slots per thread
+    out = []
+    for q in range(ntot):
+        if q < ncol:
+            c, ry = divmod(q, PPHH)
+            rx = c if c < wl else rxr + (c - wl)
+        else:
+            r, cx = divmod(q - ncol, wc)
+            rx, ry = wl + cx, (r if r < ht else ryb + (r - ht))
+        out.append((rx, ry))
+    return out
+
+
+def pop_fix_cells(Lx, Ly, x0, y0):
+    """(i, xs, ys) of the populations pulled across the lattice's edges that
+    pipe_fix_load loads (8 planes x (PY + TT) candidates, two slots)."""
+    out = []
+    for q in range(8 * (PY + TT)):
+        assert q < 2 * 256
+        i, j = 1 + q // (PY + TT), q % (PY + TT)
+        ex, ey = E[i]
+        if j < PY:
+            if ex == 0:
+                continue
+            xs, ys = (0 if ex > 0 else Lx - 1), y0 + j
+        else:
+            if ey == 0:
+                continue
+            ys, xs = (0 if ey > 0 else Ly - 1), x0 + j - PY
+        if xs < x0 or xs >= x0 + TT or xs >= Lx or ys < y0 or ys >= y0 + PY or ys >= Ly:
+            continue
+        out.append((i, xs, ys))
+    return out
+
+
+@pytest.mark.parametrize("Lx,Ly", [(64, 64), (68, 80), (100, 64), (128, 132), (96, 200), (260, 68)])
+def test_edge_fixups_cover_exactly_the_cells_the_copies_zero(Lx, Ly):
+    """Every phi cell of a tile's 36 x 20 box outside the lattice is loaded
+    exactly once (and no inside cell), its periodic image within one
+    conditional wrap; every population of the tile whose pull buf_i(r - e_i)
+    crosses an edge is loaded, and no other."""
+    for y0 in range(0, Ly, PY):
+        for x0 in range(0, Lx, TT):
+            cells = phi_fix_cells(Lx, Ly, x0, y0)
+            assert len(cells) == len(set(cells))
+            outside = {(rx, ry) for ry in range(PPHH) for rx in range(TT + 4)
+                       if not (0 <= x0 - 2 + rx < Lx and 0 <= y0 - 2 + ry < Ly)}
+            assert set(cells) == outside, (x0, y0)
+            for rx, ry in cells:
+                gx, gy = x0 - 2 + rx, y0 - 2 + ry
+                assert -Lx <= gx < 2 * Lx and -Ly <= gy < 2 * Ly  # wrap1's range
+                assert PHW * ry + rx + 2 < PHW * PPHH
+            crossing = set()
+            for ys in range(y0, min(y0 + PY, Ly)):
+                for xs in range(x0, min(x0 + TT, Lx)):
+                    for i in range(1, 9):
+                        sx, sy = xs - E[i][0], ys - E[i][1]
+                        if not (0 <= sx < Lx and 0 <= sy < Ly):
+                            crossing.add((i, xs, ys))
+            assert set(pop_fix_cells(Lx, Ly, x0, y0)) == crossing, (x0, y0)
