@@ -344,8 +344,8 @@ def run_ours(args, rank, world, local):
                "avg_launch_us": fd_avg_s * 1e6, "peak_kind": "derived (unit counts x clock)",
                "share_of_step": fd_ms / (coll_ms + fd_ms)}
     # the same kernels inside the graph-timed step: their event times above
-    # are taken on eager launches (each bracketed by events, no programmatic
-    # overlap), which sum to more than the graph step; the in-step figures
+    # are taken on eager launches (each bracketed by events), which sum to
+    # more than the graph step (launch gaps); the in-step figures
     # share the graph step's time in the proportion of the event times
     graph_lb_us = ms_max / (args.steps * LB_PER_STEP) * 1000.0
     eager_lb_us = (coll_ms + fd_ms) / 2000.0 * 1000.0

@@ -20,7 +20,8 @@
 // items -- the persistent TMA-staged kernel, through one set of tensor maps
 // per instance shape, for the instances at least 64 on a side, the tile
 // kernel for the rest -- and m / 2 launches of the two-substep wavefront FD
-// kernel over a table of (instance, strip, segment of at most 64 rows) items,
+// kernel over a table of (instance, strip, segment of at most 48 rows) items
+// (longest first; HLBM_BATCH_FD_ROWS changes the 48),
 // per LB step, captured in a CUDA graph: every population and phi value is
 // read and written once per step as on a single lattice.  The launches are
 // plain (no programmatic dependent launch: an early-scheduled grid would hold
@@ -572,7 +573,7 @@ bool tiled_eligible(const lbm_batch *b) {
 // side, a slot per run of equal shapes in storage order of up to 0xffff
 // instances; the tile kernel for the rest, or for every instance without the
 // driver's tensor-map encoder or with HLBM_BATCH_NO_TMA set) and FD strips
-// split into segments of at most 64 rows.
+// split into segments of at most 48 rows (HLBM_BATCH_FD_ROWS).
 int build_tiles(lbm_batch *b) {
   std::vector<TiledInst> ti;
   std::vector<int4> ci, fi, tmi;
@@ -624,13 +625,17 @@ int build_tiles(lbm_batch *b) {
       break;
     }
   }
+  const char *fr = std::getenv("HLBM_BATCH_FD_ROWS");
+  const int max_rows = fr ? std::max(8, std::atoi(fr)) : 48;
   for (int k = 0; k < b->count; ++k) {
     const DevInst &d = b->inst[k];
     const int strips = (d.Lx + TX - 1) / TX;
-    const int nseg = std::max(1, (d.Ly + 63) / 64), ny = (d.Ly + nseg - 1) / nseg;
+    const int nseg = std::max(1, (d.Ly + max_rows - 1) / max_rows), ny = (d.Ly + nseg - 1) / nseg;
     for (int sx = 0; sx < strips; ++sx)
       for (int ys = 0; ys < d.Ly; ys += ny) fi.push_back(make_int4(k, sx, ys, std::min(ny, d.Ly - ys)));
   }
+  // longest segments first: the CTAs are dispatched in item order
+  std::stable_sort(fi.begin(), fi.end(), [](const int4 &p, const int4 &q) { return p.w > q.w; });
   auto upload = [&](auto **dst, const auto &v) -> int {
     if (v.empty()) return LBM_OK;
     using T = typename std::decay<decltype(v)>::type::value_type;

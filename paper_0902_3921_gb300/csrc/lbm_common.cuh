@@ -23,7 +23,7 @@ namespace hlbm {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 
-bool pdl_enabled();  // HLBM_PDL=0 turns it off (read once)
+bool pdl_enabled();  // HLBM_PDL=1 turns it on (read once; off by default)
 
 // launch_pdl, or a plain launch when pdl is false (the kernel's PDL calls are
 // then no-ops)
