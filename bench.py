@@ -631,8 +631,9 @@ def batched_form(steps, local, rank, stream):
 
 def run_batched(args, rank, world, local):
     """512 independent drops (sides 32..256, half pushed by g_x = 1e-5 for the
-    first 2000 of 6000 steps) in one persistent launch per call, against 512
-    plain lattices stepped one launch sequence each, same GPU, FP32."""
+    first 2000 of 6000 steps) advanced together on the path the library chose
+    (persistent kernel or tiled launches, in a graph), against 512 plain
+    lattices stepped one launch sequence each, same GPU, FP32."""
     import torch
     from paper_0902_3921_gb300 import build as B
     from paper_0902_3921_gb300 import inputs as I
