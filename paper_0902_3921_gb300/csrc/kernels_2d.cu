@@ -964,12 +964,21 @@ __global__ void __launch_bounds__(NW * 32, 1)
   for (int j = 0; j < 4; ++j) gx[j] = wrapi(x0 + c + j, Lx);
   pdl_wait();  // u*(t) comes from the previous kernel
   pdl_trigger();
+  // a lane's four columns are one aligned float4 of the lattice when the
+  // region origin and Lx are multiples of 4 (then they never straddle the wrap)
+  const bool vec = H % 4 == 0 && (Lx & 3) == 0;
   // 1. phi -> sp, u -> sa, v -> sq (the latter two only until the
   //    coefficients are in registers)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int r = warp * K + k;
     const long long row = (long long)wrapi(y0 + r, Ly) * Lx;
+    if (vec) {
+      st4(sp, r, c, __ldg(reinterpret_cast<const float4 *>(phi_in + row + gx[0])));
+      st4(sa, r, c, __ldg(reinterpret_cast<const float4 *>(u + row + gx[0])));
+      st4(sq, r, c, __ldg(reinterpret_cast<const float4 *>(u + Sz + row + gx[0])));
+      continue;
+    }
     float e[4], f[4], g[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1111,10 +1120,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
             st4(pout, r, c, mk4(e));
           } else if (r >= H && r < H + TY && y0 + r < Ly) {
             const long long row = (long long)(y0 + r) * Lx;
+            if (vec) {  // the group is wholly inside or outside the written range
+              if (c >= H && c < H + TX && x0 + c < Lx)
+                *reinterpret_cast<float4 *>(phi_out + row + x0 + c) = mk4(e);
+            } else {
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int cc = c + jj, xg = x0 + cc;
-              if (cc >= H && cc < H + TX && xg < Lx) phi_out[row + xg] = e[jj];
+              for (int jj = 0; jj < 4; ++jj) {
+                const int cc = c + jj, xg = x0 + cc;
+                if (cc >= H && cc < H + TX && xg < Lx) phi_out[row + xg] = e[jj];
+              }
             }
           }
         }
