@@ -962,33 +962,38 @@ __global__ void __launch_bounds__(NW * 32, 1)
   int gx[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) gx[j] = wrapi(x0 + c + j, Lx);
-  pdl_wait();  // u*(t) comes from the previous kernel
-  pdl_trigger();
   // a lane's four columns are one aligned float4 of the lattice when the
   // region origin and Lx are multiples of 4 (then they never straddle the wrap)
   const bool vec = H % 4 == 0 && (Lx & 3) == 0;
   // 1. phi -> sp, u -> sa, v -> sq (the latter two only until the
   //    coefficients are in registers)
+  // (all rows are loaded into registers before any is stored, so that the
+  // loads are in flight together)
+  long long rowo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) rowo[k] = (long long)wrapi(y0 + warp * K + k, Ly) * Lx;
+  auto ldrow = [&](const float *f, int k) {
+    if (vec) return __ldg(reinterpret_cast<const float4 *>(f + rowo[k] + gx[0]));
+    float e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) e[j] = __ldg(f + rowo[k] + gx[j]);
+    return mk4(e);
+  };
+  float4 rp[K], ru[K], rv[K];
+  pdl_wait();  // u*(t) comes from the previous kernel
+  pdl_trigger();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    rp[k] = ldrow(phi_in, k);
+    ru[k] = ldrow(u, k);
+    rv[k] = ldrow(u + Sz, k);
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int r = warp * K + k;
-    const long long row = (long long)wrapi(y0 + r, Ly) * Lx;
-    if (vec) {
-      st4(sp, r, c, __ldg(reinterpret_cast<const float4 *>(phi_in + row + gx[0])));
-      st4(sa, r, c, __ldg(reinterpret_cast<const float4 *>(u + row + gx[0])));
-      st4(sq, r, c, __ldg(reinterpret_cast<const float4 *>(u + Sz + row + gx[0])));
-      continue;
-    }
-    float e[4], f[4], g[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      e[j] = __ldg(phi_in + row + gx[j]);
-      f[j] = __ldg(u + row + gx[j]);
-      g[j] = __ldg(u + Sz + row + gx[j]);
-    }
-    st4(sp, r, c, mk4(e));
-    st4(sa, r, c, mk4(f));
-    st4(sq, r, c, mk4(g));
+    st4(sp, r, c, rp[k]);
+    st4(sa, r, c, ru[k]);
+    st4(sq, r, c, rv[k]);
   }
   __syncthreads();
   // 2. advection coefficients (printed form: c0, dt u, dt v; flux form: the
