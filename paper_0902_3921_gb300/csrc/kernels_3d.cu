@@ -86,11 +86,14 @@ __global__ void __launch_bounds__(256, MINB)
     const int gx = big ? wrap1_3(x0 + rx - 2, Lx) : wrapi(x0 + rx - 2, Lx);
     const int gy = big ? wrap1_3(y0 + ry - 2, Ly) : wrapi(y0 + ry - 2, Ly);
     const C *col = phi + (long long)gy * Lx + gx;
-#pragma unroll 4
+    C v[PZ];  // the whole column in flight before any of it is stored
+#pragma unroll
     for (int rz = 0; rz < PZ; ++rz) {
       const int gz = big ? wrap1_3(z0 + rz - 2, Lz) : wrapi(z0 + rz - 2, Lz);
-      sphi[rz][ry][rx] = col[(long long)gz * pl];
+      v[rz] = col[(long long)gz * pl];
     }
+#pragma unroll
+    for (int rz = 0; rz < PZ; ++rz) sphi[rz][ry][rx] = v[rz];
   }
   __syncthreads();
   // mu on the tile + 1: one (x, y) column per thread marching in z, the 3 x 3
