@@ -213,32 +213,62 @@ __global__ void __launch_bounds__(256, MINB)
     }
     return;
   }
-  // 2. periodic images of the cells the copies left as zeros (edge CTAs only)
-  if (x0 == 0 || y0 == 0 || x0 + TT + 2 > Lx || y0 + TT + 2 > Ly) {
-    for (int k = tid; k < (TT + 4) * (TT + 4); k += 256) {  // phi: rows y0-2 .., columns x0-2 ..
-      const int ry = k / (TT + 4), rx = k - ry * (TT + 4);
-      const int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-      if (gx < 0 || gx >= Lx || gy < 0 || gy >= Ly)
-        sphi[ry][rx + 2] = phi[(long long)wrapi(gy, Ly) * Lx + wrapi(gx, Lx)];
-    }
-    // populations: the pulls from outside the lattice start at the first or
-    // last column or row
-    for (int k = tid; k < 8 * 2 * TT; k += 256) {
-      const int i = 1 + k / (2 * TT), j = k % (2 * TT);
-      const int ex = q9_ex(i), ey = q9_ey(i);
-      int xs, ys;
-      if (j < TT) {
-        if (ex == 0) continue;
-        xs = ex > 0 ? 0 : Lx - 1;
-        ys = y0 + j;
-      } else {
-        if (ey == 0) continue;
-        ys = ey > 0 ? 0 : Ly - 1;
-        xs = x0 + j - TT;
+  // 2. periodic images of the cells the copies left as zeros (edge CTAs only;
+  //    Lx, Ly >= 64, so one conditional wrap suffices).  phi: only the cells
+  //    of the 36 x 36 box beyond the lattice are visited (the column strips,
+  //    then the row strips between them); populations: the pulls from outside
+  //    the lattice start at the first or last column or row.  Each thread's
+  //    loads are issued together before any is stored.
+  {
+    const int rxr = Lx - x0 + 2, ryb = Ly - y0 + 2;  // first box column / row beyond the lattice
+    const int wl = x0 == 0 ? 2 : 0, wr = max(0, TT + 4 - rxr), ht = y0 == 0 ? 2 : 0, hb = max(0, TT + 4 - ryb);
+    if (wl + wr + ht + hb > 0) {
+      const int ncol = (TT + 4) * (wl + wr), wc = TT + 4 - wl - wr, ntot = ncol + (ht + hb) * wc;
+      for (int q0 = 0; q0 < ntot; q0 += 256) {
+        const int q = q0 + tid;
+        float v = 0.f;
+        int rx = 0, ry = 0;
+        if (q < ntot) {
+          if (q < ncol) {
+            const int c = q / (TT + 4);
+            ry = q - c * (TT + 4);
+            rx = c < wl ? c : rxr + (c - wl);
+          } else {
+            const int q2 = q - ncol, r = q2 / wc;
+            rx = wl + (q2 - r * wc);
+            ry = r < ht ? r : ryb + (r - ht);
+          }
+          v = phi[(long long)wrap1(y0 - 2 + ry, Ly) * Lx + wrap1(x0 - 2 + rx, Lx)];
+        }
+        S pv[2];
+        int pd[2];
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          pd[sl] = -1;
+          const int k = tid + 256 * sl;
+          if (q0 != 0 || k >= 8 * 2 * TT) continue;  // the populations go with the first round
+          const int i = 1 + k / (2 * TT), j = k % (2 * TT);
+          const int ex = q9_ex(i), ey = q9_ey(i);
+          int xs, ys;
+          if (j < TT) {
+            if (ex == 0) continue;
+            xs = ex > 0 ? 0 : Lx - 1;
+            ys = y0 + j;
+          } else {
+            if (ey == 0) continue;
+            ys = ey > 0 ? 0 : Ly - 1;
+            xs = x0 + j - TT;
+          }
+          if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + TT || ys >= Ly) continue;
+          const int sx = wrap1(xs - ex, Lx), sy = wrap1(ys - ey, Ly);
+          pd[sl] = G::off(i) + (ys - y0) * G::w(i) + (xs - x0) + G::col(i);
+          pv[sl] = hin[i * Sz + (long long)sy * Lx + sx];
+        }
+        if (q < ntot) sphi[ry][rx + 2] = v;
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl)
+          if (pd[sl] >= 0) pops[pd[sl]] = pv[sl];
       }
-      if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + TT || ys >= Ly) continue;
-      const int sx = wrapi(xs - ex, Lx), sy = wrapi(ys - ey, Ly);
-      pops[G::off(i) + (ys - y0) * G::w(i) + (xs - x0) + G::col(i)] = hin[i * Sz + (long long)sy * Lx + sx];
     }
   }
   __syncthreads();

@@ -59,14 +59,16 @@ def test_phi_box_covers_the_halo():
     assert -2 + PHH - 1 == TT + 1
 
 
-# ---- the edge fixups of the pipelined kernels (32 x 16 tiles) ---------------------------
-PY, PPHH = 16, 20
+# ---- the edge fixups of the TMA collide kernels -----------------------------------------
+# (the pipelined kernels' 32 x 16 tiles, loaded into at most 3 + 2 register slots per
+# thread before the copy wait; the one-tile kernels' 32 x 32 tiles, after it)
 
 
-def phi_fix_cells(Lx, Ly, x0, y0):
-    """The phi box cells (rx, ry) of tile (x0, y0) that pipe_fix_load loads,
-    in its order: the column strips (all PPHH rows), then the row strips
+def phi_fix_cells(Lx, Ly, x0, y0, PY=16):
+    """The phi box cells (rx, ry) of tile (x0, y0) that the edge fixup loads,
+    in its order: the column strips (all PY + 4 rows), then the row strips
     between them."""
+    PPHH = PY + 4
     rxr, ryb = Lx - x0 + 2, Ly - y0 + 2
     wl, wr = (2 if x0 == 0 else 0), max(0, TT + 4 - rxr)
     ht, hb = (2 if y0 == 0 else 0), max(0, PPHH - ryb)
@@ -74,7 +76,8 @@ def phi_fix_cells(Lx, Ly, x0, y0):
         return []
     ncol, wc = PPHH * (wl + wr), TT + 4 - wl - wr
     ntot = ncol + (ht + hb) * wc
-    assert ntot <= 3 * 256  # three slots per thread
+    if PY == 16:
+        assert ntot <= 3 * 256  # three slots per thread
     out = []
     for q in range(ntot):
         if q < ncol:
@@ -87,9 +90,9 @@ def phi_fix_cells(Lx, Ly, x0, y0):
     return out
 
 
-def pop_fix_cells(Lx, Ly, x0, y0):
+def pop_fix_cells(Lx, Ly, x0, y0, PY=16):
     """(i, xs, ys) of the populations pulled across the lattice's edges that
-    pipe_fix_load loads (8 planes x (PY + TT) candidates, two slots)."""
+    the edge fixup loads (8 planes x (PY + TT) candidates, two slots)."""
     out = []
     for q in range(8 * (PY + TT)):
         assert q < 2 * 256
@@ -109,15 +112,17 @@ def pop_fix_cells(Lx, Ly, x0, y0):
     return out
 
 
+@pytest.mark.parametrize("PY", [16, 32])
 @pytest.mark.parametrize("Lx,Ly", [(64, 64), (68, 80), (100, 64), (128, 132), (96, 200), (260, 68)])
-def test_edge_fixups_cover_exactly_the_cells_the_copies_zero(Lx, Ly):
+def test_edge_fixups_cover_exactly_the_cells_the_copies_zero(Lx, Ly, PY):
     """Every phi cell of a tile's 36 x 20 box outside the lattice is loaded
     exactly once (and no inside cell), its periodic image within one
     conditional wrap; every population of the tile whose pull buf_i(r - e_i)
     crosses an edge is loaded, and no other."""
+    PPHH = PY + 4
     for y0 in range(0, Ly, PY):
         for x0 in range(0, Lx, TT):
-            cells = phi_fix_cells(Lx, Ly, x0, y0)
+            cells = phi_fix_cells(Lx, Ly, x0, y0, PY)
             assert len(cells) == len(set(cells))
             outside = {(rx, ry) for ry in range(PPHH) for rx in range(TT + 4)
                        if not (0 <= x0 - 2 + rx < Lx and 0 <= y0 - 2 + ry < Ly)}
@@ -133,4 +138,4 @@ def test_edge_fixups_cover_exactly_the_cells_the_copies_zero(Lx, Ly):
                         sx, sy = xs - E[i][0], ys - E[i][1]
                         if not (0 <= sx < Lx and 0 <= sy < Ly):
                             crossing.add((i, xs, ys))
-            assert set(pop_fix_cells(Lx, Ly, x0, y0)) == crossing, (x0, y0)
+            assert set(pop_fix_cells(Lx, Ly, x0, y0, PY)) == crossing, (x0, y0)
