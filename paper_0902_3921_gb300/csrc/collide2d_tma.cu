@@ -203,6 +203,60 @@ __global__ void __launch_bounds__(256, MINB)
       spn[ry][rx] = p.cs2mT * (1.f + dn[(long long)gy * Lx + gx]);
     }
   }
+  // 2. periodic images of the cells the copies left as zeros (edge CTAs only;
+  //    Lx, Ly >= 64, so one conditional wrap suffices).  phi: only the cells
+  //    of the 36 x 36 box beyond the lattice are visited (the column strips,
+  //    then the row strips between them); populations: the pulls from outside
+  //    the lattice start at the first or last column or row.  The first
+  //    round of loads (one phi cell and two population candidates a thread)
+  //    is issued before the wait for the copies, so that it overlaps them.
+  const int rxr = Lx - x0 + 2, ryb = Ly - y0 + 2;  // first box column / row beyond the lattice
+  const int wl = x0 == 0 ? 2 : 0, wr = max(0, TT + 4 - rxr), ht = y0 == 0 ? 2 : 0, hb = max(0, TT + 4 - ryb);
+  const bool edge = wl + wr + ht + hb > 0;
+  const int ncol = (TT + 4) * (wl + wr), wc = TT + 4 - wl - wr, ntot = ncol + (ht + hb) * wc;
+  // phi cell q of the box: its place in sphi (row-major, PHW floats a row) and its value
+  auto phi_cell = [&](int q, float &v) {
+    int rx, ry;
+    if (q < ncol) {
+      const int c = q / (TT + 4);
+      ry = q - c * (TT + 4);
+      rx = c < wl ? c : rxr + (c - wl);
+    } else {
+      const int q2 = q - ncol, r = q2 / wc;
+      rx = wl + (q2 - r * wc);
+      ry = r < ht ? r : ryb + (r - ht);
+    }
+    v = phi[(long long)wrap1(y0 - 2 + ry, Ly) * Lx + wrap1(x0 - 2 + rx, Lx)];
+    return ry * PHW + rx + 2;
+  };
+  float pv0 = 0.f;
+  int pd0 = -1;
+  S hv2[2];
+  int hd2[2] = {-1, -1};
+  if (edge) {
+    if (tid < ntot) pd0 = phi_cell(tid, pv0);
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      const int k = tid + 256 * sl;
+      if (k >= 8 * 2 * TT) continue;
+      const int i = 1 + k / (2 * TT), j = k % (2 * TT);
+      const int ex = q9_ex(i), ey = q9_ey(i);
+      int xs, ys;
+      if (j < TT) {
+        if (ex == 0) continue;
+        xs = ex > 0 ? 0 : Lx - 1;
+        ys = y0 + j;
+      } else {
+        if (ey == 0) continue;
+        ys = ey > 0 ? 0 : Ly - 1;
+        xs = x0 + j - TT;
+      }
+      if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + TT || ys >= Ly) continue;
+      const int sx = wrap1(xs - ex, Lx), sy = wrap1(ys - ey, Ly);
+      hd2[sl] = G::off(i) + (ys - y0) * G::w(i) + (xs - x0) + G::col(i);
+      hv2[sl] = hin[i * Sz + (long long)sy * Lx + sx];
+    }
+  }
   const bool arrived = bar_wait(bar, 0, g_collide_tma_wait_ns);
   if (!__syncthreads_and(arrived)) {
     // the copies did not complete within the wait bound: report, let them land
@@ -213,62 +267,16 @@ __global__ void __launch_bounds__(256, MINB)
     }
     return;
   }
-  // 2. periodic images of the cells the copies left as zeros (edge CTAs only;
-  //    Lx, Ly >= 64, so one conditional wrap suffices).  phi: only the cells
-  //    of the 36 x 36 box beyond the lattice are visited (the column strips,
-  //    then the row strips between them); populations: the pulls from outside
-  //    the lattice start at the first or last column or row.  Each thread's
-  //    loads are issued together before any is stored.
-  {
-    const int rxr = Lx - x0 + 2, ryb = Ly - y0 + 2;  // first box column / row beyond the lattice
-    const int wl = x0 == 0 ? 2 : 0, wr = max(0, TT + 4 - rxr), ht = y0 == 0 ? 2 : 0, hb = max(0, TT + 4 - ryb);
-    if (wl + wr + ht + hb > 0) {
-      const int ncol = (TT + 4) * (wl + wr), wc = TT + 4 - wl - wr, ntot = ncol + (ht + hb) * wc;
-      for (int q0 = 0; q0 < ntot; q0 += 256) {
-        const int q = q0 + tid;
-        float v = 0.f;
-        int rx = 0, ry = 0;
-        if (q < ntot) {
-          if (q < ncol) {
-            const int c = q / (TT + 4);
-            ry = q - c * (TT + 4);
-            rx = c < wl ? c : rxr + (c - wl);
-          } else {
-            const int q2 = q - ncol, r = q2 / wc;
-            rx = wl + (q2 - r * wc);
-            ry = r < ht ? r : ryb + (r - ht);
-          }
-          v = phi[(long long)wrap1(y0 - 2 + ry, Ly) * Lx + wrap1(x0 - 2 + rx, Lx)];
-        }
-        S pv[2];
-        int pd[2];
+  if (edge) {
+    float *sphi_flat = &sphi[0][0];
+    if (pd0 >= 0) sphi_flat[pd0] = pv0;
 #pragma unroll
-        for (int sl = 0; sl < 2; ++sl) {
-          pd[sl] = -1;
-          const int k = tid + 256 * sl;
-          if (q0 != 0 || k >= 8 * 2 * TT) continue;  // the populations go with the first round
-          const int i = 1 + k / (2 * TT), j = k % (2 * TT);
-          const int ex = q9_ex(i), ey = q9_ey(i);
-          int xs, ys;
-          if (j < TT) {
-            if (ex == 0) continue;
-            xs = ex > 0 ? 0 : Lx - 1;
-            ys = y0 + j;
-          } else {
-            if (ey == 0) continue;
-            ys = ey > 0 ? 0 : Ly - 1;
-            xs = x0 + j - TT;
-          }
-          if (xs < x0 || xs >= x0 + TT || xs >= Lx || ys < y0 || ys >= y0 + TT || ys >= Ly) continue;
-          const int sx = wrap1(xs - ex, Lx), sy = wrap1(ys - ey, Ly);
-          pd[sl] = G::off(i) + (ys - y0) * G::w(i) + (xs - x0) + G::col(i);
-          pv[sl] = hin[i * Sz + (long long)sy * Lx + sx];
-        }
-        if (q < ntot) sphi[ry][rx + 2] = v;
-#pragma unroll
-        for (int sl = 0; sl < 2; ++sl)
-          if (pd[sl] >= 0) pops[pd[sl]] = pv[sl];
-      }
+    for (int sl = 0; sl < 2; ++sl)
+      if (hd2[sl] >= 0) pops[hd2[sl]] = hv2[sl];
+    for (int q = 256 + tid; q < ntot; q += 256) {  // ragged tiles: the rest of the phi cells
+      float v;
+      const int d = phi_cell(q, v);
+      sphi_flat[d] = v;
     }
   }
   __syncthreads();
