@@ -965,8 +965,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
   // a lane's four columns are one aligned float4 of the lattice when the
   // region origin and Lx are multiples of 4 (then they never straddle the wrap)
   const bool vec = H % 4 == 0 && (Lx & 3) == 0;
-  // 1. phi -> sp, u -> sa, v -> sq (the latter two only until the
-  //    coefficients are in registers)
+  // 1. phi -> sp, v -> sq (only until the coefficients are in registers);
+  //    u stays in registers in the printed form (a thread needs only its own
+  //    rows of it), the flux form (more coefficients) stores it to sa
   // (all rows are loaded into registers before any is stored, so that the
   // loads are in flight together)
   long long rowo[K];
@@ -992,7 +993,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
   for (int k = 0; k < K; ++k) {
     const int r = warp * K + k;
     st4(sp, r, c, rp[k]);
-    st4(sa, r, c, ru[k]);
+    if constexpr (FLUX) st4(sa, r, c, ru[k]);
     st4(sq, r, c, rv[k]);
   }
   __syncthreads();
@@ -1005,7 +1006,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
   for (int k = 0; k < K; ++k) {
     const int r = warp * K + k;
     const int rm = r > 0 ? r - 1 : r, rp = r < RY - 1 ? r + 1 : r;  // row 0 / RY-1: never valid
-    const float4 uc = ld4(sa, r, c), vc = ld4(sq, r, c), vm = ld4(sq, rm, c), vp = ld4(sq, rp, c);
+    const float4 uc = FLUX ? ld4(sa, r, c) : ru[k], vc = ld4(sq, r, c), vm = ld4(sq, rm, c), vp = ld4(sq, rp, c);
     const float uL0 = __shfl_up_sync(FULL, uc.w, 1), uR3 = __shfl_down_sync(FULL, uc.x, 1);
     float c0[4];
 #pragma unroll
@@ -1026,7 +1027,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
     }
     if constexpr (!FLUX) st4(st0, r, c, mk4(c0));
   }
-  __syncthreads();
+  // printed form: no barrier here (the first advection sweep reads the phi
+  // plane stored before the last one and this thread's own c0, and writes
+  // sa, which no thread reads until the barrier after it; sq, read above, is
+  // first overwritten after that barrier too); the flux form read sa above
+  if constexpr (FLUX) __syncthreads();
   // 3. SUB substeps of Eqs. 32-36.  sweep(in, lo, fn) runs one stencil phase
   //    over this warp's K consecutive rows r (lo <= r < RY - lo, a
   //    warp-uniform test): fn(k, r, row r - 1, row r, row r + 1 of plane
