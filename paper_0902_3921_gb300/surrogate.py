@@ -140,8 +140,11 @@ def train(side=512, lattices=8, generations=2, iters=200, window=50, t_start=200
 
 def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 16000),
              window=50, mass_tol=2e-3, phi_clamp=0.0, relax=0, log=None, late_net=None, late_from=None,
-             control=False):
+             control=False, conserve_mass=True):
     """late_net (optional) replaces net for the windows from t = late_from on.
+    conserve_mass: accepted predictions are shifted to keep the sum of phi
+    (off: the prediction's own change of the sum is kept, as the plain
+    scheme's printed advection form does not conserve it exactly).
     control: a third lattice, the plain scheme re-initialised from its own n,
     phi, u* at t_start (populations rebuilt at equilibrium, the reconstruction
     every accepted surrogate window makes) and then advanced by the plain
@@ -177,7 +180,7 @@ def evaluate(net, side=2048, seed=1000, t_start=2000, checkpoints=(4000, 8000, 1
         with torch.cuda.stream(stream):
             ev[2].record(stream)
             nwin = dt // (window + relax)
-            fb = lbm.lbm_surrogate_advance(surr.handle, use, nwin, window, mass_tol, True,
+            fb = lbm.lbm_surrogate_advance(surr.handle, use, nwin, window, mass_tol, conserve_mass,
                                            phi_clamp, relax_steps=relax)
             if dt - nwin * (window + relax):
                 surr.step(dt - nwin * (window + relax))
@@ -255,6 +258,8 @@ def main():
     ap.add_argument("--control", action="store_true",
                     help="also run the plain scheme re-initialised from its own moments at the start")
     ap.add_argument("--load", default=None, help="evaluate parameters written by --save")
+    ap.add_argument("--no-conserve-mass", action="store_true",
+                    help="keep the prediction's own change of the sum of phi")
     args = ap.parse_args()
     if args.load:
         net = load_net(args.load)
@@ -274,7 +279,8 @@ def main():
     res = evaluate(net, args.eval_side, checkpoints=tuple(int(c) for c in args.checkpoints.split(",")),
                    window=args.window, mass_tol=args.mass_tol, phi_clamp=args.phi_clamp,
                    relax=args.relax, log=lambda m: print(m, flush=True), late_net=late,
-                   late_from=args.late_from if late is not None else None, control=args.control)
+                   late_from=args.late_from if late is not None else None, control=args.control,
+                   conserve_mass=not args.no_conserve_mass)
     print(json.dumps({"training": hist, "evaluation": res, "window": args.window, "relax": args.relax}),
           flush=True)
 
