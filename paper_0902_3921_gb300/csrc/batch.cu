@@ -1,7 +1,8 @@
 // batch.cu -- many independent 2D lattices (uneven sizes, per-instance body
-// force schedules) advanced by one persistent launch.
+// force schedules) advanced together: by one persistent launch, or on the
+// tiled path described below.
 //
-// Every instance is owned by exactly one CTA (instances are assigned to CTAs
+// Persistent path: every instance is owned by exactly one CTA (instances are assigned to CTAs
 // longest-first on the host), and a CTA advances each of its instances
 // through all requested LB steps before it moves to the next one, so CTAs
 // never wait for one another: the only synchronisation is __syncthreads
@@ -865,7 +866,7 @@ int lbm_batch_step(lbm_batch *b, long long nsteps) {
   if (!b->use_graphs) {
     BCK(b, launch_batch(b, b->t, (int)nsteps), "batch kernel");
   } else {
-    // one persistent launch per call, captured once per (t0, nsteps) pair
+    // the call's launches captured once per (t0, nsteps) pair
     if (b->graph == nullptr || b->graph_steps != nsteps || b->graph_t0 != b->t) {
       if (b->graph) cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;

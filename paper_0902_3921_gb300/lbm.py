@@ -465,9 +465,10 @@ class Lattice:
 
 
 class Batch:
-    """Owning wrapper around one lbm_batch: independent 2D lattices advanced by
-    one persistent launch.  `instances` is a list of (Lx, Ly, (gx, gy),
-    force_steps)."""
+    """Owning wrapper around one lbm_batch: independent 2D lattices advanced
+    together (one persistent launch per call, or the tiled path's launches per
+    LB step; the library picks the faster at creation).  `instances` is a list
+    of (Lx, Ly, (gx, gy), force_steps)."""
 
     def __init__(self, common: LbmParams, instances, stream: int | None = None):
         lib = load_library()
