@@ -1052,7 +1052,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
   // never reaches shared memory)
   float *pin = sp, *pout = sq;
   auto clampr = [](int r) { return r < 0 ? 0 : (r > RY - 1 ? RY - 1 : r); };
-#pragma unroll 1
+#pragma unroll
   for (int s = 0; s < SUB; ++s) {
     // phih = advected phi (Eqs. 32-35)
     sweep(pin, 3 * s + 1, [&](int k, int r, const float4 &pu, const float4 &pc, const float4 &pd) {
