@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(256, MINB)
     const float A0 = om * float(q9_w(0)), B0 = p.pref * float(q9_w(0));
     const float A1 = om * float(q9_w(1)), B1 = p.pref * float(q9_w(1));
     const float A2 = om * float(q9_w(5)), B2 = p.pref * float(q9_w(5));
-#pragma unroll 1
+#pragma unroll
     for (int r = 0; r < TR; r += 2) {
       const int lya = ly0 + r, ya = y0 + lya;
       float2 Fx, Fy;
