@@ -53,7 +53,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (consecutive rows per warp, psi fused), and the TMA collide kernel with the
 # packed-pair collision (launch-shape variant 5).  ncu flushes the caches
 # before a captured launch: these are cold-cache figures.
-NCU_TRAFFIC_1024 = {"fd": ((128, 96, 4, 2), 12.628224e6), "collide": (5, 41.973248e6 + 2.389248e6)}
+NCU_TRAFFIC_1024 = {"fd": ((128, 96, 4, 2), 12.648448e6), "collide": (5, 41.977856e6 + 2.784768e6)}
 # the same collide kernel (variant 5) captured on 2048^2 (4.19 M sites; the
 # lattice no longer fits L2): 168.389120 MB read + 129.996032 MB written per
 # launch = 71.2 B/site; the 4096^2 line scales it by the site count
@@ -333,8 +333,8 @@ def run_ours(args, rank, world, local):
     fd_note = ("counts the useful flops only (164 a site and LB step); the kernel is bound by the "
                "shared-memory pipe and issue latency, not the FP32 units")
     if traffic_fd is not None:
-        fd_note += (": ncu of this launch shape at 1024^2 shows 59 % L1/shared-memory throughput, "
-                    "46 % of cycles issuing and 8.01 M warp instructions a launch (0.35 of the "
+        fd_note += (": ncu of this launch shape at 1024^2 shows 60 % L1/shared-memory throughput, "
+                    "44 % of cycles issuing and 6.78 M warp instructions a launch (0.34 of the "
                     "issue rate over its duration), with 12 B/site of DRAM traffic")
     roof_fd = {"bound": "alu", "achieved": fd_tflops, "peak": FP32_PEAK_TFLOPS, "note": fd_note,
                "unit": "TFLOP/s", "frac": fd_tflops / FP32_PEAK_TFLOPS, "traffic": traffic_fd,
