@@ -130,7 +130,13 @@ typedef struct lbm_handle lbm_handle;
  *                      keeps the 0.5 s bound), skips the tile, and the
  *                      handle reports LBM_ETIMEOUT at the next lbm_moments,
  *                      lbm_diagnostics or lbm_synchronize.  The handle can
- *                      then only be freed. */
+ *                      then only be freed.
+ * Launch choices (environment, read at creation or once per process):
+ *   HLBM_TUNING=sub,rows,cols,collide_rows[,tile]  fixed 2D launch shapes
+ *                      instead of the autotuner's timed choice (lbm_tuning
+ *                      reports either); HLBM_TUNE_VERBOSE=1 prints the timings;
+ *   HLBM_PDL=1         programmatic dependent launches between the step's
+ *                      kernels (off by default: slower on the GB300). */
 int lbm_create(const lbm_params *params, void *cuda_stream, lbm_handle **out);
 
 /* Device buffers a caller (for example a PyTorch program) allocates and lends
@@ -246,7 +252,8 @@ int lbm_load(lbm_handle *h, const char *path);
  *     maps per instance shape, for the instances at least 64 on a side
  *     (HLBM_BATCH_NO_TMA=1 sends them to the tile kernel too), the tile
  *     kernel for the rest -- and m / 2 launches of the two-substep wavefront
- *     FD kernel over their 128-column strips.
+ *     FD kernel over their 128-column strips, in segments of at most 48 rows
+ *     (HLBM_BATCH_FD_ROWS=n changes the 48).
  * Where the tiled path is eligible both are timed and the faster kept
  * (HLBM_BATCH_PATH=tiled|persistent fixes the choice; HLBM_TUNE_VERBOSE=1
  * prints the timings).  Either is captured in a CUDA graph per call.  Every
