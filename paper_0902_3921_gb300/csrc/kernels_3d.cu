@@ -51,10 +51,17 @@ __global__ void __launch_bounds__(256, MINB)
   const long long yc = (long long)yc_ * Lx, ymo = (long long)ym * Lx, ypo = (long long)yp * Lx;
   // f_i(r) = buf_i(r - e_i) of plane z (clamped into the lattice for threads
   // without a site; their values are never used)
+  // FP16 storage: the populations stay in their stored scale 2^s through the
+  // sums and the collision (the scale is folded into the moments and the
+  // weights), which is exact for a power of two and saves a multiply per
+  // population read and written
+  constexpr bool FOLD = !std::is_same<S, C>::value;
+  const C ld_scale = FOLD ? C(1) : p.inv_scale, st_scale = FOLD ? C(1) : p.scale;
+  const C wsc = FOLD ? p.scale : C(1);  // weights in the stored scale
   auto load_plane = [&](C (&hv)[19], int z) {
     const int zm = z == 0 ? Lz - 1 : z - 1, zp = z == Lz - 1 ? 0 : z + 1;
     const long long zc = (long long)z * pl, zmo = (long long)zm * pl, zpo = (long long)zp * pl;
-#define LD(i, zz, yy, xx) hv[i] = Store<S, C>::ld(hin + (i)*Sz + (zz) + (yy) + (xx), p.inv_scale)
+#define LD(i, zz, yy, xx) hv[i] = Store<S, C>::ld(hin + (i)*Sz + (zz) + (yy) + (xx), ld_scale)
     LD(0, zc, yc, xc);
     LD(1, zc, yc, xm);
     LD(2, zc, yc, xp);
@@ -190,6 +197,12 @@ __global__ void __launch_bounds__(256, MINB)
       if (q19_ez(i) > 0) jz += hv[i];
       if (q19_ez(i) < 0) jz -= hv[i];
     }
+    if constexpr (FOLD) {
+      dens *= p.inv_scale;
+      jx *= p.inv_scale;
+      jy *= p.inv_scale;
+      jz *= p.inv_scale;
+    }
     const C n = C(1) + dens;
     Fx += n * p.gx;
     Fy += n * p.gy;
@@ -218,21 +231,21 @@ __global__ void __launch_bounds__(256, MINB)
     const C n3 = C(3) * n, n45 = C(4.5) * n;
     const C pF3 = C(3) * p.pref, pF9 = C(9) * p.pref, puF = C(3) * p.pref * uF;
     {
-      const C w = C(q19_w(0));
-      Store<S, C>::st(hout + s, keep * hv[0] + om * (w * base) + w * (-puF), p.scale);
+      const C w = C(q19_w(0)) * wsc;
+      Store<S, C>::st(hout + s, keep * hv[0] + om * (w * base) + w * (-puF), st_scale);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const int i = 2 * k + 1, ib = i + 1;  // e_ib = -e_i
-      const C w = C(q19_w(i));
+      const C w = C(q19_w(i)) * wsc;
       const C eu = C(q19_ex(i)) * ux + C(q19_ey(i)) * uy + C(q19_ez(i)) * uz;
       const C eF = C(q19_ex(i)) * Fx + C(q19_ey(i)) * Fy + C(q19_ez(i)) * Fz;
       const C even = w * (base + n45 * eu * eu);
       const C odd = w * (n3 * eu);
       const C Feven = w * (pF9 * eu * eF - puF);
       const C Fodd = w * (pF3 * eF);
-      Store<S, C>::st(hout + i * Sz + s, keep * hv[i] + om * (even + odd) + (Feven + Fodd), p.scale);
-      Store<S, C>::st(hout + ib * Sz + s, keep * hv[ib] + om * (even - odd) + (Feven - Fodd), p.scale);
+      Store<S, C>::st(hout + i * Sz + s, keep * hv[i] + om * (even + odd) + (Feven + Fodd), st_scale);
+      Store<S, C>::st(hout + ib * Sz + s, keep * hv[ib] + om * (even - odd) + (Feven - Fodd), st_scale);
     }
     uout[s] = ux;
     uout[Sz + s] = uy;
