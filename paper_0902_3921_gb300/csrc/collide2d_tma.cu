@@ -429,10 +429,18 @@ __global__ void __launch_bounds__(256, MINB)
     }
   } else {
     static_assert(MODE == COLLIDE_STEP, "the packed collision is a step kernel");
+    // FP16 storage: the populations stay in the stored scale 2^s; only the
+    // moments are brought back, and the weights carry the scale, so that the
+    // new populations come out already scaled (power-of-two factors: exact)
+    constexpr bool FOLD = !std::is_same<S, float>::value;
+    const float wsc = FOLD ? p.scale : 1.f;
+    auto popr = [&](int i, int ly) {
+      return FOLD ? float(pops[G::off(i) + ly * G::w(i) + tx + G::col(i)]) : pop(i, ly);
+    };
     // per weight class w: A = w / tau, B = w (1 - 1/2tau) (Eqs. 17, 29)
-    const float A0 = om * float(q9_w(0)), B0 = p.pref * float(q9_w(0));
-    const float A1 = om * float(q9_w(1)), B1 = p.pref * float(q9_w(1));
-    const float A2 = om * float(q9_w(5)), B2 = p.pref * float(q9_w(5));
+    const float A0 = om * float(q9_w(0)) * wsc, B0 = p.pref * float(q9_w(0)) * wsc;
+    const float A1 = om * float(q9_w(1)) * wsc, B1 = p.pref * float(q9_w(1)) * wsc;
+    const float A2 = om * float(q9_w(5)) * wsc, B2 = p.pref * float(q9_w(5)) * wsc;
 #pragma unroll
     for (int r = 0; r < TR; r += 2) {
       const int lya = ly0 + r, ya = y0 + lya;
@@ -443,12 +451,17 @@ __global__ void __launch_bounds__(256, MINB)
       const bool row_b = ya + 1 < Ly;
       float2 h[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) h[i] = make_float2(pop(i, lya), pop(i, lya + 1));
+      for (int i = 0; i < 9; ++i) h[i] = make_float2(popr(i, lya), popr(i, lya + 1));
       float2 dens = h[0];
 #pragma unroll
       for (int i = 1; i < 9; ++i) dens = add2(dens, h[i]);
-      const float2 jx = add2(add2(sub2(h[1], h[3]), sub2(h[5], h[7])), sub2(h[8], h[6]));
-      const float2 jy = add2(add2(sub2(h[2], h[4]), sub2(h[5], h[7])), sub2(h[6], h[8]));
+      float2 jx = add2(add2(sub2(h[1], h[3]), sub2(h[5], h[7])), sub2(h[8], h[6]));
+      float2 jy = add2(add2(sub2(h[2], h[4]), sub2(h[5], h[7])), sub2(h[6], h[8]));
+      if constexpr (FOLD) {
+        dens = mul2(dens, s2(p.inv_scale));
+        jx = mul2(jx, s2(p.inv_scale));
+        jy = mul2(jy, s2(p.inv_scale));
+      }
       const float2 n = add2(s2(1.f), dens);
       Fx = fma2(n, s2(p.gx), Fx);
       Fy = fma2(n, s2(p.gy), Fy);
@@ -483,12 +496,12 @@ __global__ void __launch_bounds__(256, MINB)
       }
       const long long s = (long long)ya * Lx + x;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) cvt_st(hout + i * Sz + s, o[i].x, p.scale);
+      for (int i = 0; i < 9; ++i) cvt_st(hout + i * Sz + s, o[i].x, FOLD ? 1.f : p.scale);
       uout[s] = ux.x;
       uout[Sz + s] = uy.x;
       if (row_b) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) cvt_st(hout + i * Sz + s + Lx, o[i].y, p.scale);
+        for (int i = 0; i < 9; ++i) cvt_st(hout + i * Sz + s + Lx, o[i].y, FOLD ? 1.f : p.scale);
         uout[s + Lx] = ux.y;
         uout[Sz + s + Lx] = uy.y;
       }
