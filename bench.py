@@ -770,7 +770,7 @@ def drop3d_form(side, steps, warmup, local, stream):
         lbm.lbm_set_kernel_timing(lat.handle, False)
         (cms, cn), (fms, fn) = kt["collide"], kt["fd"]
         if S3 in (128, 256) and os.environ.get("HLBM_FD3_FUSED_ADV"):
-            fd_kind = "fd3g (m = 8 substeps, one kernel each: advection, psi and the new phi)"
+            fd_kind = "fd3p (m = 8 substeps, one kernel each: advection, psi and the new phi)"
         elif S3 in (128, 256):
             fd_kind = "fd3d (m = 8 substeps, each an advection pass and a fused psi / new-phi pass)"
         else:

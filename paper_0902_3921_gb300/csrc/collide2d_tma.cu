@@ -92,32 +92,6 @@ __device__ int g_collide_tma_err = 0;
 // keep 0.5 s); the host shortens it only to exercise the give-up path
 __device__ unsigned long long g_collide_tma_wait_ns = 500000000ull;
 
-__device__ __forceinline__ uint32_t su32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Waits for the mbarrier phase `parity` to complete; gives up after limit_ns
-// (at once, without polling, when limit_ns is 0: try_wait itself may block
-// for a while, long enough for the copies to land).
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-  if (limit_ns == 0) return false;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (gtimer() - t0 > limit_ns) return false;
-  }
-}
 __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
                                        uint32_t bar) {
   asm volatile(

@@ -770,35 +770,65 @@ __global__ void __launch_bounds__(F3F_NW * 32, MINB)
   }
 }
 
-// ---- one whole FD substep in one z-marching kernel (Lx = 128 V, V = 1 or 2) ----
-// The advection of Eqs. 32-35 fused with psi and the new phi of Eq. 36: a CTA
-// of F3G_NW warps owns F3G_NW - 4 output rows; warp w owns row y0 - 2 + w,
-// the whole row (V float4 per lane, quad q of lane l at x = 128 q + 4 l; the
-// periodic x neighbours by shuffles), and marches in z.  For plane k every
-// warp advects its row of plane k + 2 (phih, kept in registers for planes
-// k .. k + 2 and copied to a two-plane shared-memory ring for the rows either
-// side); after a barrier warps 1 .. NW - 2 form psi of plane k + 1 into a
-// four-plane ring; after a second barrier warps 2 .. NW - 3 form phi^{n+1} of
-// plane k.  Neither phih nor psi reaches global memory: a substep reads phi
-// and u* and writes the new phi, 20 B/site, against 32 B/site for the
-// advection pass followed by fd3f.  The two barriers per plane make each ring
-// slot's next write come after every read of its previous plane.  Its results
-// equal those of the two-kernel path bitwise, but it is latency-bound (the
-// advection's twelve loads per quad wait within the CTA's barrier phases, and
-// 128 registers leave no room to prefetch them), so it is opt-in
-// (HLBM_FD3_FUSED_ADV).
-constexpr int F3G_NW = 16;
+// ---- one whole FD substep, software-pipelined in z (Lx = 128 V, V = 1 or 2) ----
+// The advection of Eqs. 32-35 fused with psi and the new phi of Eq. 36, with
+// one barrier per plane.  A CTA of F3P_NW warps owns F3P_NW - 4 output rows;
+// warp w owns row y0 - 2 + w, the whole row (V float4 per lane, quad q of
+// lane l at x = 128 q + 4 l; periodic x neighbours by shuffles), and marches
+// in z.  Iteration k runs three phases, each reading only what earlier
+// iterations wrote, so that one barrier at its end orders them all:
+//   C (warps 2 .. NW - 3): phi^{n+1} of plane k - 2 = phih + dt Gamma lap psi,
+//     from psi of planes k - 3 .. k - 1 (three-slot ring; rows w -+ 1 of plane
+//     k - 2) and phih of plane k - 2 (own row);
+//   B (warps 1 .. NW - 2): psi of plane k = a phih + b phi^3 - kappa lap phih,
+//     from phih of planes k - 1 .. k + 1 (four-slot ring; rows w -+ 1 of
+//     plane k) into the psi ring;
+//   A (all warps): phih of plane a = k + 2 into the phih ring.
+// A warp writes only its own row of a ring, and the only same-iteration
+// reuse of a slot is by the writing warp itself (C reads its own phih of
+// plane k - 2 and psi of plane k - 3 before A and B overwrite those slots).
+// The advection inputs arrive one plane ahead: u of the warps' 16 rows and v
+// of 18 rows (y -+ 1) by bulk copies into a two-slot shared-memory ring (one
+// mbarrier a slot; warp 0 issues plane a + 1 at the top of iteration k, after
+// the barrier that ended the reads of its slot), phi and w of the own row in
+// registers marching in z, and phi of rows y -+ 1 and the next planes' own-row
+// phi and w loaded at the end of phase A, so that they are in flight across
+// the barrier and phases C and B.  A substep reads phi and u* and writes the
+// new phi (20 B/site, against 32 B/site for the advection pass followed by
+// fd3f); the arithmetic per site is that of those two kernels (the same
+// device functions and packed operations), so the results are equal bitwise.
+// Every copy wait is bounded: a wait that gives up is reported through the
+// barrier (all threads learn it together), the copies in flight are drained
+// with a bound, and the CTA returns; the host reports LBM_ETIMEOUT.
+constexpr int F3P_NW = 16;
 
-constexpr size_t fd3g_smem_bytes(int V) { return sizeof(float) * 6 * F3G_NW * 128 * V; }
+__device__ int g_fd3p_err = 0;
+__device__ unsigned long long g_fd3p_wait_ns = 500000000ull;
 
-template <bool FLUX, int V, int MINB>
-__global__ void __launch_bounds__(F3G_NW * 32, MINB)
-    fd3g_kernel(const float *__restrict__ G, const float *__restrict__ u, float *__restrict__ out,
+template <int V>
+struct F3P {
+  static constexpr int W = 128 * V;
+  static constexpr int U_OFF = 0;                                // [2][NW][W]     u rows
+  static constexpr int V_OFF = U_OFF + 2 * F3P_NW * W;           // [2][NW + 2][W] v rows
+  static constexpr int H_OFF = V_OFF + 2 * (F3P_NW + 2) * W;     // [4][NW][W]     phih
+  static constexpr int Q_OFF = H_OFF + 4 * F3P_NW * W;           // [3][NW][W]     psi
+  static constexpr int FLOATS = Q_OFF + 3 * F3P_NW * W;
+  static constexpr uint32_t TX_BYTES = (2 * F3P_NW + 2) * W * sizeof(float);  // one plane's copies
+  static constexpr size_t smem = sizeof(float) * FLOATS + 16;    // + two mbarriers
+};
+
+template <bool FLUX, int V>
+__global__ void __launch_bounds__(F3P_NW * 32, 1)
+    fd3p_kernel(const float *__restrict__ G, const float *__restrict__ u, float *__restrict__ out,
                 KParams<float> p, int nz) {
-  constexpr int NW = F3G_NW, W = 128 * V;
-  extern __shared__ __align__(16) float f3g_smem[];
-  float(*sh)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3g_smem);               // [2][NW][W] phih
-  float(*sq)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3g_smem + 2 * NW * W);  // [4][NW][W] psi
+  constexpr int NW = F3P_NW, W = 128 * V;
+  using L = F3P<V>;
+  extern __shared__ __align__(16) float f3p_smem[];
+  float(*su)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3p_smem + L::U_OFF);
+  float(*sv)[NW + 2][W] = reinterpret_cast<float(*)[NW + 2][W]>(f3p_smem + L::V_OFF);
+  float(*sh)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3p_smem + L::H_OFF);
+  float(*sq)[NW][W] = reinterpret_cast<float(*)[NW][W]>(f3p_smem + L::Q_OFF);
+  const uint32_t bar0 = su32(f3p_smem + L::FLOATS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Ly = p.Ly, Lz = p.Lz;
   const long long plane = (long long)W * Ly, Sz = plane * Lz;
@@ -806,107 +836,202 @@ __global__ void __launch_bounds__(F3G_NW * 32, MINB)
   const int y0 = blockIdx.y * (NW - 4);
   const int yr = y0 - 2 + warp;  // this warp's row (wrapped below)
   const int y = wrapi(yr, Ly), ym = wrapi(yr - 1, Ly), yp = wrapi(yr + 1, Ly);
-  const bool psiw = warp >= 1 && warp <= NW - 2;              // warp-uniform
-  const bool outw = warp >= 2 && warp <= NW - 3 && yr < Ly;   // warp-uniform
+  const bool psiw = warp >= 1 && warp <= NW - 2;             // warp-uniform
+  const bool outw = warp >= 2 && warp <= NW - 3 && yr < Ly;  // warp-uniform
   const int z0 = blockIdx.z * nz, z1 = min(z0 + nz, Lz);
-  auto g4 = [&](const float *f, int yy, int zz, int x) {
-    return __ldg(reinterpret_cast<const float4 *>(f + wrapi(zz, Lz) * plane + (long long)yy * W + x));
+  const int a0 = z0 - 2, a1 = z1 + 1;  // planes phase A advects
+  const bool cubic_half = p.cubic_at_half != 0;
+  auto g4 = [&](const float *f, int yy, int zz, int q) {
+    return __ldg(reinterpret_cast<const float4 *>(f + wrapi(zz, Lz) * plane + (long long)yy * W + 128 * q +
+                                                  4 * lane));
   };
-  auto mv = [](float4 (&d)[V], const float4 (&s2)[V]) {
+  auto ldrow = [&](const float *f, int yy, int zz, float4(&v)[V]) {
 #pragma unroll
-    for (int q = 0; q < V; ++q) d[q] = s2[q];
+    for (int q = 0; q < V; ++q) v[q] = g4(f, yy, zz, q);
   };
-  // phih of this warp's row on plane zz
-  auto advect = [&](int zz, float4 (&h)[V]) {
-    float4 pc[V], uc[V];
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      pc[q] = g4(G, y, zz, 128 * q + 4 * lane);
-      uc[q] = g4(u, y, zz, 128 * q + 4 * lane);
-    }
-    float pl[V], pr[V], ul[V], ur[V];
-    xnbr_row<V>(pc, pl, pr);
-    xnbr_row<V>(uc, ul, ur);
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const int x = 128 * q + 4 * lane;
-      const float4 pzm = g4(G, y, zz - 1, x), pzp = g4(G, y, zz + 1, x);
-      const float4 pym = g4(G, ym, zz, x), pyp = g4(G, yp, zz, x);
-      const float4 vc = g4(vv, y, zz, x), vym = g4(vv, ym, zz, x), vyp = g4(vv, yp, zz, x);
-      const float4 wc = g4(ww, y, zz, x), wzm = g4(ww, y, zz - 1, x), wzp = g4(ww, y, zz + 1, x);
-      float e[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float ph = cmp4(pc[q], j);
-        const float pxm = j == 0 ? pl[q] : cmp4(pc[q], j - 1), pxp = j == 3 ? pr[q] : cmp4(pc[q], j + 1);
-        const float uxm = j == 0 ? ul[q] : cmp4(uc[q], j - 1), uxp = j == 3 ? ur[q] : cmp4(uc[q], j + 1);
-        e[j] = adv_site<FLUX>(ph, pxm, pxp, cmp4(pym, j), cmp4(pyp, j), cmp4(pzm, j), cmp4(pzp, j), uxm,
-                              cmp4(uc[q], j), uxp, cmp4(vym, j), cmp4(vc, j), cmp4(vyp, j), cmp4(wzm, j),
-                              cmp4(wc, j), cmp4(wzp, j), p.dt);
-      }
-      h[q] = make_float4(e[0], e[1], e[2], e[3]);
-    }
-  };
-  auto put = [&](float (*ring)[NW][W], int slot, const float4 (&v)[V]) {
+  auto put = [&](float(*ring)[NW][W], int slot, const float4(&v)[V]) {
 #pragma unroll
     for (int q = 0; q < V; ++q) *reinterpret_cast<float4 *>(&ring[slot][warp][128 * q + 4 * lane]) = v[q];
   };
-  auto get = [&](float (*ring)[NW][W], int slot, int w, int q) {
-    return *reinterpret_cast<const float4 *>(&ring[slot][w][128 * q + 4 * lane]);
+  auto get = [&](const float *row, int q) { return *reinterpret_cast<const float4 *>(row + 128 * q + 4 * lane); };
+  // u and v rows of plane pl (warp 0): 16 + 18 bulk copies of one row each
+  auto issue = [&](int pl) {
+    const int s = pl & 1;
+    const uint32_t bar = bar0 + 8 * s;
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the slot first
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(L::TX_BYTES)
+                   : "memory");
+    }
+    __syncwarp();
+    const long long zo = (long long)wrapi(pl, Lz) * plane;
+    for (int i = lane; i < 2 * NW + 2; i += 32) {
+      const float *src;
+      uint32_t dst;
+      if (i < NW) {
+        src = u + zo + (long long)wrapi(y0 - 2 + i, Ly) * W;
+        dst = su32(&su[s][i][0]);
+      } else {
+        src = vv + zo + (long long)wrapi(y0 - 3 + (i - NW), Ly) * W;
+        dst = su32(&sv[s][i - NW][0]);
+      }
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+          "l"(src), "r"((uint32_t)(W * sizeof(float))), "r"(bar)
+          : "memory");
+    }
   };
-  float4 hm[V], hc[V], hp[V];  // phih of this row at planes k, k + 1, k + 2
-  advect(z0 - 2, hm);
-  advect(z0 - 1, hc);
-  put(sh, (z0 - 1) & 1, hc);
-  for (int k = z0 - 2; k < z1; ++k) {
-    advect(k + 2, hp);
-    put(sh, (k + 2) & 1, hp);
-    __syncthreads();
-    // psi of plane k + 1 (phih of rows y -+ 1 from the ring, phi for the cube)
-    if (psiw) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0) {
+    issue(a0);
+    if (a0 + 1 <= a1) issue(a0 + 1);
+  }
+  // own-row phi of planes a - 1, a, a + 1 and w of the same (a = the plane
+  // phase A advects next), phi of plane a on rows y -+ 1, and phi of plane k
+  // (the cube of phase B)
+  float4 P0[V], P1[V], P2[V], Pym[V], Pyp[V], W0[V], W1[V], W2[V], Pk[V];
+  ldrow(G, y, a0 - 1, P0);
+  ldrow(G, y, a0, P1);
+  ldrow(G, y, a0 + 1, P2);
+  ldrow(G, ym, a0, Pym);
+  ldrow(G, yp, a0, Pyp);
+  ldrow(ww, y, a0 - 1, W0);
+  ldrow(ww, y, a0, W1);
+  ldrow(ww, y, a0 + 1, W2);
+#pragma unroll
+  for (int q = 0; q < V; ++q) Pk[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float2 g2 = pf2(p.dtG, p.dtG);
+  for (int k = z0 - 4; k <= z1 + 1; ++k) {
+    if (warp == 0 && k >= z0 - 3 && k + 3 <= a1) issue(k + 3);
+    // C: phi^{n+1} of plane k - 2
+    if (k >= z0 + 2 && outw) {
+      const int zc = k - 2;
+      const float *qrow = &sq[(zc + 6) % 3][warp][0];
+      float4 qc[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) qc[q] = get(qrow, q);
+      float l[V], r[V];
+      xnbr_row<V>(qc, l, r);
+      float *orow = out + (long long)zc * plane + (long long)yr * W;
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const float4 qm = get(&sq[(zc + 5) % 3][warp][0], q), qp = get(&sq[(zc + 7) % 3][warp][0], q);
+        const float4 qym = get(&sq[(zc + 6) % 3][warp - 1][0], q), qyp = get(&sq[(zc + 6) % 3][warp + 1][0], q);
+        const float4 hm = get(&sh[zc & 3][warp][0], q);
+        float2 Lp[2];
+        lap7_quad(qc[q], qm, qp, qym, qyp, l[q], r[q], Lp[0], Lp[1]);
+        const float2 o0 = pfma(g2, Lp[0], lo2(hm)), o1 = pfma(g2, Lp[1], hi2(hm));
+        *reinterpret_cast<float4 *>(orow + 128 * q + 4 * lane) = make_float4(o0.x, o0.y, o1.x, o1.y);
+      }
+    }
+    // B: psi of plane k
+    if (k >= z0 - 1 && k <= z1 && psiw) {
+      float4 hc[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) hc[q] = get(&sh[k & 3][warp][0], q);
       float l[V], r[V];
       xnbr_row<V>(hc, l, r);
       float4 o4[V];
 #pragma unroll
       for (int q = 0; q < V; ++q) {
-        const float4 hym = get(sh, (k + 1) & 1, warp - 1, q), hyp = get(sh, (k + 1) & 1, warp + 1, q);
-        const float4 gc = g4(G, y, k + 1, 128 * q + 4 * lane);
-        float2 L[2];
-        lap7_quad(hc[q], hm[q], hp[q], hym, hyp, l[q], r[q], L[0], L[1]);
+        const float4 hm = get(&sh[(k + 3) & 3][warp][0], q), hp = get(&sh[(k + 1) & 3][warp][0], q);
+        const float4 hym = get(&sh[k & 3][warp - 1][0], q), hyp = get(&sh[k & 3][warp + 1][0], q);
+        float2 Lp[2];
+        lap7_quad(hc[q], hm, hp, hym, hyp, l[q], r[q], Lp[0], Lp[1]);
         float2 o[2];
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
           const float2 hk = kk ? hi2(hc[q]) : lo2(hc[q]);
-          const float2 cb = p.cubic_at_half ? hk : (kk ? hi2(gc) : lo2(gc));
-          o[kk] = pfma(pf2(p.a, p.a), hk, pfma(pf2(p.b, p.b), pmul(pmul(cb, cb), cb), pmul(pf2(-p.kappa, -p.kappa), L[kk])));
+          const float2 cb = cubic_half ? hk : (kk ? hi2(Pk[q]) : lo2(Pk[q]));
+          o[kk] = pfma(pf2(p.a, p.a), hk,
+                       pfma(pf2(p.b, p.b), pmul(pmul(cb, cb), cb), pmul(pf2(-p.kappa, -p.kappa), Lp[kk])));
         }
         o4[q] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
       }
-      put(sq, (k + 1) & 3, o4);
+      put(sq, (k + 6) % 3, o4);
     }
-    __syncthreads();
-    // phi^{n+1} of plane k (psi planes k - 1, k, k + 1 are in the ring)
-    if (k >= z0 && outw) {
-      float4 qc[V];
+    // A: phih of plane a = k + 2, then the loads of plane a + 1
+    bool ok = true;
+    const int a = k + 2;
+    if (a <= a1) {
+      const int s = a & 1;
+      ok = bar_wait(bar0 + 8 * s, (uint32_t)((a - a0) >> 1) & 1u, g_fd3p_wait_ns);
+      float4 uc[V];
 #pragma unroll
-      for (int q = 0; q < V; ++q) qc[q] = get(sq, k & 3, warp, q);
-      float l[V], r[V];
-      xnbr_row<V>(qc, l, r);
-      float *orow = out + (long long)k * plane + (long long)yr * W;
+      for (int q = 0; q < V; ++q) uc[q] = get(&su[s][warp][0], q);
+      float pl[V], pr[V], ul[V], ur[V];
+      xnbr_row<V>(P1, pl, pr);
+      xnbr_row<V>(uc, ul, ur);
+      float4 h[V];
 #pragma unroll
       for (int q = 0; q < V; ++q) {
-        const float4 qm = get(sq, (k + 3) & 3, warp, q), qp = get(sq, (k + 1) & 3, warp, q);
-        const float4 qym = get(sq, k & 3, warp - 1, q), qyp = get(sq, k & 3, warp + 1, q);
-        float2 L[2];
-        lap7_quad(qc[q], qm, qp, qym, qyp, l[q], r[q], L[0], L[1]);
-        const float2 g = pf2(p.dtG, p.dtG);
-        const float2 o0 = pfma(g, L[0], lo2(hm[q])), o1 = pfma(g, L[1], hi2(hm[q]));
-        *reinterpret_cast<float4 *>(orow + 128 * q + 4 * lane) = make_float4(o0.x, o0.y, o1.x, o1.y);
+        const float4 vc = get(&sv[s][warp + 1][0], q), vym = get(&sv[s][warp][0], q),
+                     vyp = get(&sv[s][warp + 2][0], q);
+        float e[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float ph = cmp4(P1[q], j);
+          const float pxm = j == 0 ? pl[q] : cmp4(P1[q], j - 1), pxp = j == 3 ? pr[q] : cmp4(P1[q], j + 1);
+          const float uxm = j == 0 ? ul[q] : cmp4(uc[q], j - 1), uxp = j == 3 ? ur[q] : cmp4(uc[q], j + 1);
+          e[j] = adv_site<FLUX>(ph, pxm, pxp, cmp4(Pym[q], j), cmp4(Pyp[q], j), cmp4(P0[q], j), cmp4(P2[q], j),
+                                uxm, cmp4(uc[q], j), uxp, cmp4(vym, j), cmp4(vc, j), cmp4(vyp, j),
+                                cmp4(W0[q], j), cmp4(W1[q], j), cmp4(W2[q], j), p.dt);
+        }
+        h[q] = make_float4(e[0], e[1], e[2], e[3]);
+      }
+      put(sh, a & 3, h);
+      // march: phi of plane a - 1 becomes the cube of the next phase B
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        Pk[q] = P0[q];
+        P0[q] = P1[q];
+        P1[q] = P2[q];
+        W0[q] = W1[q];
+        W1[q] = W2[q];
+      }
+      if (a + 1 <= a1) {
+        ldrow(G, y, a + 2, P2);
+        ldrow(G, ym, a + 1, Pym);
+        ldrow(G, yp, a + 1, Pyp);
+        ldrow(ww, y, a + 2, W2);
+      }
+    } else {
+      // no plane left to advect: phi of plane k + 1 for the last phase B
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        Pk[q] = P0[q];
+        P0[q] = P1[q];
       }
     }
-    mv(hm, hc);
-    mv(hc, hp);
+    if (!__syncthreads_and(ok)) {
+      // a copy did not land within the bound: report, drain what is in
+      // flight (planes a and a + 1, with the 0.5 s bound), leave
+      if (threadIdx.x == 0) {
+        atomicExch(&g_fd3p_err, 1);
+        for (int pl = a; pl <= min(a + 1, a1); ++pl)
+          bar_wait(bar0 + 8 * (pl & 1), (uint32_t)((pl - a0) >> 1) & 1u, 500000000ull);
+      }
+      return;
+    }
   }
+}
+
+// resident CTAs of the pipelined substep kernel on this device (queried once per V)
+template <int V>
+int fd3p_resident_v() {
+  static const int g = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fd3p_kernel<false, V>, F3P_NW * 32, F3P<V>::smem);
+    return std::max(1, sms * std::max(per, 1));
+  }();
+  return g;
 }
 
 template <typename S, typename C>
@@ -975,24 +1100,22 @@ cudaError_t fd3d_passes(lbm_handle *h, int in) {
   dim3 gridf(1, rows_f, (p.Lz + nzf - 1) / nzf);
   const int nzf1 = std::max(4, std::min(p.Lz, (int)((long long)p.Lz * rows_f / 152)));  // one CTA per SM
   dim3 gridf1(1, rows_f, (p.Lz + nzf1 - 1) / nzf1);
-  // the advection fused as well, one kernel per substep (opt-in: one CTA per
-  // SM, within one wave of z chunks; at 256^3 it takes 150 us a substep
-  // against 110 us for the advection pass and fd3f)
-  const bool fusedg = fused && std::getenv("HLBM_FD3_FUSED_ADV") != nullptr;
-  const int rows_g = (p.Ly + F3G_NW - 5) / (F3G_NW - 4);
-  const int zch = std::max(1, std::min(p.Lz, 152 / rows_g));
-  const int nzg = std::max(std::min(8, p.Lz), (p.Lz + zch - 1) / zch);
-  dim3 gridg(1, rows_g, (p.Lz + nzg - 1) / nzg);
+  // the advection fused as well, one software-pipelined kernel per substep
+  // (opt-in; one CTA per SM, within one wave of z chunks)
+  const bool fusedp = fused && std::getenv("HLBM_FD3_FUSED_ADV") != nullptr;
+  const int rows_p = (p.Ly + F3P_NW - 5) / (F3P_NW - 4);
+  const int zch = std::max(1, std::min(p.Lz, (p.Lx == 128 ? fd3p_resident_v<1>() : fd3p_resident_v<2>()) / rows_p));
+  const int nzp = (p.Lz + zch - 1) / zch;
+  dim3 gridp(1, rows_p, (p.Lz + nzp - 1) / nzp);
   for (int j = 0; j < h->m; ++j) {
     float *dst = static_cast<float *>(((h->m - 1 - j) % 2 == 0) ? h->phi[1 - in] : h->phi[2]);
-    if (fusedg) {
-      const size_t smg = fd3g_smem_bytes(p.Lx / 128);
+    if (fusedp) {
       if (p.Lx == 128) {
-        if (flux) fd3g_kernel<true, 1, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
-        else fd3g_kernel<false, 1, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
+        if (flux) fd3p_kernel<true, 1><<<gridp, F3P_NW * 32, F3P<1>::smem, h->stream>>>(src, u, dst, p, nzp);
+        else fd3p_kernel<false, 1><<<gridp, F3P_NW * 32, F3P<1>::smem, h->stream>>>(src, u, dst, p, nzp);
       } else {
-        if (flux) fd3g_kernel<true, 2, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
-        else fd3g_kernel<false, 2, 1><<<gridg, F3G_NW * 32, smg, h->stream>>>(src, u, dst, p, nzg);
+        if (flux) fd3p_kernel<true, 2><<<gridp, F3P_NW * 32, F3P<2>::smem, h->stream>>>(src, u, dst, p, nzp);
+        else fd3p_kernel<false, 2><<<gridp, F3P_NW * 32, F3P<2>::smem, h->stream>>>(src, u, dst, p, nzp);
       }
     } else if (vec) {
       if (flux) fd3v_adv_kernel<true><<<gridv, block, 0, h->stream>>>(src, u, A, p, nz);
@@ -1063,18 +1186,28 @@ cudaError_t fd3d_configure(int precision, size_t smem) {
     e = cudaFuncSetAttribute(fd3f_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(float) * 4 * F3F_NW * 256));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fd3g_kernel<false, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fd3g_smem_bytes(1));
+    e = cudaFuncSetAttribute(fd3p_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F3P<1>::smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fd3g_kernel<true, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fd3g_smem_bytes(1));
+    e = cudaFuncSetAttribute(fd3p_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F3P<1>::smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fd3g_kernel<false, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fd3g_smem_bytes(2));
+    e = cudaFuncSetAttribute(fd3p_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F3P<2>::smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fd3g_kernel<true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fd3g_smem_bytes(2));
+    e = cudaFuncSetAttribute(fd3p_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F3P<2>::smem);
   return e;
+}
+
+int fd3p_set_wait_ns(unsigned long long ns) {
+  return cudaMemcpyToSymbol(g_fd3p_wait_ns, &ns, sizeof ns) == cudaSuccess ? 0 : -1;
+}
+
+int fd3p_error(bool reset) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fd3p_err, sizeof v) != cudaSuccess) return -1;
+  if (reset && v != 0) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_fd3p_err, &zero, sizeof zero);
+  }
+  return v;
 }
 
 cudaError_t collide3d_launch(lbm_handle *h, int in, int force_on, int mode) {

@@ -121,6 +121,34 @@ __device__ __forceinline__ int wrapi(int x, int L) {
 // Wraps x in [-L, 2L) into [0, L).
 __device__ __forceinline__ int wrap1(int x, int L) { return x < 0 ? x + L : (x >= L ? x - L : x); }
 
+// ---- shared-memory addresses and bounded mbarrier waits (bulk-copy pipelines) ----
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the mbarrier phase `parity` to complete; gives up after limit_ns
+// (at once, without polling, when limit_ns is 0: try_wait itself may block
+// for a while, long enough for the copies to land).
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return false;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > limit_ns) return false;
+  }
+}
+
 // ---- kernel parameter block (host computes it in FP64, kernels read type C) -------
 template <typename C>
 struct KParams {
@@ -283,5 +311,7 @@ cudaError_t collide2d_tma_batch(const TmaShapeMaps &maps, const float *hin, floa
 
 int collide2d_tma_error(bool reset);  // 1 if a bounded wait of the kernel gave up, -1 on error
 int collide2d_tma_set_wait_ns(unsigned long long ns);  // bound of the copy waits (0 on success)
+int fd3p_error(bool reset);  // the same for the pipelined 3D FD substep kernel
+int fd3p_set_wait_ns(unsigned long long ns);
 
 }  // namespace hlbm

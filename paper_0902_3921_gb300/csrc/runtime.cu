@@ -120,6 +120,8 @@ int cuda_fail(lbm_handle *h, cudaError_t e, const char *what) {
 int check_device_waits(lbm_handle *h) {
   if (h->tma_ready && collide2d_tma_error(true) > 0)
     return fail(h, LBM_ETIMEOUT, "collide kernel: a TMA copy did not complete within its wait bound");
+  if (h->dims == 3 && h->P.precision != LBM_F64 && fd3p_error(true) > 0)
+    return fail(h, LBM_ETIMEOUT, "FD substep kernel: a bulk copy did not complete within its wait bound");
   return LBM_OK;
 }
 
@@ -708,6 +710,13 @@ static int create_impl(const lbm_params *params, void *cuda_stream, const lbm_bu
     // per kernel, shared by all handles of the process)
     e = fd3d_configure(P.precision, fd3d_smem_bytes(P.precision, 1));
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "FD shared-memory configuration"));
+    // bound of the pipelined FD substep's copy waits (as for the 2D collide below)
+    if (P.precision != LBM_F64) {
+      unsigned long long wait_ns = 500000000ull;
+      if (const char *w = std::getenv("HLBM_DEBUG_TMA_WAIT_NS")) wait_ns = std::strtoull(w, nullptr, 10);
+      if (fd3p_set_wait_ns(wait_ns) != 0)
+        return bail(fail(h, LBM_ECUDA, "FD copy wait bound: cudaMemcpyToSymbol failed"));
+    }
   } else {
     e = collide2d_configure(P.precision);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "collide shared-memory configuration"));

@@ -55,6 +55,29 @@ def test_tma_wait_that_gives_up_reports_etimeout(variant, monkeypatch):
     _fresh_run_matches_oracle()
 
 
+def test_fd3_copy_wait_that_gives_up_reports_etimeout(monkeypatch):
+    """The pipelined 3D FD substep (one kernel a substep, its u and v rows
+    staged by bulk copies): a copy wait bounded to 0 ns gives up at once,
+    every CTA drains the copies it issued and returns, and the handle reports
+    LBM_ETIMEOUT at the next moments call."""
+    monkeypatch.setenv("HLBM_FD3_FUSED_ADV", "1")
+    monkeypatch.setenv("HLBM_DEBUG_TMA_WAIT_NS", "0")
+    Lx, Ly, Lz = 128, 19, 21
+    lat = lbm.Lattice(lbm.LbmParams(dims=3, Lx=Lx, Ly=Ly, Lz=Lz, fd_substeps=-8, precision=lbm.LBM_F32DEV,
+                                    **dict(CFG1, N=1 / 6, Q=1 / 3)))
+    n, u = I.rest(3, Lx, Ly, Lz)
+    lat.init_fields(n, I.spinodal(3, Lx, Ly, Lz, seed=2), u)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(2)
+        lat.moments()
+    assert ei.value.code == lbm.LBM_ETIMEOUT, str(ei.value)
+    assert "wait bound" in str(ei.value)
+    lat.close()
+    monkeypatch.delenv("HLBM_DEBUG_TMA_WAIT_NS")
+    monkeypatch.delenv("HLBM_FD3_FUSED_ADV")
+    _fresh_run_matches_oracle()
+
+
 def test_injected_partial_allocation_failure(monkeypatch):
     monkeypatch.setenv("LBM_FAULT", "alloc:3")  # phi[0] after both population buffers
     with pytest.raises(lbm.LbmError) as ei:

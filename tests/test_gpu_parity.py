@@ -317,11 +317,12 @@ def test_3d_fp32_fd_paths(variant, fd_path, shape, monkeypatch):
 
 @pytest.mark.parametrize("shape", [(128, 19, 21), (256, 30, 17)])
 def test_3d_fused_substep_matches_two_kernel_path(shape, monkeypatch):
-    """The one-kernel FD substep (advection, psi and the new phi fused;
-    opt-in) against the advection pass followed by the psi / new-phi kernel:
-    the same FP32 arithmetic per site (the advection of both is one device
-    function, psi and the new phi the same packed operations), so after 10
-    LB steps they agree to rounding at most (bitwise when measured)."""
+    """The one-kernel FD substep (advection, psi and the new phi fused in
+    one software-pipelined kernel; opt-in) against the advection pass
+    followed by the psi / new-phi kernel: the same FP32 arithmetic per site
+    (the advection of both is one device function, psi and the new phi the
+    same packed operations), so after 10 LB steps they agree to rounding at
+    most (bitwise when measured)."""
     Lx, Ly, Lz = shape
     kw = dict(CFG1, N=1 / 6, Q=1 / 3)
     lp = lbm.LbmParams(dims=3, Lx=Lx, Ly=Ly, Lz=Lz, fd_substeps=-8, precision=lbm.LBM_F32DEV, **kw)
