@@ -224,28 +224,67 @@ __global__ void __launch_bounds__(256, MINB)
     }
     const C usq = ux * ux + uy * uy + uz * uz;
     const C uF = ux * Fx + uy * Fy + uz * Fz;
-    // BGK + Guo source (Eqs. 15, 17, 29) per opposite pair (i, i + 1): the
-    // parts even and odd in e_i are formed once and added / subtracted
     const C om = p.tau_inv, keep = C(1) - p.tau_inv;
     const C base = dens - n * (C(1.5) * usq);  // the u-independent and |u|^2 parts
-    const C n3 = C(3) * n, n45 = C(4.5) * n;
-    const C pF3 = C(3) * p.pref, pF9 = C(9) * p.pref, puF = C(3) * p.pref * uF;
-    {
-      const C w = C(q19_w(0)) * wsc;
-      Store<S, C>::st(hout + s, keep * hv[0] + om * (w * base) + w * (-puF), st_scale);
-    }
+    if constexpr (FOLD) {
+      // BGK + Guo source (Eqs. 15, 17, 29) per opposite pair (i, i + 1): with
+      // A = w / tau and B = w (1 - 1/2tau) per weight class, the part even in
+      // e_i is E = A (base + 4.5 n (e.u)^2) + B (9 (e.u)(e.F) - 3 u.F) and the
+      // odd part O = 3 A n (e.u) + 3 B (e.F); f_i = (1 - 1/tau) f_i + E + O,
+      // f_ib = (1 - 1/tau) f_ib + E - O.  e.u and e.F take only the non-zero
+      // components of e_i (the compiler may not drop a product with a zero
+      // component under IEEE rules).  FP16 storage only: the kernel is
+      // issue-bound there (417 against 444 us a launch at 256^3), while the
+      // FP32 kernel, closer to the memory roof, ran slower with this form
+      // (473 against 464 us), so it keeps the one below.
+      const C n45 = C(4.5) * n, m3uF = C(-3) * uF;
+      const C A0 = om * C(q19_w(0)) * wsc, B0 = p.pref * C(q19_w(0)) * wsc;
+      const C A1 = om * C(q19_w(1)) * wsc, B1 = p.pref * C(q19_w(1)) * wsc;  // faces
+      const C A2 = om * C(q19_w(7)) * wsc, B2 = p.pref * C(q19_w(7)) * wsc;  // edges
+      const C An3_1 = C(3) * A1 * n, An3_2 = C(3) * A2 * n;
+      Store<S, C>::st(hout + s, keep * hv[0] + (A0 * base + B0 * m3uF), st_scale);
+      auto edot = [](int ex, int ey, int ez, C a, C b, C c) {
+        C r = ex > 0 ? a : (ex < 0 ? -a : C(0));
+        if (ey != 0) r = ex != 0 ? (ey > 0 ? r + b : r - b) : (ey > 0 ? b : -b);
+        if (ez != 0) r = (ex != 0 || ey != 0) ? (ez > 0 ? r + c : r - c) : (ez > 0 ? c : -c);
+        return r;
+      };
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const int i = 2 * k + 1, ib = i + 1;  // e_ib = -e_i
-      const C w = C(q19_w(i)) * wsc;
-      const C eu = C(q19_ex(i)) * ux + C(q19_ey(i)) * uy + C(q19_ez(i)) * uz;
-      const C eF = C(q19_ex(i)) * Fx + C(q19_ey(i)) * Fy + C(q19_ez(i)) * Fz;
-      const C even = w * (base + n45 * eu * eu);
-      const C odd = w * (n3 * eu);
-      const C Feven = w * (pF9 * eu * eF - puF);
-      const C Fodd = w * (pF3 * eF);
-      Store<S, C>::st(hout + i * Sz + s, keep * hv[i] + om * (even + odd) + (Feven + Fodd), st_scale);
-      Store<S, C>::st(hout + ib * Sz + s, keep * hv[ib] + om * (even - odd) + (Feven - Fodd), st_scale);
+      for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1, ib = i + 1;  // e_ib = -e_i
+        const bool face = k < 3;
+        const C A = face ? A1 : A2, B = face ? B1 : B2, An3 = face ? An3_1 : An3_2;
+        const C eu = edot(q19_ex(i), q19_ey(i), q19_ez(i), ux, uy, uz);
+        const C eF = edot(q19_ex(i), q19_ey(i), q19_ez(i), Fx, Fy, Fz);
+        const C se = n45 * eu * eu + base;
+        const C fe = C(9) * eu * eF + m3uF;
+        const C E = A * se + B * fe;
+        const C O = An3 * eu + C(3) * B * eF;
+        Store<S, C>::st(hout + i * Sz + s, (keep * hv[i] + E) + O, st_scale);
+        Store<S, C>::st(hout + ib * Sz + s, (keep * hv[ib] + E) - O, st_scale);
+      }
+    } else {
+      // BGK + Guo source (Eqs. 15, 17, 29) per opposite pair (i, i + 1): the
+      // parts even and odd in e_i are formed once and added / subtracted
+      const C n3 = C(3) * n, n45 = C(4.5) * n;
+      const C pF3 = C(3) * p.pref, pF9 = C(9) * p.pref, puF = C(3) * p.pref * uF;
+      {
+        const C w = C(q19_w(0));
+        Store<S, C>::st(hout + s, keep * hv[0] + om * (w * base) + w * (-puF), st_scale);
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1, ib = i + 1;  // e_ib = -e_i
+        const C w = C(q19_w(i));
+        const C eu = C(q19_ex(i)) * ux + C(q19_ey(i)) * uy + C(q19_ez(i)) * uz;
+        const C eF = C(q19_ex(i)) * Fx + C(q19_ey(i)) * Fy + C(q19_ez(i)) * Fz;
+        const C even = w * (base + n45 * eu * eu);
+        const C odd = w * (n3 * eu);
+        const C Feven = w * (pF9 * eu * eF - puF);
+        const C Fodd = w * (pF3 * eF);
+        Store<S, C>::st(hout + i * Sz + s, keep * hv[i] + om * (even + odd) + (Feven + Fodd), st_scale);
+        Store<S, C>::st(hout + ib * Sz + s, keep * hv[ib] + om * (even - odd) + (Feven - Fodd), st_scale);
+      }
     }
     uout[s] = ux;
     uout[Sz + s] = uy;
