@@ -1117,6 +1117,19 @@ cudaError_t collide3d(lbm_handle *h, int in, int force_on, int mode) {
   return cudaGetLastError();
 }
 
+// resident blocks of the advection pass on this device (queried once per form)
+template <bool FLUX>
+long long f3v_resident() {
+  static const long long g = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fd3v_adv_kernel<FLUX>, 256, 0);
+    return (long long)std::max(1, sms * std::max(per, 1));
+  }();
+  return g;
+}
+
 // the m substeps of an LB step as three passes each (FP32)
 cudaError_t fd3d_passes(lbm_handle *h, int in) {
   KParams<float> p = make_params<float>(h, 0);
@@ -1126,9 +1139,21 @@ cudaError_t fd3d_passes(lbm_handle *h, int in) {
   const float *src = static_cast<const float *>(h->phi[in]);
   const bool flux = p.adv_variant == LBM_ADV_FLUX;
   const bool vec = p.Lx % 4 == 0 && p.Lx >= 4 && std::getenv("HLBM_FD3_SCALAR") == nullptr;
-  // planes per thread: about 1216 blocks (8 per SM of 152) or 16 planes
+  // planes per thread (at most F3V_NZ): the kernels run a few waves of
+  // resident blocks, and a partial last wave leaves most SMs idle while its
+  // blocks march their planes, so nz minimises waves x (nz + 2), the planes a
+  // block loads (its first two are the z neighbours of the first output)
   const long long bxy = (long long)((p.Lx / 4 + 31) / 32) * ((p.Ly + 7) / 8);
-  const int nz = (int)std::max<long long>(1, std::min<long long>(F3V_NZ, p.Lz * bxy / 1216));
+  const long long res = flux ? f3v_resident<true>() : f3v_resident<false>();
+  int nz = 1;
+  long long best = -1;
+  for (int c = 1; c <= std::min(F3V_NZ, p.Lz); ++c) {
+    const long long waves = (bxy * ((p.Lz + c - 1) / c) + res - 1) / res;
+    if (best < 0 || waves * (c + 2) < best) {
+      best = waves * (c + 2);
+      nz = c;
+    }
+  }
   dim3 gridv((p.Lx / 4 + 31) / 32, (p.Ly + 7) / 8, (p.Lz + nz - 1) / nz);
   // psi and the new phi fused (whole rows per warp: Lx = 128 or 256); planes
   // per CTA: about two (Lx = 128) or one (Lx = 256, 128 registers a thread)
