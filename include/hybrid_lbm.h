@@ -124,13 +124,19 @@ typedef struct lbm_handle lbm_handle;
  *   LBM_FAULT=h2d      lbm_init_fields fails as if its host-to-device copy
  *                      had (LBM_ECUDA, latched on the handle);
  *   HLBM_DEBUG_TMA_WAIT_NS=<ns>  bound of the TMA collide kernels' waits for
- *                      a tile's copies (default 0.5 s; process-wide, set by
- *                      each lbm_create).  A short bound makes the wait give
- *                      up: the kernel lets its issued copies land (that drain
- *                      keeps the 0.5 s bound), skips the tile, and the
- *                      handle reports LBM_ETIMEOUT at the next lbm_moments,
+ *                      a tile's copies, and of the opt-in one-kernel 3D FD
+ *                      substep's waits for its staged u and v rows (default
+ *                      0.5 s; process-wide, set by each lbm_create).  A short
+ *                      bound makes the wait give up: the kernel lets its
+ *                      issued copies land (that drain keeps the 0.5 s
+ *                      bound), skips its work, and the handle reports
+ *                      LBM_ETIMEOUT at the next lbm_moments,
  *                      lbm_diagnostics or lbm_synchronize.  The handle can
  *                      then only be freed.
+ *   HLBM_FD3_FUSED_ADV=1  3D, FP32, Lx = 128 or 256: each FD substep as one
+ *                      software-pipelined kernel (advection, psi and the new
+ *                      phi; the same results as the default two kernels,
+ *                      slower on the GB300).
  * Launch choices (environment, read at creation or once per process):
  *   HLBM_TUNING=sub,rows,cols,collide_rows[,tile]  fixed 2D launch shapes
  *                      instead of the autotuner's timed choice (lbm_tuning
